@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Chebyshev-filter throughput of the PAW-FE R-ChFSI filter on GB300.
+
+Metric: GDoF.vec/s = M * N * m / t_CF, one DoF.vec being one DoF of one vector
+advanced one Chebyshev degree (Algorithm 2 over all N vectors in blocks of B).
+Workload ``mid``: periodic 40 bohr box, 16^3 cells of degree 6 (96^3 = 884,736
+DoFs), 64 atoms x 13 projectors, N = 512 vectors in blocks of 256, degree 30.
+Inputs are seeded synthetic data, resident in HBM (3.6 GB per FP64 block set,
+far above the 129 MB L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+paper's method) on the host cores, on a bounded sample of the same workload.
+Multi-GPU: replicas only (independent problems per rank, no data exchange);
+rank 0 prints one JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+METRIC = "Cheb-filter GDoF·vec/s, FP32/TF32 vs FP64 on GB300 at eigval err ≤1e-6 Ha"
+UNIT = "GDoF*vec/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+_ORACLE_OPS = {}
+
+
+def oracle_sample(workload: str, ncols: int, m: int):
+    """Time the oracle's Algorithm 2 on `ncols` columns and degree `m` (units, seconds).
+
+    The oracle's operator set-up is built once per workload and not timed."""
+    from oracle import cheb
+    from oracle import ops as O
+    if workload not in _ORACLE_OPS:
+        _ORACLE_OPS[workload] = O.PawOperators(inputs.make_system(workload))
+    op = _ORACLE_OPS[workload]
+    X = inputs.start_columns(workload, range(ncols))
+    lam = np.linspace(-0.3, 0.2, ncols)
+    bounds = (-0.5, 0.25, 200.0)
+    t0 = time.perf_counter()
+    cheb.rchfsi_filter(op.apply_H, op.apply_S, op.apply_Sinv_approx, X, lam, m, *bounds)
+    dt = time.perf_counter() - t0
+    return float(op.mesh.ndof) * ncols * m, dt
+
+
+def _threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [os.cpu_count() or 1])
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(workload, ncols=2, m=8):
+    units, dt = oracle_sample(workload, ncols, m)
+    return {"value": units / dt / 1e9, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+            "sample": f"{workload}: {ncols} vectors, Chebyshev degree {m} (Algorithm 2, FP64 numpy/scipy), "
+                      f"{dt:.1f} s; operator set-up excluded"}
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2604_26037_gb300 as P
+
+    torch.cuda.set_device(local)
+    cfg = inputs.CONFIGS[args.workload]
+    sysd = inputs.make_system(args.workload)
+    fe = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32)
+    M, N, m = fe.ndof, cfg["nvec"], cfg["degree"]
+    g = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    X = torch.randn((M, N), dtype=torch.float64, device="cuda", generator=g)
+    lam = fe.rayleigh_ritz(X)                       # S-orthonormal Ritz vectors of the random block
+    tmin, bU = fe.lanczos_bounds(20, 7)
+    bounds = (min(lam[0], tmin), float(lam[-1]), bU)
+    out = torch.empty_like(X)
+    stream = torch.cuda.current_stream()
+
+    def timed(prec, steps, warmup, profile=False):
+        for _ in range(warmup):
+            fe.cheb_filter(X, lam, m, bounds, prec=prec, out=out)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        if profile:
+            fe.profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                fe.cheb_filter(X, lam, m, bounds, prec=prec, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        prof = fe.profile_read() if profile else None
+        if profile:
+            fe.profile_enable(False)
+        _barrier(ws)
+        ms = e0.elapsed_time(e1) / steps
+        return _max_over_ranks(ms, ws), prof, clk.summary()
+
+    ms, prof, clocks = timed(args.prec, args.steps, args.warmup, profile=True)
+    units_per_step = float(M) * N * m
+    value = units_per_step * ws / (ms / 1e3) / 1e9
+
+    # FP64 form of the same filter (the plain method), fewer steps: it is slow on GB300
+    fp64 = None
+    if args.fp64_steps > 0:
+        ms64, _, _ = timed("fp64", args.fp64_steps, 1)
+        fp64 = {"value": units_per_step * ws / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
+                "steps": args.fp64_steps, "warmup": 1}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Xh = X.cpu().pin_memory()
+        Oh = torch.empty_like(Xh).pin_memory()
+        Xd = torch.empty_like(X)
+        for _ in range(1):
+            Xd.copy_(Xh, non_blocking=True)
+            fe.cheb_filter(Xd, lam, m, bounds, prec=args.prec, out=out)
+            Oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Xd.copy_(Xh, non_blocking=True)
+            fe.cheb_filter(Xd, lam, m, bounds, prec=args.prec, out=out)
+            Oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
+        e2e = {"value": units_per_step * ws / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * 8 + N * 8), "d2h_bytes_per_step": int(Oh.numel() * 8)}
+
+    # roofline of the dominant phase
+    peaks = _peaks()
+    phases = {k: v for k, v in prof.items() if isinstance(v, dict)}
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    roof = roofline(dom, phases[dom], fe, sysd, cfg, args.prec, peaks, clocks)
+    launches = prof["total_launches"] // args.steps
+
+    res = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"tf32": "tf32", "fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.prec],
+        "data": "synthetic (seeded), inputs resident in HBM and larger than L2",
+        "config": {"workload": f"{args.workload}: L={sysd['L']} bohr, {cfg['ncell']}^3 cells, p={cfg['p']}, "
+                               f"M={M} DoFs, {sysd['natoms']} atoms x {sysd['nproj']} projectors, "
+                               f"N={N} in blocks of {cfg['block']}, degree {m}",
+                   "precision": args.prec, "y0_storage": "fp32" if args.y0_fp32 else "fp64",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roof,
+        "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in phases.items()},
+        "fp64_form": fp64,
+        "speedup_vs_fp64": (round(value / fp64["value"], 3) if fp64 else None),
+        "e2e": e2e,
+        "bounds": [float(b) for b in bounds],
+    }
+    fe.close()
+    return res
+
+
+def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
+    """Roofline of one phase of the filter, per launch, from algorithmic bytes/flops."""
+    M, B = fe.ndof, cfg["block"]
+    nc, ncells = fe.nodes_per_cell, fe.ncells
+    per_launch_ms = pinfo["ms"] / max(pinfo["intervals"], 1)
+    es = 8 if prec == "fp64" else 4
+    if phase == "cell_products":
+        flops = 2.0 * ncells * nc * nc * B
+        mat_es = {"bf16": 2, "tf32": 4, "fp32": 4, "fp64": 8}[prec]
+        byts = ncells * nc * nc * mat_es + M * B * es * 3        # H^e stream + gather + accumulate r/w
+    elif phase == "residual_Y":
+        flops = 2.0 * 2.0 * ncells * nc * nc * B                  # H^e and M^e products in FP64
+        byts = ncells * nc * nc * 8 + M * B * 8 * 3
+        es = 8
+    else:
+        flops = None
+        byts = None
+    if byts is None:
+        return {"bound": "hbm", "achieved": None, "peak": peaks["hbm"], "unit": "GB/s", "frac": None,
+                "traffic": None, "kernel": phase}
+    sec = per_launch_ms / 1e3
+    gbs = byts / sec / 1e9
+    tfs = flops / sec / 1e12
+    hbm_frac = gbs / peaks["hbm"]
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    if prec in ("tf32", "bf16"):
+        cpk = peaks["bf16"] * (0.5 if prec == "tf32" else 1.0)   # TF32 dense = bf16 x 1.1/2.25 nominal
+        cunit, cbound = "TFLOP/s", "tensor"
+    elif es == 8 or phase == "residual_Y":
+        cpk = 1.25 * sm_mhz / 2070.0                              # FP64: 1.25 TFLOP/s at 2070 MHz
+        cunit, cbound = "TFLOP/s", "alu"
+    else:
+        cpk = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12                # FP32 FFMA: 152 SMs x 128 lanes x 2
+        cunit, cbound = "TFLOP/s", "alu"
+    c_frac = tfs / cpk
+    if c_frac >= hbm_frac:
+        return {"bound": cbound, "achieved": round(tfs, 3), "peak": round(cpk, 2), "unit": cunit,
+                "frac": round(c_frac, 4), "traffic": None, "kernel": phase,
+                "algorithmic_flops_per_launch": flops, "ms_per_launch": round(per_launch_ms, 4),
+                "hbm_frac": round(hbm_frac, 4), "peak_source": peaks["src"]}
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm"], "unit": "GB/s",
+            "frac": round(hbm_frac, 4), "traffic": None, "kernel": phase,
+            "algorithmic_bytes_per_launch": byts, "ms_per_launch": round(per_launch_ms, 4),
+            "compute_frac": round(c_frac, 4), "peak_source": peaks["src"]}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    cfg = inputs.CONFIGS[args.workload]
+    ncols, m = 1, 3
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, ncols, m)
+    for _ in range(args.steps):
+        u, dt = oracle_sample(args.workload, ncols, m)
+        vals.append(u / dt / 1e9)
+    v = statistics.median(vals)
+    cb = {"value": v, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+          "sample": f"{args.workload}: {ncols} vector, Chebyshev degree {m} per step (Algorithm 2, FP64 "
+                    f"numpy/scipy); operator set-up excluded"}
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": args.workload, "precision": "fp64", "parallelism": "cpu"},
+            "cpu_baseline": cb, "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid", choices=sorted(inputs.CONFIGS))
+    ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "bf16", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--y0-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if ws > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+    else:
+        res = run_ours(args, ws, rank, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if ws > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * paw_fe.h -- C ABI of the GB300 (sm_103a) PAW finite-element Chebyshev filter.
+ *
+ * The library implements the Chebyshev-filtering step of the residual-based
+ * Chebyshev filtered subspace iteration (R-ChFSI) for the PAW generalised
+ * eigenproblem H X = S X Lambda discretised with finite elements
+ * (Algorithm 2 of the paper; Sec. 3.1 and Sec. 4.3-4.4), together with the
+ * operators it is built from and the FP64 Rayleigh-Ritz step around it
+ * (Algorithm 1, steps 4-6).
+ *
+ * Conventions
+ * -----------
+ * - Every call returns a paw_status; nothing throws or aborts across the ABI.
+ *   paw_last_error() returns a message for the last failing call made by the
+ *   calling thread (valid until that thread's next call).
+ * - Multivectors are caller-owned DEVICE arrays, DoF-major with the vector
+ *   index fastest: element (dof, j) of X is X[dof * ld + j], ld >= ncols.
+ *   (A column block of a wider array is addressed by offsetting the pointer
+ *   by the first column and passing the full row length as ld.)
+ * - Element type follows the precision argument: double for PAW_FP64,
+ *   float for PAW_FP32 / PAW_TF32 / PAW_BF16.
+ * - Small descriptor arrays (positions, shells, coupling matrices,
+ *   eigenvalues, bounds) are HOST arrays, copied or read during the call.
+ * - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *   void*; NULL = legacy default stream).  Calls that return host results
+ *   (eigenvalues, norms, bounds) synchronise that stream.
+ * - The library owns the device memory behind a handle (operator data and
+ *   workspaces); it is freed by paw_destroy().  Workspaces grow on demand,
+ *   so the first call at a new block width may allocate.
+ * - One handle must not be used from two host threads at the same time.
+ *
+ * Discretisation (Sec. 2.2, Sec. 4.1): periodic cube [0, L)^3 split into n^3
+ * equal cells; C0 Lagrange elements of degree p on Gauss-Lobatto-Legendre
+ * nodes; global DoF of lattice point (i, j, k) is i + N1 (j + N1 k) with
+ * N1 = n p.  Kinetic and mass cell matrices use (p+1)^3 Gauss points, the
+ * potential and projector integrals use (p+2)^3 Gauss points; quadrature
+ * point q = i + (p+2) (j + (p+2) k) of cell e = cx + n (cy + n cz).
+ */
+#ifndef PAW_FE_H
+#define PAW_FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paw_context *paw_handle;
+
+typedef enum {
+  PAW_OK = 0,
+  PAW_ERR_INVALID_ARG = 1,   /* bad size, pointer, ordering of bounds ...      */
+  PAW_ERR_UNSUPPORTED = 2,   /* non-periodic mesh, k != 0, l > 2, degree > 8  */
+  PAW_ERR_NOT_SPD = 3,       /* overlap not positive definite (create / RR)   */
+  PAW_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed   */
+  PAW_ERR_NO_MEMORY = 5,     /* device allocation failed                       */
+  PAW_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up             */
+  PAW_ERR_NONFINITE = 7,     /* NaN/Inf detected in an input or a result       */
+  PAW_ERR_LIBRARY = 8        /* cuBLAS / cuSOLVER reported an error            */
+} paw_status;
+
+typedef enum {
+  PAW_FP64 = 0,  /* every step in FP64: the plain method                      */
+  PAW_FP32 = 1,  /* filter bracket in FP32 storage and FP32 FMA arithmetic     */
+  PAW_TF32 = 2,  /* FP32 storage; cell products on tcgen05 tensor cores (TF32  */
+                 /* operands, FP32 accumulation in tensor memory)              */
+  PAW_BF16 = 3   /* as PAW_TF32 with BF16 cell-matrix and vector operands      */
+} paw_precision;
+
+/* Periodic cubic box: L[0] = L[1] = L[2] and n_cells equal, periodic = 1. */
+typedef struct {
+  double L[3];
+  int32_t n_cells[3];
+  int32_t periodic[3];
+} paw_mesh;
+
+/* Atom positions (bohr), host array natoms x 3.  natoms may be 0. */
+typedef struct {
+  int32_t natoms;
+  const double *positions;
+} paw_atoms;
+
+/* Projector shells shared by every atom: shell s is the Gaussian-radial
+ * projector family N_l r^l exp(-r^2 / (2 w_s^2)) Y_lm(r^) (real harmonics,
+ * m = -l..l, unit L2 norm, truncated at w_s sqrt(2 ln 1e8)), l_s in 0..2.
+ * Projectors of an atom are numbered shell by shell, m ascending. */
+typedef struct {
+  int32_t nshells;
+  const int32_t *l;
+  const double *width;
+} paw_projectors;
+
+/* Synthetic local potential V(x) = -sum_g A_g exp(-|x - c_g|^2 / (2 w_g^2))
+ * summed over periodic images within 8 w_g.  ngauss may be 0 (V = 0). */
+typedef struct {
+  int32_t ngauss;
+  const double *centers; /* ngauss x 3 */
+  const double *depth;   /* ngauss, A_g (Ha) */
+  const double *width;   /* ngauss, w_g (bohr) */
+} paw_vloc;
+
+typedef struct {
+  int32_t block;       /* vector block width B of paw_cheb_filter (0: 256)      */
+  int32_t pp_overlap;  /* 1: use G_a = <p|p> (Sec. 3.1, third approximation)     */
+  int32_t y0_fp32;     /* 1: store Y = H X - S X Lambda in FP32 in mixed modes   */
+  int32_t reserved;
+} paw_options;
+
+/* Filter bounds (Algorithm 2 inputs): a0 lower end of the wanted spectrum,
+ * bW upper end of the wanted spectrum, bU upper bound of the whole spectrum.
+ * Requires a0 < bW < bU. */
+typedef struct {
+  double a0, bW, bU;
+} paw_bounds;
+
+typedef struct {
+  int64_t ndof;        /* M = (n p)^3                                        */
+  int32_t ncells;      /* n^3                                                */
+  int32_t nodes_per_cell;  /* (p+1)^3                                       */
+  int32_t quad_per_cell;   /* (p+2)^3                                       */
+  int32_t natoms;
+  int32_t nproj;       /* projectors per atom                                */
+  int32_t degree;      /* p                                                  */
+  int64_t support_pairs;   /* number of (cell, atom) pairs in projector supports */
+  int64_t device_bytes;    /* device memory currently held by the handle       */
+} paw_info;
+
+/* Build every operator of the problem (Sec. 4.1): cell matrices
+ * H^e = 1/2 K^e + V^e (Eq. FEM Ham entries), the shared mass cell matrix M^e
+ * (Eq. FEM S_loc entries), the lumped GLL mass M_D, projector cell matrices
+ * C^{e,a} (Eq. FEM Cmatrix) and their assembly P^a, G_a = P^a^T M_D^-1 P^a
+ * and Delta_Sinv^a = dS^a (I + G_a dS^a)^-1 (Eq. Delta Sinv).
+ *   D_ij, dS_ij : host, natoms x nproj x nproj, symmetric (checked to 1e-12
+ *                 relative); Delta_H^a and Delta_S^a of Eq. FE nonlocal
+ *                 contribution.
+ *   vloc        : may be NULL (V = 0); see also paw_set_veff.
+ *   opts        : may be NULL (defaults).
+ * Errors: INVALID_ARG (sizes, asymmetry, NULL out), UNSUPPORTED (non-cubic
+ * or non-periodic box, degree outside 1..8, l > 2, a projector cutoff of
+ * half the box or more), NOT_SPD (I + G_a dS^a singular or with a
+ * non-positive eigenvalue for some atom), NO_MEMORY, CUDA. */
+paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atoms,
+                         const paw_projectors *proj, const double *D_ij,
+                         const double *dS_ij, const paw_vloc *vloc,
+                         const paw_options *opts, paw_handle *out);
+
+/* Replace the potential: V_q is a DEVICE array ncells x (p+2)^3 (FP64) of the
+ * potential at the quadrature points; rebuilds V^e and H^e (Eq. FEM Ham
+ * entries).  Synchronous. */
+paw_status paw_set_veff(paw_handle h, const double *V_q);
+
+/* Replace Delta_H (host, natoms x nproj x nproj, symmetric).  Synchronous. */
+paw_status paw_set_dij(paw_handle h, const double *D_ij);
+
+paw_status paw_get_info(paw_handle h, paw_info *out);
+
+/* Y = H X (Eq. FE nonlocal contribution: cell-matrix local part by
+ * extraction, cell products and assembly, Sec. 4.3, plus sum_a P^a D^a P^a^T).
+ * X, Y device, ncols >= 0 (0 is a no-op), ldx, ldy >= ncols; X and Y must
+ * not overlap. */
+paw_status paw_apply_H(paw_handle h, paw_precision prec, const void *X, void *Y,
+                       int ncols, int ldx, int ldy, void *stream);
+
+/* Y = S X with S = M + sum_a P^a dS^a P^a^T (consistent mass M). */
+paw_status paw_apply_S(paw_handle h, paw_precision prec, const void *X, void *Y,
+                       int ncols, int ldx, int ldy, void *stream);
+
+/* Y = Shat^-1 X, the approximate inverse overlap of Eq. Sinvapprox:
+ * M_D^-1 X - sum_a M_D^-1 P^a Delta_Sinv^a P^a^T M_D^-1 X. */
+paw_status paw_apply_Sinv_approx(paw_handle h, paw_precision prec, const void *X,
+                                 void *Y, int ncols, int ldx, int ldy, void *stream);
+
+/* Algorithm 2: Psi_f = Shat^-1 R_m + Psi_in C_m(Lambda~) for one or more
+ * blocks of columns (processed opts.block columns at a time).
+ *   X_in      : device FP64 ndof x ncols (ld ldx), the block Psi_in
+ *   lambda_in : host FP64 ncols, the eigenvalue estimates Lambda
+ *   degree    : m >= 1 (H applied m times, Shat^-1 applied m times)
+ *   X_out     : device FP64 ndof x ncols (ld ldo); may not alias X_in
+ * Y = H X - S X Lambda is formed in FP64 (step 2); for PAW_FP32/TF32/BF16 the
+ * recurrence bracket is evaluated in reduced precision, the term
+ * (2 zeta/e) Y Lambda_Y is added in FP64 and R is stored in FP32 (Sec. 4.4,
+ * mixed precision computation).  Errors: INVALID_ARG (a0 < bW < bU violated,
+ * degree < 1, sizes), NO_MEMORY, CUDA. */
+paw_status paw_cheb_filter(paw_handle h, paw_precision prec, const double *X_in,
+                           int ldx, const double *lambda_in, int ncols, int degree,
+                           paw_bounds bounds, double *X_out, int ldo, void *stream);
+
+/* Rayleigh-Ritz (Algorithm 1 steps 4-6) in FP64:
+ * H^p = X^T H X, S^p = X^T S X, H^p Q = S^p Q Lambda, X <- X Q.
+ *   X          : device FP64 ndof x N (ld), overwritten by the S-orthonormal
+ *                Ritz vectors in ascending order of Ritz value
+ *   lambda_out : host FP64 N
+ * H X and S X are formed block by block (opts.block columns) with the FP64
+ * cell kernels; the projections and the rotation use cuBLAS DGEMM and the
+ * projected problem cuSOLVER dsygvd.
+ * Errors: NOT_SPD (S^p not positive definite), LIBRARY, NO_MEMORY. */
+paw_status paw_rayleigh_ritz(paw_handle h, double *X, int ld, int N,
+                             double *lambda_out, void *stream);
+
+/* rnorm_out[i] = || H x_i - lambda_i S x_i ||_2 (FP64, unweighted), host out. */
+paw_status paw_residuals(paw_handle h, const double *X, int ld, const double *lambda,
+                         int N, double *rnorm_out, void *stream);
+
+/* k-step generalised Lanczos on Shat^-1 H in the S inner product from a seeded
+ * random start (FP64): theta_min, and upper = theta_max + |beta_k s_k| as the
+ * estimate of b_U (Algorithm 1 step 1).  Host outputs. */
+paw_status paw_lanczos_bounds(paw_handle h, int k, uint64_t seed, double *theta_min,
+                              double *upper, void *stream);
+
+/* E = tr(X^T H X) = sum_i x_i^T H x_i (host FP64 out), the subspace
+ * Rayleigh-quotient energy whose gradient paw_energy_grad returns.  X is
+ * FP64 (PAW_FP64) or FP32 (other precisions; H applied as by paw_apply_H). */
+paw_status paw_energy(paw_handle h, paw_precision prec, const void *X, int ld, int N,
+                      double *E_out, void *stream);
+
+/* Gradient of E = tr(X^T H X) with X fixed (linear in V and Delta_H):
+ *   dE_dV : device FP64 ncells x (p+2)^3, w_q detJ sum_i u_i(x_q)^2
+ *   dE_dD : device FP64 natoms x nproj x nproj, sum_i U_i U_i^T, U = P^a^T X
+ * (entries of Delta_H treated as independent).  X is FP64 or FP32 by prec. */
+paw_status paw_energy_grad(paw_handle h, paw_precision prec, const void *X, int ld,
+                           int N, double *dE_dV, double *dE_dD, void *stream);
+
+/* Phase timing of paw_cheb_filter (tracing, not part of the method).  When
+ * enabled, every phase of Algorithm 2 is bracketed by CUDA events recorded on
+ * the caller's stream; paw_profile_read synchronises and returns the summed
+ * device time per phase and the number of kernels the library launched.
+ * Phases: 0 Y = H X - S X Lambda (step 2), 1 recurrence update and M_D^-1
+ * scaling, 2 nonlocal part of Shat^-1, 3 cell products H^e T_e with
+ * extraction and assembly, 4 nonlocal part of H, 5 recovery (step 5). */
+#define PAW_NPHASES 6
+typedef struct {
+  double ms[PAW_NPHASES];
+  int64_t intervals[PAW_NPHASES];
+  int64_t launches[PAW_NPHASES];
+  int64_t total_launches;   /* all kernels launched by the library since enable */
+} paw_profile;
+
+/* enable = 1 resets the accumulators and starts recording; 0 stops. */
+paw_status paw_profile_enable(paw_handle h, int enable);
+paw_status paw_profile_read(paw_handle h, paw_profile *out);
+
+/* Device-side status words (bounded waits, non-finite checks) since the last
+ * call; PAW_OK if none was raised.  Synchronises the handle's last stream. */
+paw_status paw_sync_status(paw_handle h);
+
+paw_status paw_destroy(paw_handle h);
+
+const char *paw_last_error(void);
+
+/* Library version string (static storage). */
+const char *paw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAW_FE_H */

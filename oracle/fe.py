@@ -206,6 +206,13 @@ def gaussian_potential(pts: np.ndarray, L: float, centers, depth, width,
     V = np.zeros(pts.shape[:-1])
     for R, A, w in zip(np.asarray(centers), np.asarray(depth), np.asarray(width)):
         rc = image_cut * w
+        if rc < L / 2:
+            # at most one image lies within rc: the minimum image
+            d = pts - R
+            d -= L * np.round(d / L)
+            r2 = np.sum(d * d, -1)
+            V -= np.where(r2 < rc * rc, A * np.exp(-r2 / (2 * w * w)), 0.0)
+            continue
         nim = int(math.ceil(rc / L))
         for ix in range(-nim, nim + 1):
             for iy in range(-nim, nim + 1):
@@ -336,7 +343,7 @@ def projector_matrix(mesh: Mesh, sysd: dict, atom: int):
     npj = sysd["nproj"]
     d = min_image(pts[near] - R, mesh.L)                   # (nnear, nq, 3)
     pv = projector_values(shells, d)                       # (nnear, nq, npj)
-    Ce = np.einsum("qi,q,eqa->eia", N, W * mesh.detJ, pv)  # C^{e,a}: (nnear, nc, npj)
+    Ce = np.matmul(N.T, (W * mesh.detJ)[None, :, None] * pv)   # C^{e,a}: (nnear, nc, npj)
     alldofs = mesh.cell_dofs[near].reshape(-1)
     dofs, inv = np.unique(alldofs, return_inverse=True)
     vals = np.zeros((len(dofs), npj))

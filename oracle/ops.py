@@ -82,10 +82,10 @@ class PawOperators:
         """(1/2 K + V_mass) X by cell gather, cell product and assembly."""
         X = np.asarray(X, float)
         Xe = self._gather(X)
-        Ye = np.einsum("ij,ejv->eiv", self.K, Xe)
-        U = np.einsum("qj,ejv->eqv", self.Nq, Xe)          # values at quad points
+        Ye = np.matmul(self.K, Xe)                         # (1/2) K^e X_e, every cell
+        U = np.matmul(self.Nq, Xe)                         # values at quad points
         U *= (self.Wq[None, :] * self.Vq)[:, :, None]
-        Ye += np.einsum("qi,eqv->eiv", self.Nq, U)
+        Ye += np.matmul(self.Nq.T, U)                      # + V^e X_e
         return self._assemble(Ye)
 
     def apply_H(self, X):
@@ -94,7 +94,7 @@ class PawOperators:
 
     def apply_M(self, X):
         X = np.asarray(X, float)
-        Ye = np.einsum("ij,ejv->eiv", self.Me, self._gather(X))
+        Ye = np.matmul(self.Me, self._gather(X))
         return self._assemble(Ye)
 
     def apply_S(self, X):

@@ -1,0 +1,922 @@
+// C ABI entry points, the Algorithm 2 driver, Rayleigh-Ritz, residuals,
+// Lanczos bounds and the energy gradient.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "common.cuh"
+
+namespace pawfe {
+
+static thread_local std::string g_last_error;
+int64_t g_launch_count = 0;
+
+static cudaEvent_t prof_event(paw_context *c) {
+  auto &P = c->prof;
+  if (P.used == P.pool.size()) {
+    cudaEvent_t e;
+    PAW_CUDA(cudaEventCreate(&e));
+    P.pool.push_back(e);
+  }
+  return P.pool[P.used++];
+}
+
+PhaseScope::PhaseScope(paw_context *ctx, int phase, cudaStream_t st) : c(ctx), ph(phase), s(st) {
+  if (!c->prof.on) return;
+  a = prof_event(c);
+  PAW_CUDA(cudaEventRecord(a, s));
+  l0 = g_launch_count;
+}
+
+PhaseScope::~PhaseScope() {
+  if (!c->prof.on || !a) return;
+  cudaEvent_t b = nullptr;
+  try {
+    b = prof_event(c);
+  } catch (...) {
+    return;
+  }
+  if (cudaEventRecord(b, s) == cudaSuccess) c->prof.marks.push_back({ph, a, b});
+  c->prof.launches[ph] += g_launch_count - l0;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+paw_status fail(paw_status code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+void DevBuf::ensure(size_t nbytes, int64_t *counter) {
+  if (nbytes <= bytes && ptr) return;
+  if (ptr) {
+    cudaFree(ptr);
+    if (counter) *counter -= (int64_t)bytes;
+    ptr = nullptr;
+    bytes = 0;
+  }
+  if (nbytes == 0) return;
+  PAW_CUDA(cudaMalloc(&ptr, nbytes));
+  bytes = nbytes;
+  if (counter) *counter += (int64_t)bytes;
+}
+
+void DevBuf::release(int64_t *counter) {
+  if (ptr) {
+    cudaFree(ptr);
+    if (counter) *counter -= (int64_t)bytes;
+  }
+  ptr = nullptr;
+  bytes = 0;
+}
+
+// ============================================================== filter kernels
+// R_Y = (zeta_1/e) Y, R_X = 0 (Algorithm 2 step 3); optional FP32 copy of Y.
+template <typename TR>
+__global__ void k_cheb_init(int64_t rows, int ncols, const double *__restrict__ Y0, int ldy,
+                            double s, TR *__restrict__ RY, TR *__restrict__ RX, int ldr,
+                            float *__restrict__ Y0f) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= rows || v >= ncols) return;
+  const double y = Y0[i * ldy + v];
+  RY[i * ldr + v] = (TR)(s * y);
+  RX[i * ldr + v] = TR(0);
+  if (Y0f) Y0f[i * ldr + v] = (float)y;
+}
+
+// Loop body of Algorithm 2 before the operator products:
+//   T   = M_D^-1 R_Y                                  (first factor of Shat^-1)
+//   R_X = [-beta R_Y - gamma R_X]_(TR) + alpha Y Lambda_Y   (FP64 add, TR store)
+// The H Shat^-1 R_Y term is accumulated into R_X afterwards.
+template <typename TR, typename TY>
+__global__ void k_cheb_base(int64_t rows, int ncols, const TR *__restrict__ RY, TR *__restrict__ RX,
+                            TR *__restrict__ T, int ldr, const TY *__restrict__ Y0, int ldy,
+                            const double *__restrict__ lamY, double alpha, TR beta, TR gamma,
+                            const TR *__restrict__ mdinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= rows || v >= ncols) return;
+  const TR ry = RY[i * ldr + v];
+  const TR bracket = -beta * ry - gamma * RX[i * ldr + v];
+  const double full = (double)bracket + alpha * (double)Y0[i * ldy + v] * lamY[v];
+  RX[i * ldr + v] = (TR)full;
+  T[i * ldr + v] = mdinv[i] * ry;
+}
+
+// Algorithm 2 step 5: Psi_f = Shat^-1 R_Y + X Lambda_Y, combined in FP64.
+template <typename TR>
+__global__ void k_cheb_recover(int64_t rows, int ncols, const TR *__restrict__ T, int ldr,
+                               const double *__restrict__ X, int ldx, const double *__restrict__ lamY,
+                               double *__restrict__ Xo, int ldo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= rows || v >= ncols) return;
+  Xo[i * ldo + v] = (double)T[i * ldr + v] + X[i * ldx + v] * lamY[v];
+}
+
+static inline dim3 ew_grid(int64_t rows, int ncols) {
+  return dim3((unsigned)((rows + 7) / 8), (ncols + 31) / 32);
+}
+
+// Y = H X - S X Lambda in FP64 (Algorithm 2 step 2)
+static void residual_block(paw_context *c, const double *X, int ldx, const double *negLam_dev,
+                           double *Y, int ldy, int ncols, cudaStream_t s) {
+  zero_block<double>(Y, c->ndof, ncols, ldy, s);
+  cell_apply_simt<double>(c, c->He64.as<double>(), (long long)c->nc * c->nc, X, ldx, Y, ldy, ncols, 1.0,
+                          nullptr, s);
+  cell_apply_simt<double>(c, c->Me64.as<double>(), 0, X, ldx, Y, ldy, ncols, 1.0, negLam_dev, s);
+  if (c->nent > 0) {
+    c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npj * ncols, &c->dev_bytes);
+    double *W = c->ws_W2.as<double>();
+    nl_project<double>(c, X, ldx, ncols, nullptr, c->DH64.as<double>(), 1.0, W, s);
+    nl_expand<double>(c, W, ncols, Y, ldy, 1.0, nullptr, nullptr, s);
+    nl_project<double>(c, X, ldx, ncols, nullptr, c->DS64.as<double>(), 1.0, W, s);
+    nl_expand<double>(c, W, ncols, Y, ldy, 1.0, nullptr, negLam_dev, s);
+  }
+}
+
+template <typename T>
+static const T *mdinv_of(paw_context *c);
+template <>
+const double *mdinv_of<double>(paw_context *c) { return c->md_inv64.as<double>(); }
+template <>
+const float *mdinv_of<float>(paw_context *c) { return c->md_inv32.as<float>(); }
+
+// One block of Algorithm 2 in working precision TR.
+template <typename TR>
+static void cheb_block(paw_context *c, paw_precision prec, const double *X, int ldx, const double *lam,
+                       int nb, int m, paw_bounds bd, double *Xo, int ldo, cudaStream_t s) {
+  const int64_t M = c->ndof;
+  const double e = (bd.bU - bd.bW) / 2.0;
+  const double cc = (bd.bU + bd.bW) / 2.0;
+  double zeta = e / (bd.a0 - cc);
+  double zeta1 = zeta;
+  const double gam = 2.0 / zeta1;
+  // scalar recurrences on the host (Algorithm 2 steps 1, 3, 4)
+  std::vector<double> LX(nb, 1.0), LY(nb), lam_hist;   // lam_hist: Lambda_Y per loop step, then final
+  std::vector<double> al_h, be_h, ga_h;
+  for (int j = 0; j < nb; ++j) LY[j] = (zeta1 / e) * (lam[j] - cc);
+  for (int th = 2; th <= m; ++th) {
+    zeta1 = 1.0 / (gam - zeta);
+    const double alpha = 2.0 * zeta1 / e, beta = alpha * cc, gk = zeta * zeta1;
+    al_h.push_back(alpha);
+    be_h.push_back(beta);
+    ga_h.push_back(gk);
+    lam_hist.insert(lam_hist.end(), LY.begin(), LY.end());
+    for (int j = 0; j < nb; ++j) {
+      const double nx = alpha * LY[j] * lam[j] - beta * LY[j] - gk * LX[j];
+      LX[j] = LY[j];
+      LY[j] = nx;
+    }
+    zeta = zeta1;
+  }
+  lam_hist.insert(lam_hist.end(), LY.begin(), LY.end());
+  std::vector<double> neglam(nb);
+  for (int j = 0; j < nb; ++j) neglam[j] = -lam[j];
+  const int nsteps = m - 1;
+  c->ws_lam.ensure(sizeof(double) * (lam_hist.size() + nb), &c->dev_bytes);
+  double *d_lam = c->ws_lam.as<double>();
+  double *d_neglam = d_lam + lam_hist.size();
+  PAW_CUDA(cudaMemcpyAsync(d_lam, lam_hist.data(), sizeof(double) * lam_hist.size(), cudaMemcpyHostToDevice, s));
+  PAW_CUDA(cudaMemcpyAsync(d_neglam, neglam.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+
+  const int ldr = nb;
+  c->ws_Y0.ensure(sizeof(double) * M * nb, &c->dev_bytes);
+  c->ws_RX.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
+  c->ws_RY.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
+  c->ws_T.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
+  const bool y0f = (sizeof(TR) == 4) && c->opts.y0_fp32;
+  if (y0f) c->ws_Y0f.ensure(sizeof(float) * M * nb, &c->dev_bytes);
+  double *Y0 = c->ws_Y0.as<double>();
+  TR *RX = c->ws_RX.as<TR>(), *RY = c->ws_RY.as<TR>(), *T = c->ws_T.as<TR>();
+  const size_t wbytes = sizeof(TR) * (size_t)std::max(1, c->natoms * c->npj) * nb;
+  c->ws_W.ensure(wbytes, &c->dev_bytes);
+  TR *W = c->ws_W.as<TR>();
+
+  // step 2: Y = H X - S X Lambda (FP64)
+  {
+    PhaseScope ps(c, 0, s);
+    residual_block(c, X, ldx, d_neglam, Y0, nb, nb, s);
+  }
+  // step 3
+  const dim3 blk(32, 8);
+  {
+    PhaseScope ps(c, 1, s);
+    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, 1.0 / (bd.a0 - cc), RY, RX, ldr,
+                                                   y0f ? c->ws_Y0f.as<float>() : nullptr);
+    PAW_LAUNCH_CHECK("k_cheb_init");
+  }
+  const TR *mdinv = mdinv_of<TR>(c);
+  // step 4
+  for (int k = 0; k < nsteps; ++k) {
+    const double alpha = al_h[k];
+    {
+      PhaseScope ps(c, 1, s);
+      if (y0f)
+        k_cheb_base<TR, float><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, RY, RX, T, ldr, c->ws_Y0f.as<float>(), ldr,
+                                                              d_lam + (size_t)k * nb, alpha, (TR)be_h[k],
+                                                              (TR)ga_h[k], mdinv);
+      else
+        k_cheb_base<TR, double><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, RY, RX, T, ldr, Y0, nb,
+                                                               d_lam + (size_t)k * nb, alpha, (TR)be_h[k],
+                                                               (TR)ga_h[k], mdinv);
+      PAW_LAUNCH_CHECK("k_cheb_base");
+    }
+    if (c->nent > 0) {   // T = Shat^-1 R_Y (Eq. Sinvapprox)
+      PhaseScope ps(c, 2, s);
+      nl_project<TR>(c, T, ldr, nb, nullptr, c->DSinv64.as<double>(), 1.0, W, s);
+      nl_expand<TR>(c, W, nb, T, ldr, -1.0, mdinv, nullptr, s);
+    }
+    // R_X += alpha H T  (local cell products, then nonlocal)
+    {
+      PhaseScope ps(c, 3, s);
+      if constexpr (sizeof(TR) == 4) {
+        if (prec == PAW_TF32 || prec == PAW_BF16)
+          cell_apply_tc(c, prec, (const float *)T, ldr, (float *)RX, ldr, nb, (float)alpha, s);
+        else
+          cell_apply_simt<TR>(c, c->He32.as<TR>(), (long long)c->nc * c->nc, T, ldr, RX, ldr, nb, alpha,
+                              nullptr, s);
+      } else {
+        cell_apply_simt<TR>(c, c->He64.as<TR>(), (long long)c->nc * c->nc, T, ldr, RX, ldr, nb, alpha,
+                            nullptr, s);
+      }
+    }
+    if (c->nent > 0) {
+      PhaseScope ps(c, 4, s);
+      nl_project<TR>(c, T, ldr, nb, nullptr, c->DH64.as<double>(), alpha, W, s);
+      nl_expand<TR>(c, W, nb, RX, ldr, 1.0, nullptr, nullptr, s);
+    }
+    std::swap(RX, RY);
+  }
+  // step 5: Psi_f = Shat^-1 R_Y + X Lambda_Y
+  {
+    PhaseScope ps(c, 5, s);
+    op_Sinv<TR>(c, RY, ldr, T, ldr, nb, s);
+    k_cheb_recover<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, T, ldr, X, ldx, d_lam + (size_t)nsteps * nb, Xo,
+                                                      ldo);
+    PAW_LAUNCH_CHECK("k_cheb_recover");
+  }
+  // keep host-side scalars alive until the async copies have been consumed
+  PAW_CUDA(cudaStreamSynchronize(s));
+}
+
+// ============================================================== reductions
+// partial[chunk][v] = sum_{rows in chunk} (A[i][v] + s_v B[i][v])^2 ; B may be null
+__global__ void k_colnorm_partial(int64_t rows, int ncols, const double *__restrict__ A, int lda,
+                                  const double *__restrict__ B, int ldb, const double *__restrict__ sc,
+                                  double *__restrict__ partial, int nchunk) {
+  __shared__ double red[8][33];
+  const int v = blockIdx.y * 32 + threadIdx.x;
+  const int64_t per = (rows + nchunk - 1) / nchunk;
+  const int64_t r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+  double acc = 0.0;
+  if (v < ncols)
+    for (int64_t i = r0 + threadIdx.y; i < r1; i += 8) {
+      double a = A[i * lda + v];
+      if (B) a += sc[v] * B[i * ldb + v];
+      acc += a * a;
+    }
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && v < ncols) {
+    double s = 0.0;
+    for (int g = 0; g < 8; ++g) s += red[g][threadIdx.x];
+    partial[(size_t)blockIdx.x * ncols + v] = s;
+  }
+}
+
+// partial[block] = sum over a slice of rows of sum_v A[i][v] * B[i][v]  (FP64 accumulation)
+template <typename T>
+__global__ void k_dot_total(int64_t rows, int ncols, const T *__restrict__ A, int lda, const T *__restrict__ B,
+                            int ldb, double *__restrict__ partial) {
+  __shared__ double red[256];
+  const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+  double acc = 0.0;
+  for (int64_t idx = threadIdx.x; idx < (r1 - r0) * ncols; idx += blockDim.x) {
+    const int64_t i = r0 + idx / ncols;
+    const int v = (int)(idx % ncols);
+    acc += (double)A[i * lda + v] * (double)B[i * ldb + v];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// dot products sum_i A[i][v] * B[i][v] per column, partial sums
+__global__ void k_coldot_partial(int64_t rows, int ncols, const double *__restrict__ A, int lda,
+                                 const double *__restrict__ B, int ldb, double *__restrict__ partial,
+                                 int nchunk) {
+  __shared__ double red[8][33];
+  const int v = blockIdx.y * 32 + threadIdx.x;
+  const int64_t per = (rows + nchunk - 1) / nchunk;
+  const int64_t r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+  double acc = 0.0;
+  if (v < ncols)
+    for (int64_t i = r0 + threadIdx.y; i < r1; i += 8) acc += A[i * lda + v] * B[i * ldb + v];
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && v < ncols) {
+    double s = 0.0;
+    for (int g = 0; g < 8; ++g) s += red[g][threadIdx.x];
+    partial[(size_t)blockIdx.x * ncols + v] = s;
+  }
+}
+
+__global__ void k_sum_partials(int nchunk, int ncols, const double *__restrict__ partial,
+                               double *__restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= ncols) return;
+  double s = 0.0;
+  for (int k = 0; k < nchunk; ++k) s += partial[(size_t)k * ncols + v];
+  out[v] = s;
+}
+
+static std::vector<double> column_reduce(paw_context *c, bool dot, const double *A, int lda, const double *B,
+                                         int ldb, const double *sc_dev, int ncols, cudaStream_t s) {
+  const int nchunk = 304;
+  c->ws_red.ensure(sizeof(double) * ((size_t)nchunk * ncols + ncols), &c->dev_bytes);
+  double *part = c->ws_red.as<double>();
+  double *out = part + (size_t)nchunk * ncols;
+  dim3 g(nchunk, (ncols + 31) / 32), blk(32, 8);
+  if (dot)
+    k_coldot_partial<<<g, blk, 0, s>>>(c->ndof, ncols, A, lda, B, ldb, part, nchunk);
+  else
+    k_colnorm_partial<<<g, blk, 0, s>>>(c->ndof, ncols, A, lda, B, ldb, sc_dev, part, nchunk);
+  PAW_LAUNCH_CHECK("k_col_partial");
+  k_sum_partials<<<(ncols + 127) / 128, 128, 0, s>>>(nchunk, ncols, part, out);
+  PAW_LAUNCH_CHECK("k_sum_partials");
+  std::vector<double> h(ncols);
+  PAW_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * ncols, cudaMemcpyDeviceToHost, s));
+  PAW_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, double b,
+                        const double *__restrict__ y, double g, const double *__restrict__ z,
+                        double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = a * x[i];
+  if (y) r += b * y[i];
+  if (z) r += g * z[i];
+  out[i] = r;
+}
+
+__global__ void k_random_vec(int64_t n, uint64_t seed, double *__restrict__ v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+// ============================================================== gradient kernels
+// dV[e][q] = wq[q] * sum_v (sum_I Nq[q][I] X[dof_e(I)][v])^2, one block per cell
+template <typename T>
+__global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__restrict__ cell_dofs,
+                                                const double *__restrict__ Nq, const double *__restrict__ wq,
+                                                const T *__restrict__ X, int ldx, int ncols,
+                                                double *__restrict__ dV) {
+  extern __shared__ double xs[];   // [nc][32]
+  const int e = blockIdx.x;
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) dV[(size_t)e * nq + q] = 0.0;
+  for (int v0 = 0; v0 < ncols; v0 += 32) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nc * 32; idx += blockDim.x) {
+      const int I = idx >> 5, v = idx & 31;
+      xs[idx] = (v0 + v < ncols) ? (double)X[(size_t)cell_dofs[(size_t)e * nc + I] * ldx + v0 + v] : 0.0;
+    }
+    __syncthreads();
+    for (int q = grp; q < nq; q += 8) {
+      double u = 0.0;
+      for (int I = 0; I < nc; ++I) u += Nq[(size_t)q * nc + I] * xs[I * 32 + lane];
+      double s = u * u;
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) dV[(size_t)e * nq + q] += wq[q] * s;
+    }
+  }
+}
+
+// dD[a][al][be] = sum_v U[a][al][v] U[a][be][v]
+template <typename T>
+__global__ void k_grad_D(int npj, const T *__restrict__ U, int ldu, int ncols, double *__restrict__ dD) {
+  const int a = blockIdx.x;
+  for (int o = threadIdx.x; o < npj * npj; o += blockDim.x) {
+    const int al = o / npj, be = o % npj;
+    double s = 0.0;
+    for (int v = 0; v < ncols; ++v)
+      s += (double)U[((size_t)a * npj + al) * ldu + v] * (double)U[((size_t)a * npj + be) * ldu + v];
+    dD[(size_t)a * npj * npj + o] = s;
+  }
+}
+
+}  // namespace pawfe
+
+using namespace pawfe;
+
+// ============================================================== C ABI
+#define PAW_TRY_BEGIN try {
+#define PAW_TRY_END                                                              \
+  }                                                                              \
+  catch (const ::pawfe::Error &err) {                                            \
+    return fail(err.code, err.msg);                                              \
+  }                                                                              \
+  catch (const std::bad_alloc &) {                                               \
+    return fail(PAW_ERR_NO_MEMORY, "host allocation failed");                    \
+  }                                                                              \
+  catch (const std::exception &ex) {                                             \
+    return fail(PAW_ERR_CUDA, ex.what());                                        \
+  }
+
+static void check_sym(const double *A, int na, int n, const char *what) {
+  for (int a = 0; a < na; ++a) {
+    const double *M = A + (size_t)a * n * n;
+    double mx = 0.0;
+    for (int i = 0; i < n * n; ++i) mx = std::max(mx, std::fabs(M[i]));
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) {
+        PAW_REQUIRE(std::isfinite(M[i * n + j]), PAW_ERR_NONFINITE, std::string(what) + " has NaN/Inf");
+        PAW_REQUIRE(std::fabs(M[i * n + j] - M[j * n + i]) <= 1e-12 * std::max(mx, 1e-300), PAW_ERR_INVALID_ARG,
+                    std::string(what) + " of atom " + std::to_string(a) + " is not symmetric");
+      }
+  }
+}
+
+extern "C" {
+
+const char *paw_last_error(void) { return g_last_error.c_str(); }
+const char *paw_version(void) { return "pawfe-gb300 0.1 (sm_103a)"; }
+
+paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atoms, const paw_projectors *proj,
+                         const double *D_ij, const double *dS_ij, const paw_vloc *vloc, const paw_options *opts,
+                         paw_handle *out) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(out != nullptr && mesh != nullptr, PAW_ERR_INVALID_ARG, "mesh and out must not be NULL");
+  *out = nullptr;
+  PAW_REQUIRE(mesh->periodic[0] == 1 && mesh->periodic[1] == 1 && mesh->periodic[2] == 1, PAW_ERR_UNSUPPORTED,
+              "only fully periodic boxes are supported");
+  PAW_REQUIRE(mesh->L[0] == mesh->L[1] && mesh->L[1] == mesh->L[2] && mesh->n_cells[0] == mesh->n_cells[1] &&
+                  mesh->n_cells[1] == mesh->n_cells[2],
+              PAW_ERR_UNSUPPORTED, "only cubic boxes with equal cell counts are supported");
+  PAW_REQUIRE(mesh->L[0] > 0 && mesh->n_cells[0] >= 1, PAW_ERR_INVALID_ARG, "box size and cell count must be positive");
+  PAW_REQUIRE(degree >= 1 && degree <= 8, PAW_ERR_UNSUPPORTED, "degree must be in 1..8");
+  const int natoms = atoms ? atoms->natoms : 0;
+  PAW_REQUIRE(natoms >= 0, PAW_ERR_INVALID_ARG, "natoms < 0");
+  PAW_REQUIRE(natoms == 0 || atoms->positions, PAW_ERR_INVALID_ARG, "positions NULL");
+  int npj = 0;
+  const int nsh = (natoms > 0 && proj) ? proj->nshells : 0;
+  PAW_REQUIRE(nsh >= 0 && nsh <= 16, PAW_ERR_UNSUPPORTED, "at most 16 projector shells");
+  for (int s = 0; s < nsh; ++s) {
+    PAW_REQUIRE(proj->l[s] >= 0 && proj->l[s] <= 2, PAW_ERR_UNSUPPORTED, "projector l must be 0, 1 or 2");
+    PAW_REQUIRE(proj->width[s] > 0, PAW_ERR_INVALID_ARG, "projector width must be positive");
+    PAW_REQUIRE(proj->width[s] * std::sqrt(2.0 * std::log(1e8)) < 0.5 * mesh->L[0], PAW_ERR_UNSUPPORTED,
+                "projector cutoff must be below half the box");
+    npj += 2 * proj->l[s] + 1;
+  }
+  PAW_REQUIRE(npj <= 32, PAW_ERR_UNSUPPORTED, "more than 32 projectors per atom");
+  if (natoms > 0 && npj > 0) {
+    PAW_REQUIRE(D_ij && dS_ij, PAW_ERR_INVALID_ARG, "D_ij and dS_ij must be given when atoms have projectors");
+    check_sym(D_ij, natoms, npj, "D_ij");
+    check_sym(dS_ij, natoms, npj, "dS_ij");
+  }
+  if (vloc) {
+    PAW_REQUIRE(vloc->ngauss >= 0, PAW_ERR_INVALID_ARG, "ngauss < 0");
+    for (int g = 0; g < vloc->ngauss; ++g)
+      PAW_REQUIRE(vloc->width[g] > 0, PAW_ERR_INVALID_ARG, "Gaussian width must be positive");
+  }
+  auto *c = new paw_context();
+  try {
+    c->n = mesh->n_cells[0];
+    c->p = degree;
+    c->np1 = degree + 1;
+    c->nc = c->np1 * c->np1 * c->np1;
+    c->nq1 = degree + 2;
+    c->nq = c->nq1 * c->nq1 * c->nq1;
+    c->N1 = c->n * degree;
+    c->ndof = (int64_t)c->N1 * c->N1 * c->N1;
+    c->ncells = c->n * c->n * c->n;
+    c->L = mesh->L[0];
+    c->h = c->L / c->n;
+    c->detJ = std::pow(c->h / 2.0, 3);
+    c->natoms = natoms;
+    c->npj = npj;
+    for (int s = 0; s < nsh; ++s) {
+      c->shell_l.push_back(proj->l[s]);
+      c->shell_w.push_back(proj->width[s]);
+    }
+    if (natoms > 0) c->pos.assign(atoms->positions, atoms->positions + 3 * natoms);
+    if (natoms > 0 && npj > 0) {
+      c->D.assign(D_ij, D_ij + (size_t)natoms * npj * npj);
+      c->dS.assign(dS_ij, dS_ij + (size_t)natoms * npj * npj);
+    }
+    if (vloc && vloc->ngauss > 0) {
+      c->vg_c.assign(vloc->centers, vloc->centers + 3 * vloc->ngauss);
+      c->vg_A.assign(vloc->depth, vloc->depth + vloc->ngauss);
+      c->vg_w.assign(vloc->width, vloc->width + vloc->ngauss);
+    }
+    if (opts) c->opts = *opts;
+    if (c->opts.block <= 0) c->opts.block = 256;
+    if (npj == 0) c->natoms = 0;   // atoms without projectors carry no nonlocal term
+    build_tables(c);
+    build_operators(c, vloc);
+    build_couplings(c);
+    if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) throw Error{PAW_ERR_LIBRARY, "cublasCreate failed"};
+    if (cusolverDnCreate(&c->cusolver) != CUSOLVER_STATUS_SUCCESS)
+      throw Error{PAW_ERR_LIBRARY, "cusolverDnCreate failed"};
+    PAW_CUDA(cudaDeviceSynchronize());
+  } catch (...) {
+    paw_destroy(c);
+    throw;
+  }
+  *out = c;
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_destroy(paw_handle c) {
+  if (!c) return PAW_OK;
+  cudaDeviceSynchronize();
+  DevBuf *bufs[] = {&c->cell_dofs, &c->md_inv64, &c->md_inv32, &c->He64, &c->He32, &c->Me64, &c->Me32,
+                    &c->K64, &c->Nq64, &c->wq64, &c->Vq, &c->tc_tf32.He, &c->tc_tf32.Me, &c->tc_bf16.He,
+                    &c->tc_bf16.Me, &c->ent_dof, &c->P64, &c->P32, &c->chunk_atom, &c->chunk_beg,
+                    &c->chunk_end, &c->atom_chunk_off, &c->node_dof, &c->node_off, &c->node_ent, &c->node_atom,
+                    &c->DH64, &c->DS64, &c->DSinv64, &c->ws_partial, &c->ws_W, &c->ws_W2, &c->ws_Y0, &c->ws_RX,
+                    &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
+                    &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
+                    &c->ws_rot};
+  for (DevBuf *b : bufs) b->release(&c->dev_bytes);
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+  if (c->cublas) cublasDestroy(c->cublas);
+  if (c->cusolver) cusolverDnDestroy(c->cusolver);
+  delete c;
+  return PAW_OK;
+}
+
+paw_status paw_get_info(paw_handle c, paw_info *out) {
+  if (!c || !out) return fail(PAW_ERR_INVALID_ARG, "NULL handle or output");
+  out->ndof = c->ndof;
+  out->ncells = c->ncells;
+  out->nodes_per_cell = c->nc;
+  out->quad_per_cell = c->nq;
+  out->natoms = c->natoms;
+  out->nproj = c->npj;
+  out->degree = c->p;
+  out->support_pairs = c->npairs;
+  out->device_bytes = c->dev_bytes;
+  return PAW_OK;
+}
+
+paw_status paw_set_veff(paw_handle c, const double *V_q) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c && V_q, PAW_ERR_INVALID_ARG, "NULL handle or V_q");
+  PAW_CUDA(cudaMemcpy(c->Vq.ptr, V_q, sizeof(double) * (size_t)c->ncells * c->nq, cudaMemcpyDeviceToDevice));
+  rebuild_hamiltonian(c);
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_set_dij(paw_handle c, const double *D_ij) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c && D_ij, PAW_ERR_INVALID_ARG, "NULL handle or D_ij");
+  if (c->natoms == 0) return PAW_OK;
+  check_sym(D_ij, c->natoms, c->npj, "D_ij");
+  c->D.assign(D_ij, D_ij + (size_t)c->natoms * c->npj * c->npj);
+  PAW_CUDA(cudaDeviceSynchronize());
+  PAW_CUDA(cudaMemcpy(c->DH64.ptr, c->D.data(), sizeof(double) * c->D.size(), cudaMemcpyHostToDevice));
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+static void check_block_args(paw_context *c, const void *X, const void *Y, int ncols, int ldx, int ldy) {
+  PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+  PAW_REQUIRE(ncols >= 0, PAW_ERR_INVALID_ARG, "ncols < 0");
+  if (ncols == 0) return;
+  PAW_REQUIRE(X && Y, PAW_ERR_INVALID_ARG, "NULL X or Y");
+  PAW_REQUIRE(ldx >= ncols && ldy >= ncols, PAW_ERR_INVALID_ARG, "leading dimension smaller than ncols");
+}
+
+static void check_prec(paw_precision prec) {
+  PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16, PAW_ERR_INVALID_ARG,
+              "unknown precision");
+}
+
+paw_status paw_apply_H(paw_handle c, paw_precision prec, const void *X, void *Y, int ncols, int ldx, int ldy,
+                       void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  check_block_args(c, X, Y, ncols, ldx, ldy);
+  if (ncols == 0) return PAW_OK;
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (prec == PAW_FP64)
+    op_H<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+  else
+    op_H<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_apply_S(paw_handle c, paw_precision prec, const void *X, void *Y, int ncols, int ldx, int ldy,
+                       void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  check_block_args(c, X, Y, ncols, ldx, ldy);
+  if (ncols == 0) return PAW_OK;
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (prec == PAW_FP64)
+    op_S<double>(c, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+  else
+    op_S<float>(c, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_apply_Sinv_approx(paw_handle c, paw_precision prec, const void *X, void *Y, int ncols, int ldx,
+                                 int ldy, void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  check_block_args(c, X, Y, ncols, ldx, ldy);
+  if (ncols == 0) return PAW_OK;
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (prec == PAW_FP64)
+    op_Sinv<double>(c, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+  else
+    op_Sinv<float>(c, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_cheb_filter(paw_handle c, paw_precision prec, const double *X_in, int ldx, const double *lambda_in,
+                           int ncols, int degree, paw_bounds b, double *X_out, int ldo, void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  check_block_args(c, X_in, X_out, ncols, ldx, ldo);
+  PAW_REQUIRE(degree >= 1, PAW_ERR_INVALID_ARG, "degree must be >= 1");
+  PAW_REQUIRE(std::isfinite(b.a0) && std::isfinite(b.bW) && std::isfinite(b.bU) && b.a0 < b.bW && b.bW < b.bU,
+              PAW_ERR_INVALID_ARG, "bounds must satisfy a0 < bW < bU");
+  if (ncols == 0) return PAW_OK;
+  PAW_REQUIRE(lambda_in != nullptr, PAW_ERR_INVALID_ARG, "lambda_in NULL");
+  PAW_REQUIRE(X_in != X_out, PAW_ERR_INVALID_ARG, "X_out must not alias X_in");
+  for (int j = 0; j < ncols; ++j)
+    PAW_REQUIRE(std::isfinite(lambda_in[j]), PAW_ERR_NONFINITE, "lambda_in has NaN/Inf");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int B = c->opts.block;
+  for (int j0 = 0; j0 < ncols; j0 += B) {
+    const int nb = std::min(B, ncols - j0);
+    if (prec == PAW_FP64)
+      cheb_block<double>(c, prec, X_in + j0, ldx, lambda_in + j0, nb, degree, b, X_out + j0, ldo, s);
+    else
+      cheb_block<float>(c, prec, X_in + j0, ldx, lambda_in + j0, nb, degree, b, X_out + j0, ldo, s);
+  }
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lambda_out, void *stream) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c && X && lambda_out, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
+  PAW_REQUIRE(c->ndof < (1ll << 31), PAW_ERR_UNSUPPORTED, "ndof >= 2^31");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int M = (int)c->ndof;
+  const int Bc = std::min(N, c->opts.block);
+  c->ws_HX.ensure(sizeof(double) * (size_t)M * Bc, &c->dev_bytes);
+  c->ws_Hp.ensure(sizeof(double) * (size_t)N * N, &c->dev_bytes);
+  c->ws_Sp.ensure(sizeof(double) * (size_t)N * N, &c->dev_bytes);
+  double *HX = c->ws_HX.as<double>(), *Hp = c->ws_Hp.as<double>(), *Sp = c->ws_Sp.as<double>();
+  cublasSetStream(c->cublas, s);
+  cusolverDnSetStream(c->cusolver, s);
+  const double one = 1.0, zero = 0.0;
+  for (int j0 = 0; j0 < N; j0 += Bc) {
+    const int nb = std::min(Bc, N - j0);
+    op_H<double>(c, PAW_FP64, X + j0, ld, HX, nb, nb, s);
+    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, N, nb, M, &one, X, ld, HX, nb, &zero, Hp + (size_t)j0 * N,
+                    N) != CUBLAS_STATUS_SUCCESS)
+      throw Error{PAW_ERR_LIBRARY, "cublasDgemm (H^p) failed"};
+    op_S<double>(c, X + j0, ld, HX, nb, nb, s);
+    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, N, nb, M, &one, X, ld, HX, nb, &zero, Sp + (size_t)j0 * N,
+                    N) != CUBLAS_STATUS_SUCCESS)
+      throw Error{PAW_ERR_LIBRARY, "cublasDgemm (S^p) failed"};
+  }
+  int lwork = 0;
+  c->ws_eig.ensure(sizeof(double) * N, &c->dev_bytes);
+  c->ws_info.ensure(sizeof(int), &c->dev_bytes);
+  if (cusolverDnDsygvd_bufferSize(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                  N, Hp, N, Sp, N, c->ws_eig.as<double>(), &lwork) != CUSOLVER_STATUS_SUCCESS)
+    throw Error{PAW_ERR_LIBRARY, "cusolverDnDsygvd_bufferSize failed"};
+  c->ws_solver.ensure(sizeof(double) * std::max(1, lwork), &c->dev_bytes);
+  if (cusolverDnDsygvd(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, Hp, N,
+                       Sp, N, c->ws_eig.as<double>(), c->ws_solver.as<double>(), lwork,
+                       c->ws_info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+    throw Error{PAW_ERR_LIBRARY, "cusolverDnDsygvd failed"};
+  int info = 0;
+  PAW_CUDA(cudaMemcpyAsync(&info, c->ws_info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PAW_CUDA(cudaStreamSynchronize(s));
+  PAW_REQUIRE(info <= N, PAW_ERR_NOT_SPD, "projected overlap S^p is not positive definite");
+  PAW_REQUIRE(info == 0, PAW_ERR_LIBRARY, "dsygvd did not converge");
+  // rotation X <- X Q in row chunks
+  const int rows = std::min(M, std::max(1024, (1 << 27) / N));   // temp <= 1 GiB
+  c->ws_rot.ensure(sizeof(double) * (size_t)rows * N, &c->dev_bytes);
+  double *tmp = c->ws_rot.as<double>();
+  for (int r0 = 0; r0 < M; r0 += rows) {
+    const int nr = std::min(rows, M - r0);
+    if (cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, N, nr, N, &one, Hp, N, X + (size_t)r0 * ld, ld, &zero, tmp,
+                    N) != CUBLAS_STATUS_SUCCESS)
+      throw Error{PAW_ERR_LIBRARY, "cublasDgemm (rotation) failed"};
+    PAW_CUDA(cudaMemcpy2DAsync(X + (size_t)r0 * ld, sizeof(double) * ld, tmp, sizeof(double) * N, sizeof(double) * N,
+                               nr, cudaMemcpyDeviceToDevice, s));
+  }
+  PAW_CUDA(cudaMemcpyAsync(lambda_out, c->ws_eig.ptr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  PAW_CUDA(cudaStreamSynchronize(s));
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_residuals(paw_handle c, const double *X, int ld, const double *lambda, int N, double *rnorm_out,
+                         void *stream) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c && X && lambda && rnorm_out, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int Bc = std::min(N, c->opts.block);
+  c->ws_HX.ensure(sizeof(double) * (size_t)c->ndof * Bc, &c->dev_bytes);
+  c->ws_SX.ensure(sizeof(double) * (size_t)c->ndof * Bc, &c->dev_bytes);
+  c->ws_colscale.ensure(sizeof(double) * Bc, &c->dev_bytes);
+  for (int j0 = 0; j0 < N; j0 += Bc) {
+    const int nb = std::min(Bc, N - j0);
+    std::vector<double> nl(nb);
+    for (int j = 0; j < nb; ++j) nl[j] = -lambda[j0 + j];
+    PAW_CUDA(cudaMemcpyAsync(c->ws_colscale.ptr, nl.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    op_H<double>(c, PAW_FP64, X + j0, ld, c->ws_HX.as<double>(), nb, nb, s);
+    op_S<double>(c, X + j0, ld, c->ws_SX.as<double>(), nb, nb, s);
+    std::vector<double> r = column_reduce(c, false, c->ws_HX.as<double>(), nb, c->ws_SX.as<double>(), nb,
+                                          c->ws_colscale.as<double>(), nb, s);
+    for (int j = 0; j < nb; ++j) rnorm_out[j0 + j] = std::sqrt(r[j]);
+  }
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_lanczos_bounds(paw_handle c, int k, uint64_t seed, double *theta_min, double *upper, void *stream) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c && theta_min && upper, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_REQUIRE(k >= 2 && k <= 200, PAW_ERR_INVALID_ARG, "k must be in 2..200");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int64_t M = c->ndof;
+  c->ws_vec.ensure(sizeof(double) * M * 5, &c->dev_bytes);
+  double *v = c->ws_vec.as<double>(), *vp = v + M, *w = v + 2 * M, *Hv = v + 3 * M, *Sw = v + 4 * M;
+  const unsigned g = (unsigned)((M + 255) / 256);
+  k_random_vec<<<g, 256, 0, s>>>(M, seed, v);
+  PAW_LAUNCH_CHECK("k_random_vec");
+  op_S<double>(c, v, 1, Sw, 1, 1, s);
+  double nrm = std::sqrt(column_reduce(c, true, v, 1, Sw, 1, nullptr, 1, s)[0]);
+  k_axpby<<<g, 256, 0, s>>>(M, 1.0 / nrm, v, 0.0, nullptr, 0.0, nullptr, v);
+  PAW_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * M, s));
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int j = 0; j < k; ++j) {
+    op_H<double>(c, PAW_FP64, v, 1, Hv, 1, 1, s);
+    op_Sinv<double>(c, Hv, 1, w, 1, 1, s);
+    op_S<double>(c, w, 1, Sw, 1, 1, s);
+    const double a = column_reduce(c, true, v, 1, Sw, 1, nullptr, 1, s)[0];
+    k_axpby<<<g, 256, 0, s>>>(M, 1.0, w, -a, v, -beta, vp, w);
+    op_S<double>(c, w, 1, Sw, 1, 1, s);
+    beta = std::sqrt(std::max(column_reduce(c, true, w, 1, Sw, 1, nullptr, 1, s)[0], 0.0));
+    al.push_back(a);
+    be.push_back(beta);
+    PAW_CUDA(cudaMemcpyAsync(vp, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    if (beta == 0.0) break;
+    k_axpby<<<g, 256, 0, s>>>(M, 1.0 / beta, w, 0.0, nullptr, 0.0, nullptr, v);
+  }
+  const int n = (int)al.size();
+  std::vector<double> T((size_t)n * n, 0.0), ev, V;
+  for (int i = 0; i < n; ++i) {
+    T[(size_t)i * n + i] = al[i];
+    if (i + 1 < n) T[(size_t)i * n + i + 1] = T[(size_t)(i + 1) * n + i] = be[i];
+  }
+  jacobi_eigh(n, T, ev, V);
+  *theta_min = ev[0];
+  *upper = ev[n - 1] + std::fabs(be[n - 1] * V[(size_t)(n - 1) * n + (n - 1)]);
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_energy(paw_handle c, paw_precision prec, const void *X, int ld, int N, double *E_out,
+                      void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  PAW_REQUIRE(c && X && E_out, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const size_t es = prec == PAW_FP64 ? sizeof(double) : sizeof(float);
+  c->ws_HX.ensure(es * (size_t)c->ndof * N, &c->dev_bytes);
+  const int nchunk = 304;
+  c->ws_red.ensure(sizeof(double) * (nchunk + 1), &c->dev_bytes);
+  double *part = c->ws_red.as<double>();
+  if (prec == PAW_FP64) {
+    op_H<double>(c, prec, (const double *)X, ld, c->ws_HX.as<double>(), N, N, s);
+    k_dot_total<double><<<nchunk, 256, 0, s>>>(c->ndof, N, (const double *)X, ld, c->ws_HX.as<double>(), N, part);
+  } else {
+    op_H<float>(c, prec, (const float *)X, ld, c->ws_HX.as<float>(), N, N, s);
+    k_dot_total<float><<<nchunk, 256, 0, s>>>(c->ndof, N, (const float *)X, ld, c->ws_HX.as<float>(), N, part);
+  }
+  PAW_LAUNCH_CHECK("k_dot_total");
+  k_sum_partials<<<1, 32, 0, s>>>(nchunk, 1, part, part + nchunk);
+  PAW_LAUNCH_CHECK("k_sum_partials");
+  PAW_CUDA(cudaMemcpyAsync(E_out, part + nchunk, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PAW_CUDA(cudaStreamSynchronize(s));
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int ld, int N, double *dE_dV,
+                           double *dE_dD, void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  PAW_REQUIRE(c && X && dE_dV, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const size_t shm = sizeof(double) * c->nc * 32;
+  if (prec == PAW_FP64) {
+    PAW_CUDA(cudaFuncSetAttribute(k_grad_V<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_grad_V<double><<<c->ncells, 256, shm, s>>>(c->nc, c->nq, c->cell_dofs.as<int>(), c->Nq64.as<double>(),
+                                                  c->wq64.as<double>(), (const double *)X, ld, N, dE_dV);
+  } else {
+    PAW_CUDA(cudaFuncSetAttribute(k_grad_V<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_grad_V<float><<<c->ncells, 256, shm, s>>>(c->nc, c->nq, c->cell_dofs.as<int>(), c->Nq64.as<double>(),
+                                                 c->wq64.as<double>(), (const float *)X, ld, N, dE_dV);
+  }
+  PAW_LAUNCH_CHECK("k_grad_V");
+  if (c->nent > 0 && dE_dD) {
+    if (prec == PAW_FP64) {
+      c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npj * N, &c->dev_bytes);
+      nl_project<double>(c, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
+      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->ws_W2.as<double>(), N, N, dE_dD);
+    } else {
+      c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npj * N, &c->dev_bytes);
+      nl_project<float>(c, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
+      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->ws_W2.as<float>(), N, N, dE_dD);
+    }
+    PAW_LAUNCH_CHECK("k_grad_D");
+  }
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_profile_enable(paw_handle c, int enable) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+  PAW_CUDA(cudaDeviceSynchronize());
+  c->prof.on = enable != 0;
+  c->prof.marks.clear();
+  c->prof.used = 0;
+  for (int i = 0; i < PAW_NPHASES; ++i) c->prof.launches[i] = 0;
+  c->prof.launch0 = g_launch_count;
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_profile_read(paw_handle c, paw_profile *out) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c && out, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_CUDA(cudaDeviceSynchronize());
+  std::memset(out, 0, sizeof(*out));
+  for (const auto &m : c->prof.marks) {
+    float ms = 0.f;
+    PAW_CUDA(cudaEventElapsedTime(&ms, m.a, m.b));
+    out->ms[m.phase] += ms;
+    out->intervals[m.phase] += 1;
+  }
+  for (int i = 0; i < PAW_NPHASES; ++i) out->launches[i] = c->prof.launches[i];
+  out->total_launches = g_launch_count - c->prof.launch0;
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_sync_status(paw_handle c) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+  PAW_CUDA(cudaStreamSynchronize(c->last_stream));
+  PAW_CUDA(cudaGetLastError());
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// Internal declarations shared by the translation units of libpawfe.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "paw_fe.h"
+
+namespace pawfe {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  paw_status code;
+  std::string msg;
+};
+
+void set_error(const std::string &msg);
+paw_status fail(paw_status code, const std::string &msg);
+
+#define PAW_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      throw ::pawfe::Error{e_ == cudaErrorMemoryAllocation ? PAW_ERR_NO_MEMORY \
+                                                           : PAW_ERR_CUDA,     \
+                           std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    }                                                                         \
+  } while (0)
+
+// every kernel launch is followed by PAW_LAUNCH_CHECK, which also counts it
+extern int64_t g_launch_count;
+
+#define PAW_LAUNCH_CHECK(what)                                                \
+  do {                                                                        \
+    ++::pawfe::g_launch_count;                                                \
+    cudaError_t e_ = cudaGetLastError();                                      \
+    if (e_ != cudaSuccess)                                                    \
+      throw ::pawfe::Error{PAW_ERR_CUDA,                                      \
+                           std::string("launch ") + (what) + ": " +           \
+                               cudaGetErrorString(e_)};                       \
+  } while (0)
+
+#define PAW_REQUIRE(cond, code, msg)                                          \
+  do {                                                                        \
+    if (!(cond)) throw ::pawfe::Error{(code), (msg)};                         \
+  } while (0)
+
+// ---------------------------------------------------------------- memory
+// Device buffer owned by a context.  Grows, never shrinks.
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t nbytes, int64_t *counter);
+  void release(int64_t *counter);
+  template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Per-precision cell-matrix storage used by the tensor-core kernels.
+struct TcMats {
+  DevBuf He;        // per-cell H^e, pre-tiled for the tcgen05 operand layout
+  DevBuf Me;        // shared mass matrix, same layout
+  int valid = 0;
+  int kchunks = 0;  // K-chunks of 128 bytes
+  int ntile = 0;    // rows of one N tile (multiple of 16)
+  int ntiles = 0;   // N tiles per cell
+  size_t chunk_bytes = 0;   // bytes of one (ntile x 128 B) chunk
+  size_t cell_bytes = 0;    // bytes of one cell (ntiles * kchunks chunks)
+};
+
+// Phase timing (paw_profile_enable / paw_profile_read)
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  int64_t launches[PAW_NPHASES] = {0};
+  int64_t launch0 = 0;
+};
+
+}  // namespace pawfe
+
+// ---------------------------------------------------------------- context
+struct paw_context {
+  // mesh and discretisation
+  int n = 0, p = 0, np1 = 0, nc = 0, nq1 = 0, nq = 0, N1 = 0, ncells = 0;
+  int64_t ndof = 0;
+  double L = 0, h = 0, detJ = 0;
+  int natoms = 0, npj = 0;
+  std::vector<int> shell_l;
+  std::vector<double> shell_w;
+  std::vector<double> pos, D, dS, G, Dsinv;   // host copies
+  std::vector<double> vg_c, vg_A, vg_w;       // local potential Gaussians
+  paw_options opts{};
+  int64_t dev_bytes = 0;
+
+  // host tables (built by the library's own FE code)
+  std::vector<double> K_ref, M_ref, Nq, wq;   // nc*nc, nc*nc, nq*nc, nq
+  std::vector<double> gq;                     // (p+2) Gauss nodes on [-1,1]
+
+  // device operator data
+  pawfe::DevBuf cell_dofs;   // int32 ncells*nc
+  pawfe::DevBuf md_inv64, md_inv32;           // 1 / M_D
+  pawfe::DevBuf He64, He32;                   // ncells*nc*nc
+  pawfe::DevBuf Me64, Me32, K64;              // nc*nc
+  pawfe::DevBuf Nq64, wq64;                   // nq*nc, nq
+  pawfe::DevBuf Vq;                           // ncells*nq
+  pawfe::TcMats tc_tf32, tc_bf16;
+
+  // projectors: atom-major support entries
+  int64_t nent = 0;                           // sum_a |supp_a| (node entries)
+  int64_t npairs = 0;                         // (cell, atom) support pairs
+  std::vector<int64_t> ent_off;               // natoms+1
+  pawfe::DevBuf ent_dof;                      // int32 nent
+  pawfe::DevBuf P64, P32;                     // nent * npj
+  // projection chunks (stage 1 of P^T X)
+  int nchunks = 0;
+  pawfe::DevBuf chunk_atom, chunk_beg, chunk_end;   // int32 nchunks
+  pawfe::DevBuf atom_chunk_off;                     // int32 natoms+1
+  // node-major view for P W (expansion)
+  int nnodes = 0;
+  pawfe::DevBuf node_dof, node_off, node_ent, node_atom;  // int32
+  // couplings (FP64, natoms*npj*npj)
+  pawfe::DevBuf DH64, DS64, DSinv64;
+
+  // workspaces
+  pawfe::DevBuf ws_partial, ws_W, ws_W2, ws_Y0, ws_RX, ws_RY, ws_T, ws_Y0f;
+  pawfe::DevBuf ws_lam, ws_colscale, ws_red, ws_vec;
+  pawfe::DevBuf ws_HX, ws_SX, ws_Hp, ws_Sp, ws_eig, ws_solver, ws_info, ws_rot;
+
+  cublasHandle_t cublas = nullptr;
+  cusolverDnHandle_t cusolver = nullptr;
+  cudaStream_t last_stream = nullptr;
+  pawfe::Profiler prof;
+};
+
+namespace pawfe {
+
+// ---------------------------------------------------------------- setup.cu
+void build_tables(paw_context *c);
+void build_operators(paw_context *c, const paw_vloc *vloc);
+void rebuild_hamiltonian(paw_context *c);
+void build_couplings(paw_context *c);
+
+// ---------------------------------------------------------------- ops.cu
+// Y += alpha * colscale[j] * (sum_e Q_e^T A_e Q_e X)  with A_e = mats + e*stride
+template <typename T>
+void cell_apply_simt(paw_context *c, const T *mats, long long stride, const T *X, int ldx,
+                     T *Y, int ldy, int ncols, double alpha, const double *colscale,
+                     cudaStream_t s);
+// W[a] = coup_scale * coup[a] * P^a^T (rowscale .* X)
+template <typename T>
+void nl_project(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale,
+                const double *coup, double coup_scale, T *W, cudaStream_t s);
+// Y[dof] += alpha * rowscale[dof] * colscale[j] * sum_a P^a W[a]
+template <typename T>
+void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, double alpha,
+               const T *rowscale, const double *colscale, cudaStream_t s);
+template <typename T>
+void zero_block(T *Y, int64_t rows, int ncols, int ld, cudaStream_t s);
+template <typename T>
+void scale_rows(const T *X, int ldx, T *Y, int ldy, int64_t rows, int ncols,
+                const T *rowscale, cudaStream_t s);
+
+// full operators into Y (overwrite); the element type is T
+template <typename T>
+void op_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy,
+          int ncols, cudaStream_t s);
+template <typename T>
+void op_S(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols,
+          cudaStream_t s);
+template <typename T>
+void op_Sinv(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols,
+             cudaStream_t s);
+
+// tensor-core cell products (cell_tc.cu)
+void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s);
+void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
+                   float *Y, int ldy, int ncols, float alpha, cudaStream_t s);
+
+// RAII bracket of one phase of the filter (records events only when enabled)
+struct PhaseScope {
+  paw_context *c;
+  int ph;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int64_t l0 = 0;
+  PhaseScope(paw_context *ctx, int phase, cudaStream_t st);
+  ~PhaseScope();
+};
+
+// small host linear algebra (setup.cu)
+void jacobi_eigh(int n, std::vector<double> &A, std::vector<double> &evals,
+                 std::vector<double> &evecs);
+bool invert_small(int n, std::vector<double> &A);
+
+}  // namespace pawfe

@@ -1,0 +1,50 @@
+"""Shared helpers for the GPU parity tests (CUDA path vs the FP64 oracle)."""
+import functools
+
+import numpy as np
+
+import inputs
+from tests.oracle_systems import mini_system, sym_random
+
+
+@functools.lru_cache(maxsize=None)
+def system(name):
+    if name == "tiny":
+        return inputs.make_system("tiny")
+    if name == "p6":
+        # degree-6 cells (343 nodes, like the mid workload) on a small box
+        rng = np.random.default_rng(21)
+        return mini_system(L=15.0, n=3, p=6, positions=[[2.2, 3.1, 4.4], [8.1, 7.7, 6.2], [5.0, 10.5, 1.2]],
+                           shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
+                           D=sym_random(rng, 3, 13, 0.1), dS=sym_random(rng, 3, 13, 0.02),
+                           vdepth=2.0, vwidth=1.0)
+    if name == "p5":
+        rng = np.random.default_rng(22)
+        return mini_system(L=10.0, n=3, p=5, positions=[[2.2, 3.1, 4.4], [7.1, 6.7, 6.2]],
+                           shells=[(0, 0.7), (1, 0.7), (2, 0.7)],
+                           D=sym_random(rng, 2, 9, 0.1), dS=sym_random(rng, 2, 9, 0.02),
+                           vdepth=2.0, vwidth=1.0)
+    raise KeyError(name)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_ops(name):
+    from oracle import ops as O
+    return O.PawOperators(system(name))
+
+
+def gpu_fe(name, **kw):
+    import paper_2604_26037_gb300 as P
+    return P.PawFE.from_system(system(name), **kw)
+
+
+def to_dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def rel_err(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
