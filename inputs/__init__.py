@@ -46,6 +46,11 @@ CONFIGS = {
                   shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
                   lattice=(8, 8, 4), jitter=0.3,
                   nvec=3000, block=512, degree=40, iters=1, nwanted=3000),
+    # small degree-6 case for profiler captures (same cell size and projector set as mid)
+    "small6": dict(index=5, L=20.0, ncell=8, p=6, natoms=8,
+                   shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
+                   lattice=(2, 2, 2), jitter=0.3,
+                   nvec=256, block=256, degree=4, iters=1, nwanted=256),
     "grad16": dict(index=4, L=40.0, ncell=16, p=4, natoms=64,
                    shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
                    lattice=(4, 4, 4), jitter=0.3,

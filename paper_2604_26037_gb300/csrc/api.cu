@@ -259,6 +259,8 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   }
   // keep host-side scalars alive until the async copies have been consumed
   PAW_CUDA(cudaStreamSynchronize(s));
+  if (prec == PAW_TF32 || prec == PAW_BF16)
+    PAW_REQUIRE(tc_read_status() == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
 }
 
 // ============================================================== reductions
@@ -915,6 +917,7 @@ paw_status paw_sync_status(paw_handle c) {
   PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
   PAW_CUDA(cudaStreamSynchronize(c->last_stream));
   PAW_CUDA(cudaGetLastError());
+  PAW_REQUIRE(tc_read_status() == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
   return PAW_OK;
   PAW_TRY_END
 }

@@ -1,14 +1,460 @@
-// Tensor-core (tcgen05) cell products -- placeholder until the kernel lands.
+// Cell products on the 5th-generation tensor cores (tcgen05) of sm_103a.
+//
+//   Y[dof_e(n)][v] += alpha * sum_k H^e[n][k] T[dof_e(k)][v]       (Sec. 4.3 steps i, iii, iv)
+//
+// One CTA computes D[v][n] = sum_k T_e[k][v] H^e[n][k] for one cell e, one tile
+// of output nodes n (MMA N) and 128 vectors v (MMA M):
+//   A operand  T_e^T  (M = 128 vectors x K nodes): gathered from the global
+//              DoF-major block by all threads (one vector row per thread,
+//              coalesced across the warp), written transposed into a K-major
+//              128-byte-swizzled shared-memory tile.
+//   B operand  H^e    (N nodes x K nodes, K-major): pre-arranged once in global
+//              memory in exactly the swizzled shared-memory image, copied with
+//              one cp.async.bulk per K-chunk (mbarrier transaction count).
+//   D          FP32 accumulators in tensor memory (128 lanes x N columns).
+// K advances in 128-byte chunks (32 TF32 or 64 BF16 nodes), double-buffered.
+// The epilogue reads TMEM with tcgen05.ld (lane = vector) and scatter-adds each
+// output node row with coalesced FP32 reductions: node rows of the DoF-major
+// block are contiguous in the vector index.
+//
+// Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the CTA
+// records a status word, skips its epilogue, frees its tensor memory and exits.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace pawfe {
 
-void tc_prepare(paw_context *, paw_precision, cudaStream_t) {
-  throw Error{PAW_ERR_UNSUPPORTED, "tensor-core cell kernels are not built yet"};
+__device__ int g_tc_status = 0;
+
+namespace {
+
+constexpr int MT = 128;            // vectors per CTA = MMA M
+constexpr int THREADS = 128;
+constexpr int STAGES = 2;
+constexpr uint32_t A_BYTES = MT * 128;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-void cell_apply_tc(paw_context *, paw_precision, const float *, int, float *, int, int, float, cudaStream_t) {
-  throw Error{PAW_ERR_UNSUPPORTED, "tensor-core cell kernels are not built yet"};
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on the given phase parity: false after WAIT_NS nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accum) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (SBO); LBO unused for this layout.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A and B both TF32 (kind::tf32) or
+// both BF16 (kind::f16), both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc(bool bf16, int M, int N) {
+  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+struct TcArgs {
+  const uint8_t *Ht;       // tiled cell matrices
+  size_t cell_bytes;       // bytes of one cell in Ht (0: shared matrix)
+  int nc, ntile, ntiles, kchunks, vtiles;
+  const int *cell_dofs;
+  const float *X;
+  int ldx;
+  float *Y;
+  int ldy, ncols;
+  float alpha;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
+  constexpr int EPR = BF16 ? 64 : 32;   // K elements per 128-byte row
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t B_BYTES = (uint32_t)a.ntile * 128u;
+  const uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);   // full[2], done[2], acc
+  uint32_t *taddr_smem = reinterpret_cast<uint32_t *>(bars + 5);
+  int *dofs = reinterpret_cast<int *>(taddr_smem + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bid = blockIdx.x;
+  const int vt = bid % a.vtiles;
+  const int t = (bid / a.vtiles) % a.ntiles;
+  const int e = bid / (a.vtiles * a.ntiles);
+  const int kpad = a.kchunks * EPR;
+
+  for (int i = tid; i < kpad; i += THREADS) dofs[i] = (i < a.nc) ? a.cell_dofs[(size_t)e * a.nc + i] : -1;
+  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]), accb = smem_u32(&bars[4]);
+  if (tid == 0) {
+    mbar_init(full0, THREADS + 1);
+    mbar_init(full0 + 8, THREADS + 1);
+    mbar_init(done0, 1);
+    mbar_init(done0 + 8, 1);
+    mbar_init(accb, 1);
+    fence_barrier_init();
+    fence_proxy_async();
+  }
+  if (warp == 0) {
+    __syncwarp();
+    tmem_alloc(smem_u32(taddr_smem), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *taddr_smem;
+
+  const int v = vt * MT + tid;            // gather row of this thread
+  const bool vok = v < a.ncols;
+  const uint8_t *Hsrc = a.Ht + (size_t)e * a.cell_bytes + (size_t)t * a.kchunks * B_BYTES;
+  const uint32_t idesc = make_idesc(BF16, MT, a.ntile);
+  bool ok = true;
+
+  for (int kc = 0; kc < a.kchunks; ++kc) {
+    const int s = kc & 1;
+    const uint32_t use = (uint32_t)(kc >> 1);
+    uint8_t *sA = base + s * STAGE_BYTES;
+    uint8_t *sB = sA + A_BYTES;
+    const uint32_t full = full0 + 8u * s, done = done0 + 8u * s;
+    if (kc >= STAGES && !mbar_wait(done, (use - 1) & 1u)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      mbar_arrive_tx(full, B_BYTES);
+      bulk_g2s(smem_u32(sB), Hsrc + (size_t)kc * B_BYTES, B_BYTES, full);
+    }
+    // gather: row tid of the A tile holds nodes kc*EPR .. +EPR-1 of vector v
+    uint8_t *row = sA + tid * 128;
+    const int k0 = kc * EPR;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      uint4 q;
+      if constexpr (BF16) {
+        float f[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int d = dofs[k0 + 8 * c + u];
+          f[u] = (vok && d >= 0) ? a.X[(size_t)d * a.ldx + v] : 0.f;
+        }
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(f[0], f[1]);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(f[2], f[3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(f[4], f[5]);
+        __nv_bfloat162 p3 = __floats2bfloat162_rn(f[6], f[7]);
+        q.x = *reinterpret_cast<uint32_t *>(&p0);
+        q.y = *reinterpret_cast<uint32_t *>(&p1);
+        q.z = *reinterpret_cast<uint32_t *>(&p2);
+        q.w = *reinterpret_cast<uint32_t *>(&p3);
+      } else {
+        float f[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int d = dofs[k0 + 4 * c + u];
+          f[u] = (vok && d >= 0) ? a.X[(size_t)d * a.ldx + v] : 0.f;
+        }
+        q.x = __float_as_uint(f[0]);
+        q.y = __float_as_uint(f[1]);
+        q.z = __float_as_uint(f[2]);
+        q.w = __float_as_uint(f[3]);
+      }
+      *reinterpret_cast<uint4 *>(row + ((c ^ (tid & 7)) << 4)) = q;
+    }
+    fence_proxy_async();
+    mbar_arrive(full);
+    if (tid == 0) {
+      if (!mbar_wait(full, use & 1u)) {
+        mbar_wait(full, use & 1u);   // second bounded wait: let the bulk copy in flight land
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t ad = sw128_desc(smem_u32(sA));
+      const uint64_t bd = sw128_desc(smem_u32(sB));
+#pragma unroll
+      for (int j = 0; j < 4; ++j)   // 4 MMAs of 32 bytes of K each
+        mma<BF16>(tmem, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc, (kc | j) != 0);
+      mma_commit(done);
+    }
+  }
+  if (tid == 0 && ok) mma_commit(accb);
+  if (!mbar_wait(accb, 0)) ok = false;
+  tc_fence_after();
+
+  if (ok) {
+    const int vout = vt * MT + warp * 32 + lane;
+    const bool wok = vout < a.ncols;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < a.ntile; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tl + (uint32_t)c0, r);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int nl = c0 + j;
+        const int n = t * a.ntile + nl;
+        if (wok && nl < a.ntile && n < a.nc)
+          atomicAdd(&a.Y[(size_t)dofs[n] * a.ldy + vout], a.alpha * __uint_as_float(r[j]));
+      }
+    }
+  } else if (lane == 0) {
+    atomicExch(&g_tc_status, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// H^e (FP32, row-major per cell) -> swizzled K-major tiles, TF32-rounded or BF16.
+template <bool BF16>
+__global__ void k_tile_mats(const float *__restrict__ He, long long stride, int ncells, int nc, int ntile,
+                            int ntiles, int kchunks, uint8_t *__restrict__ out) {
+  constexpr int EPR = BF16 ? 64 : 32;
+  const int64_t total = (int64_t)ncells * ntiles * kchunks * ntile * 8;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int c = (int)(idx & 7);
+  int64_t r1 = idx >> 3;
+  const int r = (int)(r1 % ntile);
+  r1 /= ntile;
+  const int kc = (int)(r1 % kchunks);
+  r1 /= kchunks;
+  const int t = (int)(r1 % ntiles);
+  const int e = (int)(r1 / ntiles);
+  const int n = t * ntile + r;
+  const float *H = He + (long long)e * stride;
+  uint4 q;
+  if constexpr (BF16) {
+    float f[8];
+    for (int u = 0; u < 8; ++u) {
+      const int k = kc * EPR + 8 * c + u;
+      f[u] = (n < nc && k < nc) ? H[(size_t)n * nc + k] : 0.f;
+    }
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(f[0], f[1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(f[2], f[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(f[4], f[5]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(f[6], f[7]);
+    q.x = *reinterpret_cast<uint32_t *>(&p0);
+    q.y = *reinterpret_cast<uint32_t *>(&p1);
+    q.z = *reinterpret_cast<uint32_t *>(&p2);
+    q.w = *reinterpret_cast<uint32_t *>(&p3);
+  } else {
+    uint32_t w[4];
+    for (int u = 0; u < 4; ++u) {
+      const int k = kc * EPR + 4 * c + u;
+      const float f = (n < nc && k < nc) ? H[(size_t)n * nc + k] : 0.f;
+      uint32_t o;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(o) : "f"(f));
+      w[u] = o;
+    }
+    q = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  const size_t chunk = (size_t)ntile * 128;
+  uint8_t *dst = out + ((((size_t)e * ntiles + t) * kchunks + kc) * chunk) + (size_t)r * 128 + ((c ^ (r & 7)) << 4);
+  *reinterpret_cast<uint4 *>(dst) = q;
+}
+
+}  // namespace
+
+static void tile_geometry(int nc, bool bf16, int &ntile, int &ntiles, int &kchunks) {
+  const int epr = bf16 ? 64 : 32;
+  ntiles = (nc + 255) / 256;
+  const int per = (nc + ntiles - 1) / ntiles;
+  ntile = ((per + 15) / 16) * 16;
+  kchunks = (nc + epr - 1) / epr;
+}
+
+void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s) {
+  const bool bf16 = prec == PAW_BF16;
+  TcMats &T = bf16 ? c->tc_bf16 : c->tc_tf32;
+  if (T.valid) return;
+  tile_geometry(c->nc, bf16, T.ntile, T.ntiles, T.kchunks);
+  T.chunk_bytes = (size_t)T.ntile * 128;
+  T.cell_bytes = T.chunk_bytes * T.kchunks * T.ntiles;
+  T.He.ensure(T.cell_bytes * c->ncells, &c->dev_bytes);
+  const int64_t total = (int64_t)c->ncells * T.ntiles * T.kchunks * T.ntile * 8;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  if (bf16)
+    k_tile_mats<true><<<grid, 256, 0, s>>>(c->He32.as<float>(), (long long)c->nc * c->nc, c->ncells, c->nc,
+                                           T.ntile, T.ntiles, T.kchunks, T.He.as<uint8_t>());
+  else
+    k_tile_mats<false><<<grid, 256, 0, s>>>(c->He32.as<float>(), (long long)c->nc * c->nc, c->ncells, c->nc,
+                                            T.ntile, T.ntiles, T.kchunks, T.He.as<uint8_t>());
+  PAW_LAUNCH_CHECK("k_tile_mats");
+  T.valid = 1;
+}
+
+size_t tc_smem_bytes(int ntile, int kchunks, bool bf16) {
+  const int epr = bf16 ? 64 : 32;
+  const size_t stage = A_BYTES + (size_t)ntile * 128;
+  size_t b = 1024 + STAGES * stage + 5 * 8 + 16 + sizeof(int) * (size_t)kchunks * epr;
+  // at most two CTAs per SM so that their tensor-memory allocations (2 x 256 columns) always fit
+  return b < 80 * 1024 ? 80 * 1024 : b;
+}
+
+void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, float *Y, int ldy, int ncols,
+                   float alpha, cudaStream_t s) {
+  if (ncols <= 0) return;
+  const bool bf16 = prec == PAW_BF16;
+  tc_prepare(c, prec, s);
+  TcMats &T = bf16 ? c->tc_bf16 : c->tc_tf32;
+  TcArgs a;
+  a.Ht = T.He.as<uint8_t>();
+  a.cell_bytes = T.cell_bytes;
+  a.nc = c->nc;
+  a.ntile = T.ntile;
+  a.ntiles = T.ntiles;
+  a.kchunks = T.kchunks;
+  a.vtiles = (ncols + MT - 1) / MT;
+  a.cell_dofs = c->cell_dofs.as<int>();
+  a.X = X;
+  a.ldx = ldx;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.ncols = ncols;
+  a.alpha = alpha;
+  const size_t shm = tc_smem_bytes(T.ntile, T.kchunks, bf16);
+  const int64_t blocks = (int64_t)c->ncells * T.ntiles * a.vtiles;
+  PAW_REQUIRE(blocks < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many cell tiles");
+  if (bf16) {
+    PAW_CUDA(cudaFuncSetAttribute(k_cell_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_cell_tc<true><<<(unsigned)blocks, THREADS, shm, s>>>(a);
+  } else {
+    PAW_CUDA(cudaFuncSetAttribute(k_cell_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_cell_tc<false><<<(unsigned)blocks, THREADS, shm, s>>>(a);
+  }
+  PAW_LAUNCH_CHECK("k_cell_tc");
+}
+
+int tc_read_status() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) return -1;
+  if (v) {
+    int z = 0;
+    cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int));
+  }
+  return v;
 }
 
 }  // namespace pawfe

@@ -185,6 +185,8 @@ void op_Sinv(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols,
 void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s);
 void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
                    float *Y, int ldy, int ncols, float alpha, cudaStream_t s);
+// 0: no bounded wait expired since the last read; 1: one did (cleared on read)
+int tc_read_status();
 
 // RAII bracket of one phase of the filter (records events only when enabled)
 struct PhaseScope {
