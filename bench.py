@@ -265,6 +265,10 @@ def run_ours(args, ws, rank, local):
     return res
 
 
+def fe_np1(nc):
+    return int(round(nc ** (1.0 / 3.0)))
+
+
 def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
     """Roofline of one phase of the filter, per launch, from algorithmic bytes/flops."""
     M, B = fe.ndof, cfg["block"]
@@ -275,9 +279,12 @@ def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
         flops = 2.0 * ncells * nc * nc * B
         mat_es = {"bf16": 2, "tf32": 4, "fp32": 4, "fp64": 8}[prec]
         byts = ncells * nc * nc * mat_es + M * B * es * 3        # H^e stream + gather + accumulate r/w
-    elif phase == "residual_Y":
-        flops = 2.0 * 2.0 * ncells * nc * nc * B                  # H^e and M^e products in FP64
-        byts = ncells * nc * nc * 8 + M * B * 8 * 3
+    elif phase == "residual_local":
+        # sum-factorised (1/2 K + V - lambda M) per cell and vector, FP64 (see sumfac.cu)
+        n1, q1 = fe_np1(nc), fe_np1(nc) + 1
+        fma_cell = 7 * n1 ** 4 + 2 * (q1 * n1 ** 3 + q1 * q1 * n1 ** 2 + q1 ** 3 * n1)
+        flops = 2.0 * fma_cell * ncells * B
+        byts = M * B * 8 * 3
         es = 8
     else:
         flops = None
@@ -290,10 +297,13 @@ def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
     tfs = flops / sec / 1e12
     hbm_frac = gbs / peaks["hbm"]
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    if prec in ("tf32", "bf16"):
+    if phase == "residual_local" or es == 8:
+        cpk = 1.25 * sm_mhz / 2070.0                              # FP64: 1.25 TFLOP/s at 2070 MHz
+        cunit, cbound = "TFLOP/s", "alu"
+    elif prec in ("tf32", "bf16"):
         cpk = peaks["bf16"] * (0.5 if prec == "tf32" else 1.0)   # TF32 dense = bf16 x 1.1/2.25 nominal
         cunit, cbound = "TFLOP/s", "tensor"
-    elif es == 8 or phase == "residual_Y":
+    elif es == 8 or phase == "residual_local":
         cpk = 1.25 * sm_mhz / 2070.0                              # FP64: 1.25 TFLOP/s at 2070 MHz
         cunit, cbound = "TFLOP/s", "alu"
     else:

@@ -225,9 +225,11 @@ paw_status paw_energy_grad(paw_handle h, paw_precision prec, const void *X, int 
  * enabled, every phase of Algorithm 2 is bracketed by CUDA events recorded on
  * the caller's stream; paw_profile_read synchronises and returns the summed
  * device time per phase and the number of kernels the library launched.
- * Phases: 0 Y = H X - S X Lambda (step 2), 1 recurrence update and M_D^-1
- * scaling, 2 nonlocal part of Shat^-1, 3 cell products H^e T_e with
- * extraction and assembly, 4 nonlocal part of H, 5 recovery (step 5). */
+ * Phases: 0 local part of Y = H X - S X Lambda (step 2, FP64 cell kernel),
+ * 1 recurrence update fused with T = Shat^-1 R_Y and the nonlocal part of
+ * alpha H T, 2 projector contraction P^T M_D^-1 R_Y and couplings, 3 cell
+ * products H^e T_e with extraction and assembly, 4 nonlocal part of
+ * Y = H X - S X Lambda, 5 recovery (step 5). */
 #define PAW_NPHASES 6
 typedef struct {
   double ms[PAW_NPHASES];

@@ -226,7 +226,7 @@ class PawFE:
     def sync_status(self):
         _check(self._lib.paw_sync_status(self._h))
 
-    PHASES = ("residual_Y", "recurrence", "sinv_nonlocal", "cell_products", "h_nonlocal", "recovery")
+    PHASES = ("residual_local", "recurrence", "projection", "cell_products", "residual_nonlocal", "recovery")
 
     def profile_enable(self, on=True):
         _check(self._lib.paw_profile_enable(self._h, int(bool(on))))

@@ -71,36 +71,56 @@ void DevBuf::release(int64_t *counter) {
 }
 
 // ============================================================== filter kernels
-// R_Y = (zeta_1/e) Y, R_X = 0 (Algorithm 2 step 3); optional FP32 copy of Y.
+// R_Y = (zeta_1/e) Y, R_X = 0 (Algorithm 2 step 3).  For the FP32 recurrence Y is
+// also split into two FP32 words hi + lo (lo omitted when Y is kept in FP32 only).
 template <typename TR>
 __global__ void k_cheb_init(int64_t rows, int ncols, const double *__restrict__ Y0, int ldy,
                             double s, TR *__restrict__ RY, TR *__restrict__ RX, int ldr,
-                            float *__restrict__ Y0f) {
+                            float *__restrict__ Yhi, float *__restrict__ Ylo) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
   const int v = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= rows || v >= ncols) return;
   const double y = Y0[i * ldy + v];
   RY[i * ldr + v] = (TR)(s * y);
   RX[i * ldr + v] = TR(0);
-  if (Y0f) Y0f[i * ldr + v] = (float)y;
+  if (Yhi) {
+    const float h = (float)y;
+    Yhi[i * ldr + v] = h;
+    if (Ylo) Ylo[i * ldr + v] = (float)(y - (double)h);
+  }
 }
 
-// Loop body of Algorithm 2 before the operator products:
-//   T   = M_D^-1 R_Y                                  (first factor of Shat^-1)
-//   R_X = [-beta R_Y - gamma R_X]_(TR) + alpha Y Lambda_Y   (FP64 add, TR store)
-// The H Shat^-1 R_Y term is accumulated into R_X afterwards.
-template <typename TR, typename TY>
+// Loop body of Algorithm 2 when no atom carries projectors:
+//   T = M_D^-1 R_Y,  R_X = [-beta R_Y - gamma R_X] + c_j Y,  c_j = alpha Lambda_Y[j]
+// (FP32: Y as hi/lo words, c_j as chi + clo, error-free product and sum).
+__device__ __forceinline__ float add_product_ef(float b, float ch, float cl, float yh, float yl) {
+  // explicit round-to-nearest operations: no contraction into FMA may alter the two-sum
+  const float th = __fmul_rn(ch, yh);
+  const float te = fmaf(ch, yh, -th);                    // exact error of ch * yh
+  const float tl = fmaf(ch, yl, fmaf(cl, yh, te));
+  const float s = __fadd_rn(b, th);                      // two-sum of b and th
+  const float bp = __fsub_rn(s, b);
+  const float err = __fadd_rn(__fsub_rn(b, __fsub_rn(s, bp)), __fsub_rn(th, bp));
+  return __fadd_rn(s, __fadd_rn(err, tl));
+}
+
+template <typename TR>
 __global__ void k_cheb_base(int64_t rows, int ncols, const TR *__restrict__ RY, TR *__restrict__ RX,
-                            TR *__restrict__ T, int ldr, const TY *__restrict__ Y0, int ldy,
-                            const double *__restrict__ lamY, double alpha, TR beta, TR gamma,
-                            const TR *__restrict__ mdinv) {
+                            TR *__restrict__ T, int ldr, const void *__restrict__ Y0, const float *__restrict__ Ylo,
+                            int ldy, const double *__restrict__ c64, const float *__restrict__ chi,
+                            const float *__restrict__ clo, TR beta, TR gamma, const TR *__restrict__ mdinv) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
   const int v = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= rows || v >= ncols) return;
   const TR ry = RY[i * ldr + v];
   const TR bracket = -beta * ry - gamma * RX[i * ldr + v];
-  const double full = (double)bracket + alpha * (double)Y0[i * ldy + v] * lamY[v];
-  RX[i * ldr + v] = (TR)full;
+  if constexpr (sizeof(TR) == 4) {
+    const float yh = static_cast<const float *>(Y0)[i * ldy + v];
+    const float yl = Ylo ? Ylo[i * ldy + v] : 0.f;
+    RX[i * ldr + v] = add_product_ef(bracket, chi[v], clo[v], yh, yl);
+  } else {
+    RX[i * ldr + v] = fma(c64[v], static_cast<const double *>(Y0)[i * ldy + v], bracket);
+  }
   T[i * ldr + v] = mdinv[i] * ry;
 }
 
@@ -123,16 +143,18 @@ static inline dim3 ew_grid(int64_t rows, int ncols) {
 static void residual_block(paw_context *c, const double *X, int ldx, const double *negLam_dev,
                            double *Y, int ldy, int ncols, cudaStream_t s) {
   zero_block<double>(Y, c->ndof, ncols, ldy, s);
-  cell_apply_simt<double>(c, c->He64.as<double>(), (long long)c->nc * c->nc, X, ldx, Y, ldy, ncols, 1.0,
-                          nullptr, s);
-  cell_apply_simt<double>(c, c->Me64.as<double>(), 0, X, ldx, Y, ldy, ncols, 1.0, negLam_dev, s);
-  if (c->nent > 0) {
-    c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npj * ncols, &c->dev_bytes);
+  // (1/2 K^e + V^e - lambda_j M^e) X_e in one sum-factorised pass
+  {
+    PhaseScope ps(c, 0, s);
+    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, 0.0, negLam_dev, s);
+  }
+  if (c->nown_pairs > 0) {
+    PhaseScope ps(c, 4, s);
+    // sum_a P^a (D_H^a - lambda_j dS^a) P^a^T x_j: one projection, one expansion
+    c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
     double *W = c->ws_W2.as<double>();
-    nl_project<double>(c, X, ldx, ncols, nullptr, c->DH64.as<double>(), 1.0, W, s);
-    nl_expand<double>(c, W, ncols, Y, ldy, 1.0, nullptr, nullptr, s);
-    nl_project<double>(c, X, ldx, ncols, nullptr, c->DS64.as<double>(), 1.0, W, s);
-    nl_expand<double>(c, W, ncols, Y, ldy, 1.0, nullptr, negLam_dev, s);
+    nl_project_residual<double>(c, X, ldx, ncols, negLam_dev, W, s);
+    nl_expand<double>(c, W, ncols, Y, ldy, nullptr, s);
   }
 }
 
@@ -153,9 +175,9 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   double zeta = e / (bd.a0 - cc);
   double zeta1 = zeta;
   const double gam = 2.0 / zeta1;
-  // scalar recurrences on the host (Algorithm 2 steps 1, 3, 4)
-  std::vector<double> LX(nb, 1.0), LY(nb), lam_hist;   // lam_hist: Lambda_Y per loop step, then final
-  std::vector<double> al_h, be_h, ga_h;
+  // scalar recurrences on the host (Algorithm 2 steps 1, 3, 4); cf[k][j] = alpha_k Lambda_Y[j]
+  std::vector<double> LX(nb, 1.0), LY(nb), cf;
+  std::vector<double> be_h, ga_h, al_h;
   for (int j = 0; j < nb; ++j) LY[j] = (zeta1 / e) * (lam[j] - cc);
   for (int th = 2; th <= m; ++th) {
     zeta1 = 1.0 / (gam - zeta);
@@ -163,7 +185,7 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
     al_h.push_back(alpha);
     be_h.push_back(beta);
     ga_h.push_back(gk);
-    lam_hist.insert(lam_hist.end(), LY.begin(), LY.end());
+    for (int j = 0; j < nb; ++j) cf.push_back(alpha * LY[j]);
     for (int j = 0; j < nb; ++j) {
       const double nx = alpha * LY[j] * lam[j] - beta * LY[j] - gk * LX[j];
       LX[j] = LY[j];
@@ -171,81 +193,84 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
     }
     zeta = zeta1;
   }
-  lam_hist.insert(lam_hist.end(), LY.begin(), LY.end());
-  std::vector<double> neglam(nb);
-  for (int j = 0; j < nb; ++j) neglam[j] = -lam[j];
   const int nsteps = m - 1;
-  c->ws_lam.ensure(sizeof(double) * (lam_hist.size() + nb), &c->dev_bytes);
-  double *d_lam = c->ws_lam.as<double>();
-  double *d_neglam = d_lam + lam_hist.size();
-  PAW_CUDA(cudaMemcpyAsync(d_lam, lam_hist.data(), sizeof(double) * lam_hist.size(), cudaMemcpyHostToDevice, s));
-  PAW_CUDA(cudaMemcpyAsync(d_neglam, neglam.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  // device scalars: [-Lambda (nb)][Lambda_Y final (nb)][cf (nsteps*nb)] and the FP32 split of cf
+  std::vector<double> hd(2 * (size_t)nb + cf.size());
+  for (int j = 0; j < nb; ++j) {
+    hd[j] = -lam[j];
+    hd[nb + j] = LY[j];
+  }
+  std::copy(cf.begin(), cf.end(), hd.begin() + 2 * nb);
+  std::vector<float> hf(2 * cf.size() + 2);
+  for (size_t i = 0; i < cf.size(); ++i) {
+    const float h = (float)cf[i];
+    hf[i] = h;
+    hf[cf.size() + i] = (float)(cf[i] - (double)h);
+  }
+  c->ws_lam.ensure(sizeof(double) * hd.size(), &c->dev_bytes);
+  c->ws_cf.ensure(sizeof(float) * hf.size(), &c->dev_bytes);
+  double *d_neglam = c->ws_lam.as<double>();
+  const double *d_lyfin = d_neglam + nb, *d_cf = d_neglam + 2 * nb;
+  const float *d_chi = c->ws_cf.as<float>(), *d_clo = d_chi + cf.size();
+  PAW_CUDA(cudaMemcpyAsync(d_neglam, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice, s));
+  PAW_CUDA(cudaMemcpyAsync(c->ws_cf.ptr, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, s));
 
   const int ldr = nb;
+  constexpr bool f32 = sizeof(TR) == 4;
   c->ws_Y0.ensure(sizeof(double) * M * nb, &c->dev_bytes);
   c->ws_RX.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
   c->ws_RY.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
   c->ws_T.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
-  const bool y0f = (sizeof(TR) == 4) && c->opts.y0_fp32;
-  if (y0f) c->ws_Y0f.ensure(sizeof(float) * M * nb, &c->dev_bytes);
+  const bool lo = f32 && !c->opts.y0_fp32;
+  if (f32) c->ws_Y0f.ensure(sizeof(float) * M * nb, &c->dev_bytes);
+  if (lo) c->ws_Y0lo.ensure(sizeof(float) * M * nb, &c->dev_bytes);
   double *Y0 = c->ws_Y0.as<double>();
+  float *Yhi = f32 ? c->ws_Y0f.as<float>() : nullptr;
+  float *Ylo = lo ? c->ws_Y0lo.as<float>() : nullptr;
   TR *RX = c->ws_RX.as<TR>(), *RY = c->ws_RY.as<TR>(), *T = c->ws_T.as<TR>();
-  const size_t wbytes = sizeof(TR) * (size_t)std::max(1, c->natoms * c->npj) * nb;
+  const size_t wbytes = sizeof(TR) * (size_t)std::max(1, c->natoms * c->npad) * nb;
   c->ws_W.ensure(wbytes, &c->dev_bytes);
-  TR *W = c->ws_W.as<TR>();
+  c->ws_W2.ensure(sizeof(double) * (size_t)std::max(1, c->natoms * c->npad) * nb, &c->dev_bytes);
 
-  // step 2: Y = H X - S X Lambda (FP64)
-  {
-    PhaseScope ps(c, 0, s);
-    residual_block(c, X, ldx, d_neglam, Y0, nb, nb, s);
-  }
+  // step 2: Y = H X - S X Lambda (FP64; phases 0 and 4)
+  residual_block(c, X, ldx, d_neglam, Y0, nb, nb, s);
+  TR *WS = c->ws_W.as<TR>(), *WH = c->ws_W2.as<TR>();
   // step 3
   const dim3 blk(32, 8);
   {
     PhaseScope ps(c, 1, s);
-    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, 1.0 / (bd.a0 - cc), RY, RX, ldr,
-                                                   y0f ? c->ws_Y0f.as<float>() : nullptr);
+    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, 1.0 / (bd.a0 - cc), RY, RX, ldr, Yhi, Ylo);
     PAW_LAUNCH_CHECK("k_cheb_init");
   }
   const TR *mdinv = mdinv_of<TR>(c);
-  // step 4
+  // step 4: R_X <- alpha H Shat^-1 R_Y - beta R_Y - gamma R_X + alpha Y Lambda_Y
   for (int k = 0; k < nsteps; ++k) {
     const double alpha = al_h[k];
-    {
+    const size_t ko = (size_t)k * nb;
+    if (c->nown_pairs > 0) {
+      // one projection gives the coefficients of Shat^-1 (W_S) and of the nonlocal H (W_H)
+      {
+        PhaseScope ps(c, 2, s);
+        nl_project_filter<TR>(c, RY, ldr, nb, mdinv, alpha, WS, WH, s);
+      }
+      // T = Shat^-1 R_Y and the recurrence update with the nonlocal part of alpha H T
       PhaseScope ps(c, 1, s);
-      if (y0f)
-        k_cheb_base<TR, float><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, RY, RX, T, ldr, c->ws_Y0f.as<float>(), ldr,
-                                                              d_lam + (size_t)k * nb, alpha, (TR)be_h[k],
-                                                              (TR)ga_h[k], mdinv);
+      if constexpr (f32)
+        nl_recurrence_f32(c, WS, WH, nb, RY, RX, T, ldr, mdinv, Yhi, Ylo, ldr, d_chi + ko, d_clo + ko, be_h[k],
+                          ga_h[k], s);
       else
-        k_cheb_base<TR, double><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, RY, RX, T, ldr, Y0, nb,
-                                                               d_lam + (size_t)k * nb, alpha, (TR)be_h[k],
-                                                               (TR)ga_h[k], mdinv);
+        nl_recurrence_f64(c, WS, WH, nb, RY, RX, T, ldr, mdinv, Y0, nb, d_cf + ko, be_h[k], ga_h[k], s);
+    } else {
+      PhaseScope ps(c, 1, s);
+      k_cheb_base<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, RY, RX, T, ldr, f32 ? (const void *)Yhi : (const void *)Y0,
+                                                     Ylo, nb, d_cf + ko, d_chi + ko, d_clo + ko, (TR)be_h[k],
+                                                     (TR)ga_h[k], mdinv);
       PAW_LAUNCH_CHECK("k_cheb_base");
     }
-    if (c->nent > 0) {   // T = Shat^-1 R_Y (Eq. Sinvapprox)
-      PhaseScope ps(c, 2, s);
-      nl_project<TR>(c, T, ldr, nb, nullptr, c->DSinv64.as<double>(), 1.0, W, s);
-      nl_expand<TR>(c, W, nb, T, ldr, -1.0, mdinv, nullptr, s);
-    }
-    // R_X += alpha H T  (local cell products, then nonlocal)
+    // R_X += alpha H_loc T (cell products with extraction and assembly)
     {
       PhaseScope ps(c, 3, s);
-      if constexpr (sizeof(TR) == 4) {
-        if (prec == PAW_TF32 || prec == PAW_BF16)
-          cell_apply_tc(c, prec, (const float *)T, ldr, (float *)RX, ldr, nb, (float)alpha, s);
-        else
-          cell_apply_simt<TR>(c, c->He32.as<TR>(), (long long)c->nc * c->nc, T, ldr, RX, ldr, nb, alpha,
-                              nullptr, s);
-      } else {
-        cell_apply_simt<TR>(c, c->He64.as<TR>(), (long long)c->nc * c->nc, T, ldr, RX, ldr, nb, alpha,
-                            nullptr, s);
-      }
-    }
-    if (c->nent > 0) {
-      PhaseScope ps(c, 4, s);
-      nl_project<TR>(c, T, ldr, nb, nullptr, c->DH64.as<double>(), alpha, W, s);
-      nl_expand<TR>(c, W, nb, RX, ldr, 1.0, nullptr, nullptr, s);
+      local_H<TR>(c, prec, T, ldr, RX, ldr, nb, alpha, s);
     }
     std::swap(RX, RY);
   }
@@ -253,8 +278,7 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   {
     PhaseScope ps(c, 5, s);
     op_Sinv<TR>(c, RY, ldr, T, ldr, nb, s);
-    k_cheb_recover<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, T, ldr, X, ldx, d_lam + (size_t)nsteps * nb, Xo,
-                                                      ldo);
+    k_cheb_recover<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, T, ldr, X, ldx, d_lyfin, Xo, ldo);
     PAW_LAUNCH_CHECK("k_cheb_recover");
   }
   // keep host-side scalars alive until the async copies have been consumed
@@ -410,13 +434,13 @@ __global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__res
 
 // dD[a][al][be] = sum_v U[a][al][v] U[a][be][v]
 template <typename T>
-__global__ void k_grad_D(int npj, const T *__restrict__ U, int ldu, int ncols, double *__restrict__ dD) {
+__global__ void k_grad_D(int npj, int npad, const T *__restrict__ U, int ldu, int ncols, double *__restrict__ dD) {
   const int a = blockIdx.x;
   for (int o = threadIdx.x; o < npj * npj; o += blockDim.x) {
     const int al = o / npj, be = o % npj;
     double s = 0.0;
     for (int v = 0; v < ncols; ++v)
-      s += (double)U[((size_t)a * npj + al) * ldu + v] * (double)U[((size_t)a * npj + be) * ldu + v];
+      s += (double)U[((size_t)a * npad + al) * ldu + v] * (double)U[((size_t)a * npad + be) * ldu + v];
     dD[(size_t)a * npj * npj + o] = s;
   }
 }
@@ -549,12 +573,13 @@ paw_status paw_destroy(paw_handle c) {
   cudaDeviceSynchronize();
   DevBuf *bufs[] = {&c->cell_dofs, &c->md_inv64, &c->md_inv32, &c->He64, &c->He32, &c->Me64, &c->Me32,
                     &c->K64, &c->Nq64, &c->wq64, &c->Vq, &c->tc_tf32.He, &c->tc_tf32.Me, &c->tc_bf16.He,
-                    &c->tc_bf16.Me, &c->ent_dof, &c->P64, &c->P32, &c->chunk_atom, &c->chunk_beg,
-                    &c->chunk_end, &c->atom_chunk_off, &c->node_dof, &c->node_off, &c->node_ent, &c->node_atom,
+                    &c->tc_bf16.Me, &c->ent_dof, &c->P64, &c->P32, &c->own_off, &c->own_atom, &c->ownP64,
+                    &c->ownP32,
                     &c->DH64, &c->DS64, &c->DSinv64, &c->ws_partial, &c->ws_W, &c->ws_W2, &c->ws_Y0, &c->ws_RX,
                     &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
-                    &c->ws_rot};
+                    &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
+                    &c->apair_off, &c->apair, &c->ws_pp};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   if (c->cublas) cublasDestroy(c->cublas);
@@ -866,15 +891,15 @@ paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int 
                                                  c->wq64.as<double>(), (const float *)X, ld, N, dE_dV);
   }
   PAW_LAUNCH_CHECK("k_grad_V");
-  if (c->nent > 0 && dE_dD) {
+  if (c->nown_pairs > 0 && dE_dD) {
     if (prec == PAW_FP64) {
-      c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npj * N, &c->dev_bytes);
+      c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
       nl_project<double>(c, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
-      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->ws_W2.as<double>(), N, N, dE_dD);
+      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N, dE_dD);
     } else {
-      c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npj * N, &c->dev_bytes);
+      c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
       nl_project<float>(c, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
-      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->ws_W2.as<float>(), N, N, dE_dD);
+      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N, dE_dD);
     }
     PAW_LAUNCH_CHECK("k_grad_D");
   }

@@ -30,7 +30,7 @@ __device__ int g_tc_status = 0;
 namespace {
 
 constexpr int MT = 128;            // vectors per CTA = MMA M
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;           // two gather threads per A row
 constexpr int STAGES = 2;
 constexpr uint32_t A_BYTES = MT * 128;
 constexpr uint32_t TMEM_COLS = 256;
@@ -188,6 +188,8 @@ struct TcArgs {
 template <bool BF16>
 __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
   constexpr int EPR = BF16 ? 64 : 32;   // K elements per 128-byte row
+  constexpr int GPT = EPR / 2;           // elements gathered per thread and K-chunk (half a row)
+  constexpr int EPC = EPR / 8;           // elements per 16-byte chunk
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t B_BYTES = (uint32_t)a.ntile * 128u;
@@ -224,11 +226,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
   tc_fence_after();
   const uint32_t tmem = *taddr_smem;
 
-  const int v = vt * MT + tid;            // gather row of this thread
+  // gather role: row r of the A tile (vector v), half `hf` of its 128 bytes
+  const int r = tid & (MT - 1), hf = tid >> 7;
+  const int v = vt * MT + r;
   const bool vok = v < a.ncols;
   const uint8_t *Hsrc = a.Ht + (size_t)e * a.cell_bytes + (size_t)t * a.kchunks * B_BYTES;
   const uint32_t idesc = make_idesc(BF16, MT, a.ntile);
   bool ok = true;
+
+  float cur[GPT], nxt[GPT];
+  auto load_chunk = [&](int kc, float(&f)[GPT]) {
+    const int k0 = kc * EPR + hf * GPT;
+#pragma unroll
+    for (int u = 0; u < GPT; ++u) {
+      const int d = dofs[k0 + u];
+      f[u] = (vok && d >= 0) ? __ldg(a.X + (size_t)d * a.ldx + v) : 0.f;
+    }
+  };
+  load_chunk(0, nxt);
 
   for (int kc = 0; kc < a.kchunks; ++kc) {
     const int s = kc & 1;
@@ -236,6 +251,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
     uint8_t *sA = base + s * STAGE_BYTES;
     uint8_t *sB = sA + A_BYTES;
     const uint32_t full = full0 + 8u * s, done = done0 + 8u * s;
+#pragma unroll
+    for (int u = 0; u < GPT; ++u) cur[u] = nxt[u];
+    if (kc + 1 < a.kchunks) load_chunk(kc + 1, nxt);   // in flight while this chunk is stored and multiplied
     if (kc >= STAGES && !mbar_wait(done, (use - 1) & 1u)) {
       ok = false;
       break;
@@ -244,40 +262,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
       mbar_arrive_tx(full, B_BYTES);
       bulk_g2s(smem_u32(sB), Hsrc + (size_t)kc * B_BYTES, B_BYTES, full);
     }
-    // gather: row tid of the A tile holds nodes kc*EPR .. +EPR-1 of vector v
-    uint8_t *row = sA + tid * 128;
-    const int k0 = kc * EPR;
+    uint8_t *row = sA + r * 128;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int cc = 0; cc < 4; ++cc) {
+      const int c = hf * 4 + cc;
       uint4 q;
       if constexpr (BF16) {
-        float f[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int d = dofs[k0 + 8 * c + u];
-          f[u] = (vok && d >= 0) ? a.X[(size_t)d * a.ldx + v] : 0.f;
-        }
-        __nv_bfloat162 p0 = __floats2bfloat162_rn(f[0], f[1]);
-        __nv_bfloat162 p1 = __floats2bfloat162_rn(f[2], f[3]);
-        __nv_bfloat162 p2 = __floats2bfloat162_rn(f[4], f[5]);
-        __nv_bfloat162 p3 = __floats2bfloat162_rn(f[6], f[7]);
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(cur[cc * EPC + 0], cur[cc * EPC + 1]);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(cur[cc * EPC + 2], cur[cc * EPC + 3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(cur[cc * EPC + 4], cur[cc * EPC + 5]);
+        __nv_bfloat162 p3 = __floats2bfloat162_rn(cur[cc * EPC + 6], cur[cc * EPC + 7]);
         q.x = *reinterpret_cast<uint32_t *>(&p0);
         q.y = *reinterpret_cast<uint32_t *>(&p1);
         q.z = *reinterpret_cast<uint32_t *>(&p2);
         q.w = *reinterpret_cast<uint32_t *>(&p3);
       } else {
-        float f[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int d = dofs[k0 + 4 * c + u];
-          f[u] = (vok && d >= 0) ? a.X[(size_t)d * a.ldx + v] : 0.f;
-        }
-        q.x = __float_as_uint(f[0]);
-        q.y = __float_as_uint(f[1]);
-        q.z = __float_as_uint(f[2]);
-        q.w = __float_as_uint(f[3]);
+        q = make_uint4(__float_as_uint(cur[cc * 4 + 0]), __float_as_uint(cur[cc * 4 + 1]),
+                       __float_as_uint(cur[cc * 4 + 2]), __float_as_uint(cur[cc * 4 + 3]));
       }
-      *reinterpret_cast<uint4 *>(row + ((c ^ (tid & 7)) << 4)) = q;
+      *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = q;
     }
     fence_proxy_async();
     mbar_arrive(full);
@@ -301,18 +304,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
   tc_fence_after();
 
   if (ok) {
-    const int vout = vt * MT + warp * 32 + lane;
+    // warp w reads TMEM lane quarter (w & 3) = vectors 32 (w & 3) .. +31; the two warp
+    // groups split the columns (output nodes) of the tile
+    const int q = warp & 3, ch = warp >> 2;
+    const int nch = (a.ntile + 31) / 32;
+    const int per = (nch + 1) / 2;
+    const int c_beg = ch * per * 32, c_end = min(a.ntile, (ch + 1) * per * 32);
+    const int vout = vt * MT + q * 32 + lane;
     const bool wok = vout < a.ncols;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < a.ntile; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tl + (uint32_t)c0, r);
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+    for (int c0 = c_beg; c0 < c_end; c0 += 32) {
+      uint32_t rr[32];
+      tmem_ld32(tl + (uint32_t)c0, rr);
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int nl = c0 + j;
         const int n = t * a.ntile + nl;
-        if (wok && nl < a.ntile && n < a.nc)
-          atomicAdd(&a.Y[(size_t)dofs[n] * a.ldy + vout], a.alpha * __uint_as_float(r[j]));
+        if (wok && nl < c_end && n < a.nc)
+          atomicAdd(&a.Y[(size_t)dofs[n] * a.ldy + vout], a.alpha * __uint_as_float(rr[j]));
       }
     }
   } else if (lane == 0) {

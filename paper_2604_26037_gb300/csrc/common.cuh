@@ -105,6 +105,7 @@ struct paw_context {
   // host tables (built by the library's own FE code)
   std::vector<double> K_ref, M_ref, Nq, wq;   // nc*nc, nc*nc, nq*nc, nq
   std::vector<double> gq;                     // (p+2) Gauss nodes on [-1,1]
+  std::vector<double> M1, D1, phiq;           // 1D mass, stiffness ((p+1) Gauss), Lagrange at (p+2) Gauss
 
   // device operator data
   pawfe::DevBuf cell_dofs;   // int32 ncells*nc
@@ -113,6 +114,8 @@ struct paw_context {
   pawfe::DevBuf Me64, Me32, K64;              // nc*nc
   pawfe::DevBuf Nq64, wq64;                   // nq*nc, nq
   pawfe::DevBuf Vq;                           // ncells*nq
+  pawfe::DevBuf wV;                           // ncells*nq: w_q detJ V_q (sum-factorised V^e)
+  int wV_valid = 0;
   pawfe::TcMats tc_tf32, tc_bf16;
 
   // projectors: atom-major support entries
@@ -121,19 +124,30 @@ struct paw_context {
   std::vector<int64_t> ent_off;               // natoms+1
   pawfe::DevBuf ent_dof;                      // int32 nent
   pawfe::DevBuf P64, P32;                     // nent * npj
-  // projection chunks (stage 1 of P^T X)
-  int nchunks = 0;
-  pawfe::DevBuf chunk_atom, chunk_beg, chunk_end;   // int32 nchunks
-  pawfe::DevBuf atom_chunk_off;                     // int32 natoms+1
-  // node-major view for P W (expansion)
-  int nnodes = 0;
-  pawfe::DevBuf node_dof, node_off, node_ent, node_atom;  // int32
+  // owner-cell view: every DoF is owned by exactly one cell (its local indices
+  // a, b, c < p); pair k = (cell, atom) lists the atoms whose P^a is nonzero on
+  // an owned node of the cell, with the assembled values P^a at those nodes.
+  int npad = 16;                              // npj rounded up to 16
+  int own = 0;                                // owned nodes per cell = p^3
+  int64_t nown_pairs = 0;
+  int max_own_pairs = 0;                      // largest pair count of one cell
+  pawfe::DevBuf own_off;                      // int32 ncells+1
+  pawfe::DevBuf own_atom;                     // int32 nown_pairs
+  pawfe::DevBuf ownP64, ownP32;               // nown_pairs * own * npad
+  pawfe::DevBuf apair_off, apair;             // atom-major list of the pairs (int32)
+  // atom-pair Gram blocks G_ab = P^a^T M_D^-1 P^b for atoms with common support
+  // nodes (CSR over atoms, a included); lets P^T Shat^-1 R follow from P^T M_D^-1 R
+  pawfe::DevBuf gnb_off, gnb_atom;            // int32 natoms+1, ngpairs
+  pawfe::DevBuf Gfull;                        // FP64 ngpairs * npad * npad
+  int64_t ngpairs = 0;
+  std::vector<double> mdinv_h;                // 1 / M_D on the host
   // couplings (FP64, natoms*npj*npj)
   pawfe::DevBuf DH64, DS64, DSinv64;
 
   // workspaces
-  pawfe::DevBuf ws_partial, ws_W, ws_W2, ws_Y0, ws_RX, ws_RY, ws_T, ws_Y0f;
+  pawfe::DevBuf ws_partial, ws_W, ws_W2, ws_Y0, ws_RX, ws_RY, ws_T, ws_Y0f, ws_Y0lo, ws_cf;
   pawfe::DevBuf ws_lam, ws_colscale, ws_red, ws_vec;
+  pawfe::DevBuf ws_pp;                        // per-pair projection partials
   pawfe::DevBuf ws_HX, ws_SX, ws_Hp, ws_Sp, ws_eig, ws_solver, ws_info, ws_rot;
 
   cublasHandle_t cublas = nullptr;
@@ -156,14 +170,46 @@ template <typename T>
 void cell_apply_simt(paw_context *c, const T *mats, long long stride, const T *X, int ldx,
                      T *Y, int ldy, int ncols, double alpha, const double *colscale,
                      cudaStream_t s);
-// W[a] = coup_scale * coup[a] * P^a^T (rowscale .* X)
+// W[a] = coup_scale * coup[a] * P^a^T (rowscale .* X); W is natoms x npad x ncols
 template <typename T>
 void nl_project(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale,
                 const double *coup, double coup_scale, T *W, cudaStream_t s);
-// Y[dof] += alpha * rowscale[dof] * colscale[j] * sum_a P^a W[a]
+// Y[dof] += colscale[j] * sum_a P^a W[a]   (owner-cell expansion, no atomics)
 template <typename T>
-void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, double alpha,
-               const T *rowscale, const double *colscale, cudaStream_t s);
+void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, const double *colscale,
+               cudaStream_t s);
+// Y = M_D^-1 (X - sum_a P^a W[a])
+template <typename T>
+void nl_sinv_out(paw_context *c, const T *W, int ncols, const T *X, int ldx, T *Y, int ldy,
+                 const T *mdinv, cudaStream_t s);
+// W[a] = (D_H[a] + cs[j] dS[a]) P^a^T X  (nonlocal part of H X - S X Lambda, cs = -Lambda)
+template <typename T>
+void nl_project_residual(paw_context *c, const T *X, int ldx, int ncols, const double *cs, T *W,
+                         cudaStream_t s);
+// One projection per filter step: U = P^T M_D^-1 R_Y, W_S = Dsinv U and
+// W_H = alpha D_H (U - G W_S) = alpha D_H P^T Shat^-1 R_Y (G: atom-pair Gram blocks)
+template <typename T>
+void nl_project_filter(paw_context *c, const T *RY, int ldr, int ncols, const T *mdinv, double alpha,
+                       T *WS, T *WH, cudaStream_t s);
+// T = M_D^-1 (R_Y - sum_a P^a W_S[a]);
+// R_X = [-beta R_Y - gamma R_X + sum_a P^a W_H[a]] + c_j Y   with c_j = alpha Lambda_Y[j]
+// FP32: Y given as hi/lo FP32 words (lo may be NULL), c_j as chi + clo, exact-product sum.
+void nl_recurrence_f32(paw_context *c, const float *WS, const float *WH, int ncols, const float *RY,
+                       float *RX, float *Tout, int ldr, const float *mdinv, const float *Y0hi,
+                       const float *Y0lo, int ldy0, const float *chi, const float *clo, double beta,
+                       double gamma, cudaStream_t s);
+void nl_recurrence_f64(paw_context *c, const double *WS, const double *WH, int ncols,
+                       const double *RY, double *RX, double *Tout, int ldr, const double *mdinv,
+                       const double *Y0, int ldy0, const double *c64, double beta, double gamma,
+                       cudaStream_t s);
+// FP64 sum-factorised local operator (sumfac.cu):
+// Y += alpha * (cK K^e + cV V^e + (cM + cMcol[j]) M^e) X, cell by cell with assembly
+void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
+              double cK, double cV, double cM, const double *cMcol, cudaStream_t s);
+// local part of H, accumulated with factor alpha
+template <typename T>
+void local_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols,
+             double alpha, cudaStream_t s);
 template <typename T>
 void zero_block(T *Y, int64_t rows, int ncols, int ld, cudaStream_t s);
 template <typename T>

@@ -1,0 +1,659 @@
+// Nonlocal PAW terms on the GPU (Eq. FE nonlocal contribution, Eqs. Sinvapprox
+// and Delta Sinv) in an owner-cell formulation.
+//
+// Every DoF is owned by exactly one cell (its local indices a, b, c < p).  A
+// block handles the p^3 owned nodes of one cell for a tile of vectors and the
+// (cell, atom) pairs k whose P^a is nonzero on those nodes (assembled values
+// P[k][o][al], padded to npad projectors):
+//   projection  U[a][al][v] += sum_o P[k][o][al] s(o) X[o][v]       (block-reduced, FP atomics)
+//   coupling    W[a] = C[a] U[a]                                    (small dense npj x npj)
+//   expansion   S[o][v]      = sum_k sum_al P[k][o][al] W[a_k][al][v] (no atomics: rows are owned)
+// so each owned row is read once per pass instead of once per atom whose
+// support contains it.  One filter step needs one projection: with
+// T = M_D^-1 (R - sum_b P^b W_S[b]) the coefficients of the nonlocal H term
+// follow from P^a^T T = U^a - sum_b G_ab W_S[b], G_ab = P^a^T M_D^-1 P^b.
+//
+// The recurrence expansion adds the term (2 zeta/e) Y Lambda_Y "in full
+// precision" without FP64 instructions: Y is split once per block into two
+// FP32 words (hi + lo) and the product and sum are formed with error-free
+// FP32 transformations (about 48 significant bits), then rounded once to FP32.
+#include "common.cuh"
+
+namespace pawfe {
+
+template <typename T>
+struct ProjCfg;
+template <>
+struct ProjCfg<float> {
+  static constexpr int VT = 64;
+};
+template <>
+struct ProjCfg<double> {
+  static constexpr int VT = 32;
+};
+template <typename T>
+struct ExpCfg;
+template <>
+struct ExpCfg<float> {
+  static constexpr int VT = 32;
+};
+template <>
+struct ExpCfg<double> {
+  static constexpr int VT = 16;
+};
+
+constexpr int OWN_MAX = 512;   // p <= 8
+
+// Offsets of the owned nodes of cell e relative to its first owned DoF.
+__device__ __forceinline__ int64_t owned_table(int e, int n, int p, int N1, int *ooff, int own) {
+  for (int o = threadIdx.x; o < own; o += blockDim.x) {
+    const int a = o % p, b = (o / p) % p, cc = o / (p * p);
+    ooff[o] = a + N1 * (b + N1 * cc);
+  }
+  const int cx = e % n, cy = (e / n) % n, cz = e / (n * n);
+  return (int64_t)cx * p + (int64_t)N1 * ((int64_t)cy * p + (int64_t)N1 * ((int64_t)cz * p));
+}
+
+// 4 consecutive elements, 16-byte aligned (one 16-byte access for float, two for double)
+__device__ __forceinline__ void ld4(const float *p, float (&r)[4]) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  r[0] = q.x;
+  r[1] = q.y;
+  r[2] = q.z;
+  r[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&r)[4]) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0];
+  const double2 b = reinterpret_cast<const double2 *>(p)[1];
+  r[0] = a.x;
+  r[1] = a.y;
+  r[2] = b.x;
+  r[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&r)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(r[0], r[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(r[2], r[3]);
+}
+
+// ------------------------------------------------------------------ projection
+// Thread tile 4 projectors x 4 vectors; the owned nodes are split over OG
+// thread groups whose partial sums are reduced through shared memory.
+template <typename T, int NPAD>
+__global__ void __launch_bounds__(256) k_own_project(int n, int p, int N1, const int *__restrict__ own_off,
+                                                     const int *__restrict__ own_atom, const T *__restrict__ oP,
+                                                     const T *__restrict__ X, int ldx, int ncols,
+                                                     const T *__restrict__ rowscale, int npj, T *__restrict__ U,
+                                                     int x_aligned) {
+  constexpr int VT = ProjCfg<T>::VT;
+  constexpr int TPG = (NPAD / 4) * (VT / 4);   // threads per node group
+  constexpr int OG = 256 / TPG;                // node groups
+  __shared__ int ooff[OWN_MAX];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int e = blockIdx.y, v0 = blockIdx.x * VT;   // vector tiles of one cell are adjacent: P reused from L2
+  const int k0 = own_off[e], k1 = own_off[e + 1];
+  if (k0 == k1) return;
+  const int own = p * p * p;
+  T *Xs = reinterpret_cast<T *>(sm_raw);          // [own][VT]
+  T *red = Xs + (size_t)own * VT;                 // [OG][NPAD][VT]
+  const int tid = threadIdx.x;
+  const int64_t base = owned_table(e, n, p, N1, ooff, own);
+  __syncthreads();
+  const bool vec = x_aligned != 0;   // base and row pitch of X 16-byte aligned (checked on the host)
+  for (int idx = tid; idx < own * (VT / 4); idx += 256) {
+    const int o = idx / (VT / 4), q = idx - o * (VT / 4);
+    const int64_t d = base + ooff[o];
+    const int v = v0 + 4 * q;
+    T x[4];
+    if (vec && v + 3 < ncols) {
+      ld4(X + d * ldx + v, x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = (v + j < ncols) ? X[d * ldx + v + j] : T(0);
+    }
+    if (rowscale) {
+      const T s = rowscale[d];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] *= s;
+    }
+    st4(Xs + (size_t)o * VT + 4 * q, x);
+  }
+  __syncthreads();
+  const int og = tid / TPG, r = tid - og * TPG;
+  const int aq = r / (VT / 4), vq = r - aq * (VT / 4);
+  for (int k = k0; k < k1; ++k) {
+    const T *Pk = oP + (size_t)k * own * NPAD + aq * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int o = og; o < own; o += OG) {
+      T pv[4], xv[4];
+      ld4(Pk + (size_t)o * NPAD, pv);
+      ld4(Xs + (size_t)o * VT + vq * 4, xv);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(pv[i], xv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) st4(red + ((size_t)og * NPAD + aq * 4 + i) * VT + vq * 4, acc[i]);
+    __syncthreads();
+    // per-pair partial sums: plain coalesced stores, reduced per atom by k_pair_reduce
+    for (int idx = tid; idx < NPAD * VT; idx += 256) {
+      const int al = idx / VT, v = idx - al * VT;
+      if (v0 + v < ncols) {
+        T sum = T(0);
+#pragma unroll
+        for (int g = 0; g < OG; ++g) sum += red[(size_t)g * NPAD * VT + idx];
+        U[((size_t)k * NPAD + al) * ncols + v0 + v] = sum;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// U[a][al][v] = sum over the pairs k of atom a (fixed order) of partial[k][al][v]
+// One warp per (atom, projector, 32 vectors); four interleaved partial sums keep
+// several loads in flight, combined in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(32) k_pair_reduce(const int *__restrict__ aoff, const int *__restrict__ apair,
+                                                    const T *__restrict__ partial, int npad, int ncols,
+                                                    T *__restrict__ U) {
+  const int v = blockIdx.x * 32 + threadIdx.x;
+  const int al = blockIdx.y, a = blockIdx.z;
+  if (v >= ncols) return;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  const int s0 = aoff[a], s1 = aoff[a + 1];
+  int s = s0;
+  for (; s + 3 < s1; s += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += partial[((size_t)apair[s + u] * npad + al) * ncols + v];
+  }
+  for (; s < s1; ++s) acc[0] += partial[((size_t)apair[s] * npad + al) * ncols + v];
+  U[((size_t)a * npad + al) * ncols + v] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// ------------------------------------------------------------------ coupling
+// W[a][al][v] = coup_scale * sum_be (C[a][al][be] + cs[v] C2[a][al][be]) U[a][be][v]
+// (C NULL: identity; C2, cs optional); rows al >= npj are zero.
+template <typename T, int NPAD>
+__global__ void k_own_couple(int npj, const T *__restrict__ U, const double *__restrict__ C,
+                             const double *__restrict__ C2, const double *__restrict__ cs, double coup_scale,
+                             T *__restrict__ W, int ncols) {
+  const int a = blockIdx.x;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (v >= ncols) return;
+  double u[NPAD];
+#pragma unroll
+  for (int be = 0; be < NPAD; ++be) u[be] = (be < npj) ? (double)U[((size_t)a * NPAD + be) * ncols + v] : 0.0;
+  const double *Ca = C ? C + (size_t)a * npj * npj : nullptr;
+  const double *C2a = C2 ? C2 + (size_t)a * npj * npj : nullptr;
+  const double sv = cs ? cs[v] : 0.0;
+  for (int al = 0; al < NPAD; ++al) {
+    double w = 0.0;
+    if (al < npj) {
+      if (Ca) {
+#pragma unroll
+        for (int be = 0; be < NPAD; ++be)
+          if (be < npj) w += (Ca[al * npj + be] + (C2a ? sv * C2a[al * npj + be] : 0.0)) * u[be];
+      } else {
+#pragma unroll
+        for (int be = 0; be < NPAD; ++be)
+          if (be == al) w = u[be];
+      }
+    }
+    W[((size_t)a * NPAD + al) * ncols + v] = (T)(coup_scale * w);
+  }
+}
+
+// W_H[a] = scale * D_H[a] (U[a] - sum_b G_ab W_S[b])  (= scale D_H P^a^T Shat^-1 R)
+template <typename T, int NPAD>
+__global__ void k_own_couple_h(int npj, const int *__restrict__ goff, const int *__restrict__ gatom,
+                               const double *__restrict__ G, const T *__restrict__ U, const T *__restrict__ WS,
+                               const double *__restrict__ DH, double scale, T *__restrict__ WH, int ncols) {
+  const int a = blockIdx.x;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (v >= ncols) return;
+  double u[NPAD];
+#pragma unroll
+  for (int be = 0; be < NPAD; ++be) u[be] = (be < npj) ? (double)U[((size_t)a * NPAD + be) * ncols + v] : 0.0;
+  for (int s = goff[a]; s < goff[a + 1]; ++s) {
+    const int b = gatom[s];
+    const double *Gs = G + (size_t)s * NPAD * NPAD;
+    double w[NPAD];
+#pragma unroll
+    for (int ga = 0; ga < NPAD; ++ga) w[ga] = (ga < npj) ? (double)WS[((size_t)b * NPAD + ga) * ncols + v] : 0.0;
+#pragma unroll
+    for (int be = 0; be < NPAD; ++be) {
+      double t = 0.0;
+#pragma unroll
+      for (int ga = 0; ga < NPAD; ++ga) t += Gs[be * NPAD + ga] * w[ga];
+      u[be] -= t;
+    }
+  }
+  const double *Da = DH + (size_t)a * npj * npj;
+  for (int al = 0; al < NPAD; ++al) {
+    double w = 0.0;
+    if (al < npj) {
+#pragma unroll
+      for (int be = 0; be < NPAD; ++be)
+        if (be < npj) w += Da[al * npj + be] * u[be];
+    }
+    WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * w);
+  }
+}
+
+// ------------------------------------------------------------------ expansion
+// fl32(b + c y) for c = ch + cl, y = yh + yl, with error-free FP32 steps.
+__device__ __forceinline__ float add_product_df(float b, float ch, float cl, float yh, float yl) {
+  // explicit round-to-nearest operations: no contraction into FMA may alter the two-sum
+  const float th = __fmul_rn(ch, yh);
+  const float te = fmaf(ch, yh, -th);                    // exact error of ch * yh
+  const float tl = fmaf(ch, yl, fmaf(cl, yh, te));
+  const float s = __fadd_rn(b, th);                      // two-sum of b and th
+  const float bp = __fsub_rn(s, b);
+  const float err = __fadd_rn(__fsub_rn(b, __fsub_rn(s, bp)), __fsub_rn(th, bp));
+  return __fadd_rn(s, __fadd_rn(err, tl));
+}
+
+constexpr int EXP_ADD = 0, EXP_SINV = 1, EXP_RECURRENCE = 2;
+
+struct ExpArgs {
+  int n, p, N1;
+  const int *own_off, *own_atom;
+  int ncols;
+  const double *cs;              // ADD: per-column factor (may be NULL)
+  const void *Xin;               // SINV: X; RECURRENCE: R_Y
+  int ldx;
+  void *Y;                       // ADD/SINV output; RECURRENCE: T
+  int ldy;
+  const void *mdinv;
+  void *RX;                      // RECURRENCE: R_X (ld = ldx)
+  const void *Y0, *Y0lo;         // RECURRENCE: Y (FP64) or its FP32 hi/lo split
+  int ldy0;
+  const double *c64;             // FP64 path: alpha * Lambda_Y per column
+  const float *chi, *clo;        // FP32 path: the same, split in two FP32 words
+  double beta, gamma;
+  int vec_ok;                    // every row pointer above 16-byte aligned (set by own_expand)
+};
+
+// Expansion with a fused output stage.  W of every pair of the cell is staged
+// in shared memory (at most 48 pairs); a thread owns 4 vectors of one node row
+// at a time.
+//   EXP_ADD        Y += cs[v] * S1
+//   EXP_SINV       Y  = md_inv * (X - S1)                                         (Eq. Sinvapprox)
+//   EXP_RECURRENCE T  = md_inv * (R_Y - S1)
+//                  R_X = [-beta R_Y - gamma R_X + S2] + alpha Y Lambda_Y   (S2: nonlocal part of alpha H T)
+// with S1 = sum_k P[k][o] . W1[a_k], S2 = sum_k P[k][o] . W2[a_k].
+template <typename T, int NPAD, int MODE>
+__global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__restrict__ oP, const T *__restrict__ W1,
+                                                    const T *__restrict__ W2) {
+  constexpr int VT = ExpCfg<T>::VT;
+  constexpr int G = VT / 4;               // groups of 4 vectors
+  constexpr int OR = 256 / G;             // node rows per pass
+  constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
+  __shared__ int ooff[OWN_MAX];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int e = blockIdx.y, v0 = blockIdx.x * VT;   // vector tiles of one cell are adjacent: P reused from L2
+  const int k0 = A.own_off[e], k1 = A.own_off[e + 1];
+  if (MODE == EXP_ADD && k0 == k1) return;
+  const int own = A.p * A.p * A.p;
+  const int np = k1 - k0;
+  const int ncols = A.ncols;
+  T *Ws = reinterpret_cast<T *>(sm_raw);   // [NW][np][NPAD][VT]
+  const int tid = threadIdx.x;
+  const int64_t base = owned_table(e, A.n, A.p, A.N1, ooff, own);
+  for (int idx = tid; idx < NW * np * (NPAD * VT / 4); idx += 256) {
+    const int q = idx % (VT / 4), rest = idx / (VT / 4), al = rest % NPAD, r2 = rest / NPAD, kk = r2 % np,
+              w = r2 / np;
+    const T *Wsrc = (w == 0) ? W1 : W2;
+    const int v = v0 + 4 * q;
+    const T *src = Wsrc + ((size_t)A.own_atom[k0 + kk] * NPAD + al) * ncols + v;
+    T x[4];
+    if (ncols % 4 == 0 && v + 3 < ncols) {
+      ld4(src, x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = (v + j < ncols) ? src[j] : T(0);
+    }
+    st4(Ws + (((size_t)w * np + kk) * NPAD + al) * VT + 4 * q, x);
+  }
+  __syncthreads();
+  const int g = tid % G, orow = tid / G;
+  const int v = v0 + g * 4;
+  const bool full4 = (v + 3 < ncols);
+  const T *Xin = static_cast<const T *>(A.Xin);
+  T *Y = static_cast<T *>(A.Y);
+  T *RX = static_cast<T *>(A.RX);
+  const T *mdinv = static_cast<const T *>(A.mdinv);
+  const bool vec = full4 && A.vec_ok;
+  // output stage of one node row o with its sums s1, s2 over the 4 vectors v .. v+3
+  auto emit = [&](int o, const T (&s1)[4], const T (&s2)[4]) {
+    const int64_t d = base + ooff[o];
+    if (MODE == EXP_ADD) {
+      T *yp = Y + d * A.ldy + v;
+      if (vec) {
+        T y[4];
+        ld4(yp, y);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] += (A.cs ? T(A.cs[v + j]) : T(1)) * s1[j];
+        st4(yp, y);
+      } else {
+        for (int j = 0; j < 4; ++j)
+          if (v + j < ncols) yp[j] += (A.cs ? T(A.cs[v + j]) : T(1)) * s1[j];
+      }
+    } else if (MODE == EXP_SINV) {
+      const T m = mdinv[d];
+      const T *xp = Xin + d * A.ldx + v;
+      T *yp = Y + d * A.ldy + v;
+      if (vec) {
+        T x[4], y[4];
+        ld4(xp, x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = m * (x[j] - s1[j]);
+        st4(yp, y);
+      } else {
+        for (int j = 0; j < 4; ++j)
+          if (v + j < ncols) yp[j] = m * (xp[j] - s1[j]);
+      }
+    } else {
+      const T m = mdinv[d];
+      const T *rp = Xin + d * A.ldx + v;
+      T *rxp = RX + d * A.ldx + v;
+      T *tp = Y + d * A.ldy + v;
+      T ry[4], rx[4], t[4], out[4];
+      if (vec) {
+        ld4(rp, ry);
+        ld4(rxp, rx);
+      } else {
+        for (int j = 0; j < 4; ++j) {
+          ry[j] = (v + j < ncols) ? rp[j] : T(0);
+          rx[j] = (v + j < ncols) ? rxp[j] : T(0);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        t[j] = m * (ry[j] - s1[j]);
+        const T bracket = -T(A.beta) * ry[j] - T(A.gamma) * rx[j] + s2[j];
+        const int vj = min(v + j, ncols - 1);
+        if constexpr (sizeof(T) == 4) {
+          const float *yh = static_cast<const float *>(A.Y0);
+          const float *yl = static_cast<const float *>(A.Y0lo);
+          const float yhv = yh[d * A.ldy0 + vj];
+          const float ylv = yl ? yl[d * A.ldy0 + vj] : 0.f;
+          out[j] = add_product_df(bracket, A.chi[vj], A.clo[vj], yhv, ylv);
+        } else {
+          const double *y0 = static_cast<const double *>(A.Y0);
+          out[j] = fma(A.c64[vj], y0[d * A.ldy0 + vj], bracket);
+        }
+      }
+      if (vec) {
+        st4(tp, t);
+        st4(rxp, out);
+      } else {
+        for (int j = 0; j < 4; ++j)
+          if (v + j < ncols) {
+            tp[j] = t[j];
+            rxp[j] = out[j];
+          }
+      }
+    }
+  };
+  // RB node rows per thread and pass: every W fragment read from shared memory
+  // feeds RB x 4 FMAs per sum
+  constexpr int RB = 4;
+  for (int o0 = orow; o0 < own; o0 += OR * RB) {
+    T s1[RB][4], s2[RB][4];
+    int orr[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      orr[r] = min(o0 + r * OR, own - 1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        s1[r][j] = T(0);
+        s2[r][j] = T(0);
+      }
+    }
+    for (int kk = 0; kk < np; ++kk) {
+      const T *Pb = oP + (size_t)(k0 + kk) * own * NPAD;
+      const T *W1k = Ws + (size_t)kk * NPAD * VT + g * 4;
+      const T *W2k = Ws + ((size_t)np + kk) * NPAD * VT + g * 4;
+#pragma unroll
+      for (int aq = 0; aq < NPAD / 4; ++aq) {
+        T pv[RB][4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) ld4(Pb + (size_t)orr[r] * NPAD + aq * 4, pv[r]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          T w1[4];
+          ld4(W1k + (aq * 4 + i) * VT, w1);
+#pragma unroll
+          for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s1[r][j] = fma(pv[r][i], w1[j], s1[r][j]);
+          if (NW == 2) {
+            T w2[4];
+            ld4(W2k + (aq * 4 + i) * VT, w2);
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) s2[r][j] = fma(pv[r][i], w2[j], s2[r][j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      if (o0 + r * OR < own) emit(o0 + r * OR, s1[r], s2[r]);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+// true when p (may be NULL) and the row pitch allow 16-byte vector access
+static bool aligned16(const void *p, size_t pitch_bytes) {
+  return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && (pitch_bytes % 16 == 0);
+}
+
+template <typename T>
+static const T *ownP(paw_context *c);
+template <>
+const double *ownP<double>(paw_context *c) { return c->ownP64.as<double>(); }
+template <>
+const float *ownP<float>(paw_context *c) { return c->ownP32.as<float>(); }
+
+template <typename T, int NPAD>
+static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, T *U, cudaStream_t s) {
+  constexpr int VT = ProjCfg<T>::VT;
+  constexpr int TPG = (NPAD / 4) * (VT / 4);
+  constexpr int OG = 256 / TPG;
+  const size_t shm = sizeof(T) * ((size_t)c->own * VT + (size_t)OG * NPAD * VT);
+  PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+              "projection tile exceeds shared memory (degree too high)");
+  PAW_CUDA(cudaFuncSetAttribute(k_own_project<T, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  dim3 g1((ncols + VT - 1) / VT, c->ncells);
+  const int xa = aligned16(X, ldx * sizeof(T)) ? 1 : 0;
+  k_own_project<T, NPAD><<<g1, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_atom.as<int>(),
+                                              ownP<T>(c), X, ldx, ncols, rowscale, c->npj, U, xa);
+  PAW_LAUNCH_CHECK("k_own_project");
+}
+
+// U = P^T (rowscale .* X) into c->ws_partial (natoms x npad x ncols): per-pair
+// partials, then a fixed-order sum per atom (deterministic, no atomics)
+template <typename T>
+static T *project_U(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, cudaStream_t s) {
+  const size_t ub = sizeof(T) * (size_t)c->natoms * c->npad * ncols;
+  c->ws_partial.ensure(ub, &c->dev_bytes);
+  c->ws_pp.ensure(sizeof(T) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
+  T *U = c->ws_partial.as<T>(), *PP = c->ws_pp.as<T>();
+  if (c->npad == 16)
+    project_impl<T, 16>(c, X, ldx, ncols, rowscale, PP, s);
+  else
+    project_impl<T, 32>(c, X, ldx, ncols, rowscale, PP, s);
+  dim3 g((ncols + 31) / 32, c->npad, c->natoms);
+  k_pair_reduce<T><<<g, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
+  PAW_LAUNCH_CHECK("k_pair_reduce");
+  return U;
+}
+
+template <typename T>
+static void couple(paw_context *c, const T *U, const double *C, const double *C2, const double *cs,
+                   double scale, T *W, int ncols, cudaStream_t s) {
+  dim3 g2(c->natoms, (ncols + 63) / 64);
+  if (c->npad == 16)
+    k_own_couple<T, 16><<<g2, 64, 0, s>>>(c->npj, U, C, C2, cs, scale, W, ncols);
+  else
+    k_own_couple<T, 32><<<g2, 64, 0, s>>>(c->npj, U, C, C2, cs, scale, W, ncols);
+  PAW_LAUNCH_CHECK("k_own_couple");
+}
+
+template <typename T>
+void nl_project(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, const double *coup,
+                double coup_scale, T *W, cudaStream_t s) {
+  if (c->nown_pairs == 0 || ncols <= 0) return;
+  const T *U = project_U<T>(c, X, ldx, ncols, rowscale, s);
+  couple<T>(c, U, coup, nullptr, nullptr, coup_scale, W, ncols, s);
+}
+
+template <typename T>
+void nl_project_residual(paw_context *c, const T *X, int ldx, int ncols, const double *cs, T *W, cudaStream_t s) {
+  if (c->nown_pairs == 0 || ncols <= 0) return;
+  const T *U = project_U<T>(c, X, ldx, ncols, nullptr, s);
+  couple<T>(c, U, c->DH64.as<double>(), c->DS64.as<double>(), cs, 1.0, W, ncols, s);
+}
+
+template <typename T>
+void nl_project_filter(paw_context *c, const T *RY, int ldr, int ncols, const T *mdinv, double alpha, T *WS, T *WH,
+                       cudaStream_t s) {
+  if (c->nown_pairs == 0 || ncols <= 0) return;
+  const T *U = project_U<T>(c, RY, ldr, ncols, mdinv, s);
+  couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, WS, ncols, s);
+  dim3 g2(c->natoms, (ncols + 63) / 64);
+  if (c->npad == 16)
+    k_own_couple_h<T, 16><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(),
+                                             c->Gfull.as<double>(), U, WS, c->DH64.as<double>(), alpha, WH, ncols);
+  else
+    k_own_couple_h<T, 32><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(),
+                                             c->Gfull.as<double>(), U, WS, c->DH64.as<double>(), alpha, WH, ncols);
+  PAW_LAUNCH_CHECK("k_own_couple_h");
+}
+
+template <typename T, int MODE>
+static void own_expand(paw_context *c, ExpArgs A, const T *W1, const T *W2, cudaStream_t s) {
+  constexpr int VT = ExpCfg<T>::VT;
+  const size_t y0e = (sizeof(T) == 4) ? sizeof(float) : sizeof(double);
+  A.vec_ok = aligned16(A.Y, A.ldy * sizeof(T)) && aligned16(A.Xin, A.ldx * sizeof(T)) &&
+             aligned16(A.RX, A.ldx * sizeof(T)) && aligned16(A.Y0, A.ldy0 * y0e) &&
+             aligned16(A.Y0lo, A.ldy0 * sizeof(float));
+  constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
+  const size_t shm = sizeof(T) * (size_t)NW * std::max(1, c->max_own_pairs) * c->npad * VT;
+  PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+              "too many atoms on one cell for the expansion kernel");
+  dim3 g((A.ncols + VT - 1) / VT, c->ncells);
+  if (c->npad == 16) {
+    auto kern = k_own_expand<T, 16, MODE>;
+    PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
+  } else {
+    auto kern = k_own_expand<T, 32, MODE>;
+    PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
+  }
+  PAW_LAUNCH_CHECK("k_own_expand");
+}
+
+static ExpArgs exp_args(paw_context *c, int ncols) {
+  ExpArgs A{};
+  A.n = c->n;
+  A.p = c->p;
+  A.N1 = c->N1;
+  A.own_off = c->own_off.as<int>();
+  A.own_atom = c->own_atom.as<int>();
+  A.ncols = ncols;
+  return A;
+}
+
+template <typename T>
+void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, const double *colscale, cudaStream_t s) {
+  if (c->nown_pairs == 0 || ncols <= 0) return;
+  ExpArgs A = exp_args(c, ncols);
+  A.Y = Y;
+  A.ldy = ldy;
+  A.ldx = ldy;
+  A.ldy0 = 4;
+  A.cs = colscale;
+  own_expand<T, EXP_ADD>(c, A, W, nullptr, s);
+}
+
+template <typename T>
+void nl_sinv_out(paw_context *c, const T *W, int ncols, const T *X, int ldx, T *Y, int ldy, const T *mdinv,
+                 cudaStream_t s) {
+  ExpArgs A = exp_args(c, ncols);
+  A.Xin = X;
+  A.ldx = ldx;
+  A.Y = Y;
+  A.ldy = ldy;
+  A.ldy0 = 4;
+  A.mdinv = mdinv;
+  own_expand<T, EXP_SINV>(c, A, W, nullptr, s);
+}
+
+void nl_recurrence_f32(paw_context *c, const float *WS, const float *WH, int ncols, const float *RY, float *RX,
+                       float *Tout, int ldr, const float *mdinv, const float *Y0hi, const float *Y0lo, int ldy0,
+                       const float *chi, const float *clo, double beta, double gamma, cudaStream_t s) {
+  ExpArgs A = exp_args(c, ncols);
+  A.Xin = RY;
+  A.ldx = ldr;
+  A.Y = Tout;
+  A.ldy = ldr;
+  A.mdinv = mdinv;
+  A.RX = RX;
+  A.Y0 = Y0hi;
+  A.Y0lo = Y0lo;
+  A.ldy0 = ldy0;
+  A.chi = chi;
+  A.clo = clo;
+  A.beta = beta;
+  A.gamma = gamma;
+  own_expand<float, EXP_RECURRENCE>(c, A, WS, WH, s);
+}
+
+void nl_recurrence_f64(paw_context *c, const double *WS, const double *WH, int ncols, const double *RY, double *RX,
+                       double *Tout, int ldr, const double *mdinv, const double *Y0, int ldy0, const double *c64,
+                       double beta, double gamma, cudaStream_t s) {
+  ExpArgs A = exp_args(c, ncols);
+  A.Xin = RY;
+  A.ldx = ldr;
+  A.Y = Tout;
+  A.ldy = ldr;
+  A.mdinv = mdinv;
+  A.RX = RX;
+  A.Y0 = Y0;
+  A.ldy0 = ldy0;
+  A.c64 = c64;
+  A.beta = beta;
+  A.gamma = gamma;
+  own_expand<double, EXP_RECURRENCE>(c, A, WS, WH, s);
+}
+
+template void nl_project<double>(paw_context *, const double *, int, int, const double *, const double *,
+                                 double, double *, cudaStream_t);
+template void nl_project<float>(paw_context *, const float *, int, int, const float *, const double *,
+                                double, float *, cudaStream_t);
+template void nl_project_residual<double>(paw_context *, const double *, int, int, const double *, double *,
+                                          cudaStream_t);
+template void nl_project_filter<double>(paw_context *, const double *, int, int, const double *, double, double *,
+                                        double *, cudaStream_t);
+template void nl_project_filter<float>(paw_context *, const float *, int, int, const float *, double, float *,
+                                       float *, cudaStream_t);
+template void nl_expand<double>(paw_context *, const double *, int, double *, int, const double *, cudaStream_t);
+template void nl_expand<float>(paw_context *, const float *, int, float *, int, const double *, cudaStream_t);
+template void nl_sinv_out<double>(paw_context *, const double *, int, const double *, int, double *, int,
+                                  const double *, cudaStream_t);
+template void nl_sinv_out<float>(paw_context *, const float *, int, const float *, int, float *, int,
+                                 const float *, cudaStream_t);
+
+}  // namespace pawfe

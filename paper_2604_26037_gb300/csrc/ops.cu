@@ -119,148 +119,6 @@ template void cell_apply_simt<double>(paw_context *, const double *, long long, 
 template void cell_apply_simt<float>(paw_context *, const float *, long long, const float *, int,
                                      float *, int, int, double, const double *, cudaStream_t);
 
-// ============================================================== projector kernels
-constexpr int MAXPJ = 32;
-constexpr int PVT = 32;   // vectors per block (one warp wide)
-constexpr int PRG = 4;    // entry groups per block
-
-// Stage 1: partial[chunk][al][v] = sum_{s in chunk} P[s][al] * rowscale[dof_s] * X[dof_s][v]
-template <typename T>
-__global__ void __launch_bounds__(PVT *PRG) k_nl_partial(
-    const int *__restrict__ ch_beg, const int *__restrict__ ch_end, const int *__restrict__ ent_dof,
-    const T *__restrict__ P, int npj, const T *__restrict__ X, int ldx, int ncols,
-    const T *__restrict__ rowscale, T *__restrict__ partial, int ldp) {
-  __shared__ T red[PRG][MAXPJ][PVT];
-  const int ch = blockIdx.x;
-  const int v = blockIdx.y * PVT + threadIdx.x;
-  const int b = ch_beg[ch], en = ch_end[ch];
-  T acc[MAXPJ];
-#pragma unroll
-  for (int al = 0; al < MAXPJ; ++al) acc[al] = T(0);
-  if (v < ncols) {
-    for (int s = b + threadIdx.y; s < en; s += PRG) {
-      const int d = ent_dof[s];
-      T x = X[(size_t)d * ldx + v];
-      if (rowscale) x *= rowscale[d];
-      const T *Ps = P + (size_t)s * npj;
-#pragma unroll
-      for (int al = 0; al < MAXPJ; ++al)
-        if (al < npj) acc[al] = fma(Ps[al], x, acc[al]);
-    }
-  }
-#pragma unroll
-  for (int al = 0; al < MAXPJ; ++al)
-    if (al < npj) red[threadIdx.y][al][threadIdx.x] = acc[al];
-  __syncthreads();
-  for (int al = threadIdx.y; al < npj; al += PRG) {
-    T sum = T(0);
-#pragma unroll
-    for (int g = 0; g < PRG; ++g) sum += red[g][al][threadIdx.x];
-    if (v < ncols) partial[((size_t)ch * npj + al) * ldp + v] = sum;
-  }
-}
-
-// Stage 2: U = sum over the atom's chunks; W[a][al][v] = coup_scale * sum_be coup[a][al][be] U[be][v]
-template <typename T>
-__global__ void __launch_bounds__(PVT) k_nl_couple(const int *__restrict__ atom_ch, int npj,
-                                                   const T *__restrict__ partial, int ldp,
-                                                   const double *__restrict__ coup, double coup_scale,
-                                                   T *__restrict__ W, int ncols) {
-  const int a = blockIdx.x;
-  const int v = blockIdx.y * PVT + threadIdx.x;
-  if (v >= ncols) return;
-  double U[MAXPJ];
-#pragma unroll
-  for (int al = 0; al < MAXPJ; ++al) U[al] = 0.0;
-  for (int ch = atom_ch[a]; ch < atom_ch[a + 1]; ++ch)
-#pragma unroll
-    for (int al = 0; al < MAXPJ; ++al)
-      if (al < npj) U[al] += (double)partial[((size_t)ch * npj + al) * ldp + v];
-  const double *Ca = coup ? coup + (size_t)a * npj * npj : nullptr;
-  for (int al = 0; al < npj; ++al) {
-    double w = 0.0;
-    if (Ca) {
-#pragma unroll
-      for (int be = 0; be < MAXPJ; ++be)
-        if (be < npj) w += Ca[al * npj + be] * U[be];
-    } else {
-#pragma unroll
-      for (int be = 0; be < MAXPJ; ++be)
-        if (be == al) w = U[be];
-    }
-    W[((size_t)a * npj + al) * ldp + v] = (T)(coup_scale * w);
-  }
-}
-
-// Expansion: Y[dof][v] += alpha * rowscale[dof] * colscale[v] * sum_{(a,s) at dof} P[s] . W[a][:, v]
-template <typename T>
-__global__ void __launch_bounds__(PVT *PRG) k_nl_expand(
-    int nnodes, const int *__restrict__ node_dof, const int *__restrict__ node_off,
-    const int *__restrict__ node_ent, const int *__restrict__ node_atom, const T *__restrict__ P,
-    int npj, const T *__restrict__ W, int ldw, T *__restrict__ Y, int ldy, int ncols, T alpha,
-    const T *__restrict__ rowscale, const double *__restrict__ colscale) {
-  const int u = blockIdx.x * PRG + threadIdx.y;
-  const int v = blockIdx.y * PVT + threadIdx.x;
-  if (u >= nnodes || v >= ncols) return;
-  T sum = T(0);
-  for (int k = node_off[u]; k < node_off[u + 1]; ++k) {
-    const int s = node_ent[k], a = node_atom[k];
-    const T *Ps = P + (size_t)s * npj;
-    const T *Wa = W + (size_t)a * npj * ldw + v;
-    for (int al = 0; al < npj; ++al) sum = fma(Ps[al], Wa[(size_t)al * ldw], sum);
-  }
-  const int d = node_dof[u];
-  T f = alpha;
-  if (rowscale) f *= rowscale[d];
-  if (colscale) f *= T(colscale[v]);
-  Y[(size_t)d * ldy + v] += f * sum;
-}
-
-template <typename T>
-static const T *Pvals(paw_context *c);
-template <>
-const double *Pvals<double>(paw_context *c) { return c->P64.as<double>(); }
-template <>
-const float *Pvals<float>(paw_context *c) { return c->P32.as<float>(); }
-
-template <typename T>
-void nl_project(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, const double *coup,
-                double coup_scale, T *W, cudaStream_t s) {
-  if (c->nent == 0 || ncols <= 0) return;
-  PAW_REQUIRE(c->npj <= MAXPJ, PAW_ERR_UNSUPPORTED, "more than 32 projectors per atom");
-  const int ldp = ncols;
-  c->ws_partial.ensure(sizeof(T) * (size_t)c->nchunks * c->npj * ldp, &c->dev_bytes);
-  dim3 g1(c->nchunks, (ncols + PVT - 1) / PVT);
-  k_nl_partial<T><<<g1, dim3(PVT, PRG), 0, s>>>(c->chunk_beg.as<int>(), c->chunk_end.as<int>(),
-                                                c->ent_dof.as<int>(), Pvals<T>(c), c->npj, X, ldx,
-                                                ncols, rowscale, c->ws_partial.as<T>(), ldp);
-  PAW_LAUNCH_CHECK("k_nl_partial");
-  dim3 g2(c->natoms, (ncols + PVT - 1) / PVT);
-  k_nl_couple<T><<<g2, PVT, 0, s>>>(c->atom_chunk_off.as<int>(), c->npj, c->ws_partial.as<T>(), ldp,
-                                    coup, coup_scale, W, ncols);
-  PAW_LAUNCH_CHECK("k_nl_couple");
-}
-
-template <typename T>
-void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, double alpha, const T *rowscale,
-               const double *colscale, cudaStream_t s) {
-  if (c->nent == 0 || ncols <= 0) return;
-  dim3 g((c->nnodes + PRG - 1) / PRG, (ncols + PVT - 1) / PVT);
-  k_nl_expand<T><<<g, dim3(PVT, PRG), 0, s>>>(c->nnodes, c->node_dof.as<int>(), c->node_off.as<int>(),
-                                              c->node_ent.as<int>(), c->node_atom.as<int>(), Pvals<T>(c),
-                                              c->npj, W, ncols, Y, ldy, ncols, (T)alpha, rowscale, colscale);
-  PAW_LAUNCH_CHECK("k_nl_expand");
-}
-
-template void nl_project<double>(paw_context *, const double *, int, int, const double *, const double *,
-                                 double, double *, cudaStream_t);
-template void nl_project<float>(paw_context *, const float *, int, int, const float *, const double *,
-                                double, float *, cudaStream_t);
-template void nl_expand<double>(paw_context *, const double *, int, double *, int, double, const double *,
-                                const double *, cudaStream_t);
-template void nl_expand<float>(paw_context *, const float *, int, float *, int, double, const float *,
-                               const double *, cudaStream_t);
-
 // ============================================================== elementwise
 template <typename T>
 __global__ void k_zero_block(T *Y, int64_t rows, int ncols, int ld) {
@@ -307,17 +165,9 @@ template void scale_rows<float>(const float *, int, float *, int, int64_t, int, 
 
 // ============================================================== composed operators
 template <typename T>
-static const T *HeMats(paw_context *c);
-template <>
-const double *HeMats<double>(paw_context *c) { return c->He64.as<double>(); }
-template <>
-const float *HeMats<float>(paw_context *c) { return c->He32.as<float>(); }
+static const T *HeMats(paw_context *c) { return c->He32.as<T>(); }
 template <typename T>
-static const T *MeMats(paw_context *c);
-template <>
-const double *MeMats<double>(paw_context *c) { return c->Me64.as<double>(); }
-template <>
-const float *MeMats<float>(paw_context *c) { return c->Me32.as<float>(); }
+static const T *MeMats(paw_context *c) { return c->Me32.as<T>(); }
 template <typename T>
 static const T *MdInv(paw_context *c);
 template <>
@@ -325,49 +175,63 @@ const double *MdInv<double>(paw_context *c) { return c->md_inv64.as<double>(); }
 template <>
 const float *MdInv<float>(paw_context *c) { return c->md_inv32.as<float>(); }
 
+// Local part H_loc X (Eq. FEM Ham entries) accumulated into Y with factor alpha:
+// FP64 through the sum-factorised cell kernel, FP32 through the SIMT or
+// tensor-core cell-matrix kernels.
+template <typename T>
+void local_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols, double alpha,
+             cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    local_sf(c, X, ldx, Y, ldy, ncols, alpha, 1.0, 1.0, 0.0, nullptr, s);
+  } else {
+    if (prec == PAW_TF32 || prec == PAW_BF16)
+      cell_apply_tc(c, prec, X, ldx, Y, ldy, ncols, (float)alpha, s);
+    else
+      cell_apply_simt<T>(c, HeMats<T>(c), (long long)c->nc * c->nc, X, ldx, Y, ldy, ncols, alpha, nullptr, s);
+  }
+}
+
 template <typename T>
 void op_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols,
           cudaStream_t s) {
   zero_block<T>(Y, c->ndof, ncols, ldy, s);
-  if constexpr (sizeof(T) == 4) {
-    if (prec == PAW_TF32 || prec == PAW_BF16) {
-      cell_apply_tc(c, prec, X, ldx, Y, ldy, ncols, 1.0f, s);
-    } else {
-      cell_apply_simt<T>(c, HeMats<T>(c), (long long)c->nc * c->nc, X, ldx, Y, ldy, ncols, 1.0,
-                         nullptr, s);
-    }
-  } else {
-    cell_apply_simt<T>(c, HeMats<T>(c), (long long)c->nc * c->nc, X, ldx, Y, ldy, ncols, 1.0,
-                       nullptr, s);
-  }
-  if (c->nent > 0) {
-    c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npj * ncols, &c->dev_bytes);
+  local_H<T>(c, prec, X, ldx, Y, ldy, ncols, 1.0, s);
+  if (c->nown_pairs > 0) {
+    c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
     nl_project<T>(c, X, ldx, ncols, nullptr, c->DH64.as<double>(), 1.0, c->ws_W.as<T>(), s);
-    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, 1.0, nullptr, nullptr, s);
+    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, nullptr, s);
   }
 }
 
 template <typename T>
 void op_S(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStream_t s) {
   zero_block<T>(Y, c->ndof, ncols, ldy, s);
-  cell_apply_simt<T>(c, MeMats<T>(c), 0, X, ldx, Y, ldy, ncols, 1.0, nullptr, s);
-  if (c->nent > 0) {
-    c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npj * ncols, &c->dev_bytes);
+  if constexpr (sizeof(T) == 8)
+    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 0.0, 0.0, 1.0, nullptr, s);
+  else
+    cell_apply_simt<T>(c, MeMats<T>(c), 0, X, ldx, Y, ldy, ncols, 1.0, nullptr, s);
+  if (c->nown_pairs > 0) {
+    c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
     nl_project<T>(c, X, ldx, ncols, nullptr, c->DS64.as<double>(), 1.0, c->ws_W.as<T>(), s);
-    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, 1.0, nullptr, nullptr, s);
+    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, nullptr, s);
   }
 }
 
 template <typename T>
 void op_Sinv(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStream_t s) {
-  scale_rows<T>(X, ldx, Y, ldy, c->ndof, ncols, MdInv<T>(c), s);
-  if (c->nent > 0) {
-    c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npj * ncols, &c->dev_bytes);
-    nl_project<T>(c, Y, ldy, ncols, nullptr, c->DSinv64.as<double>(), 1.0, c->ws_W.as<T>(), s);
-    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, -1.0, MdInv<T>(c), nullptr, s);
+  if (c->nown_pairs == 0) {
+    scale_rows<T>(X, ldx, Y, ldy, c->ndof, ncols, MdInv<T>(c), s);
+    return;
   }
+  c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
+  nl_project<T>(c, X, ldx, ncols, MdInv<T>(c), c->DSinv64.as<double>(), 1.0, c->ws_W.as<T>(), s);
+  nl_sinv_out<T>(c, c->ws_W.as<T>(), ncols, X, ldx, Y, ldy, MdInv<T>(c), s);
 }
 
+template void local_H<double>(paw_context *, paw_precision, const double *, int, double *, int, int, double,
+                              cudaStream_t);
+template void local_H<float>(paw_context *, paw_precision, const float *, int, float *, int, int, double,
+                             cudaStream_t);
 template void op_H<double>(paw_context *, paw_precision, const double *, int, double *, int, int, cudaStream_t);
 template void op_H<float>(paw_context *, paw_precision, const float *, int, float *, int, int, cudaStream_t);
 template void op_S<double>(paw_context *, const double *, int, double *, int, int, cudaStream_t);

@@ -122,6 +122,8 @@ void build_tables(paw_context *c) {
       M1[(size_t)a * np1 + b] = m;
       D1[(size_t)a * np1 + b] = d;
     }
+  c->M1 = M1;
+  c->D1 = D1;
   const double hh = c->h / 2.0;
   c->K_ref.assign((size_t)nc * nc, 0.0);
   c->M_ref.assign((size_t)nc * nc, 0.0);
@@ -141,6 +143,7 @@ void build_tables(paw_context *c) {
   lagrange_tables(xi, g2, phi2, dphi2);
   const int nq1 = p + 2, nq = nq1 * nq1 * nq1;
   c->gq = g2;
+  c->phiq = phi2;   // phiq[i * np1 + a] = phi_a(g_i)
   c->Nq.assign((size_t)nq * nc, 0.0);
   c->wq.assign(nq, 0.0);
   for (int q = 0; q < nq; ++q) {
@@ -162,6 +165,7 @@ void build_tables(paw_context *c) {
     mdi[d] = 1.0 / (hh * hh * hh * what[i] * what[j] * what[k]);
     mdf[d] = (float)mdi[d];
   }
+  c->mdinv_h = mdi;
   c->md_inv64.ensure(sizeof(double) * c->ndof, &c->dev_bytes);
   c->md_inv32.ensure(sizeof(float) * c->ndof, &c->dev_bytes);
   PAW_CUDA(cudaMemcpy(c->md_inv64.ptr, mdi.data(), sizeof(double) * c->ndof, cudaMemcpyHostToDevice));
@@ -364,6 +368,7 @@ void rebuild_hamiltonian(paw_context *c) {
   PAW_LAUNCH_CHECK("k_build_He");
   c->tc_tf32.valid = 0;
   c->tc_bf16.valid = 0;
+  c->wV_valid = 0;
   PAW_CUDA(cudaDeviceSynchronize());
 }
 
@@ -403,8 +408,7 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
   if (natoms == 0 || npj == 0) {
     c->nent = 0;
     c->npairs = 0;
-    c->nnodes = 0;
-    c->nchunks = 0;
+    c->nown_pairs = 0;
     return;
   }
   double rmax = 0.0;
@@ -501,55 +505,119 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
   d_pos.release(&tmpc);
   d_gq.release(&tmpc);
 
-  // ---- projection chunks (atom-major)
-  const int CH = 256;
-  std::vector<int> ch_atom, ch_beg, ch_end, atom_ch(natoms + 1, 0);
-  for (int a = 0; a < natoms; ++a) {
-    for (int64_t b = c->ent_off[a]; b < c->ent_off[a + 1]; b += CH) {
-      ch_atom.push_back(a);
-      ch_beg.push_back((int)b);
-      ch_end.push_back((int)std::min<int64_t>(b + CH, c->ent_off[a + 1]));
+  // ---- owner-cell pairs with assembled projector values on owned nodes
+  {
+    const int p = c->p, N1 = c->N1;
+    c->own = p * p * p;
+    c->npad = npj <= 16 ? 16 : 32;
+    std::vector<double> P((size_t)c->nent * npj);
+    PAW_CUDA(cudaMemcpy(P.data(), c->P64.ptr, sizeof(double) * P.size(), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> keys;   // cell * natoms + atom
+    keys.reserve(c->nent / 16 + 16);
+    std::vector<int> ent_owner(c->nent), ent_slot(c->nent);
+    for (int a = 0; a < natoms; ++a)
+      for (int64_t s = c->ent_off[a]; s < c->ent_off[a + 1]; ++s) {
+        const int d = ent_dof[s];
+        const int i = d % N1, j = (d / N1) % N1, k = d / (N1 * N1);
+        const int e = (i / p) + c->n * ((j / p) + c->n * (k / p));
+        ent_owner[s] = e;
+        ent_slot[s] = (i % p) + p * ((j % p) + p * (k % p));
+        keys.push_back((int64_t)e * natoms + a);
+      }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    c->nown_pairs = (int64_t)keys.size();
+    std::vector<int> off(c->ncells + 1, 0), oatom(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) {
+      off[keys[k] / natoms + 1]++;
+      oatom[k] = (int)(keys[k] % natoms);
     }
-    atom_ch[a + 1] = (int)ch_atom.size();
-  }
-  c->nchunks = (int)ch_atom.size();
-  c->chunk_atom.ensure(sizeof(int) * std::max(1, c->nchunks), &c->dev_bytes);
-  c->chunk_beg.ensure(sizeof(int) * std::max(1, c->nchunks), &c->dev_bytes);
-  c->chunk_end.ensure(sizeof(int) * std::max(1, c->nchunks), &c->dev_bytes);
-  c->atom_chunk_off.ensure(sizeof(int) * (natoms + 1), &c->dev_bytes);
-  PAW_CUDA(cudaMemcpy(c->chunk_atom.ptr, ch_atom.data(), sizeof(int) * c->nchunks, cudaMemcpyHostToDevice));
-  PAW_CUDA(cudaMemcpy(c->chunk_beg.ptr, ch_beg.data(), sizeof(int) * c->nchunks, cudaMemcpyHostToDevice));
-  PAW_CUDA(cudaMemcpy(c->chunk_end.ptr, ch_end.data(), sizeof(int) * c->nchunks, cudaMemcpyHostToDevice));
-  PAW_CUDA(cudaMemcpy(c->atom_chunk_off.ptr, atom_ch.data(), sizeof(int) * (natoms + 1), cudaMemcpyHostToDevice));
+    for (int e = 0; e < c->ncells; ++e) {
+      c->max_own_pairs = std::max(c->max_own_pairs, off[e + 1]);
+      off[e + 1] += off[e];
+    }
+    PAW_REQUIRE(c->max_own_pairs <= 48, PAW_ERR_UNSUPPORTED,
+                "more than 48 atoms have projector support on the nodes of one cell");
+    const size_t blk = (size_t)c->own * c->npad;
+    std::vector<double> oP(keys.size() * blk, 0.0);
+    for (int a = 0; a < natoms; ++a)
+      for (int64_t s = c->ent_off[a]; s < c->ent_off[a + 1]; ++s) {
+        const int64_t key = (int64_t)ent_owner[s] * natoms + a;
+        const size_t k = std::lower_bound(keys.begin(), keys.end(), key) - keys.begin();
+        double *dst = oP.data() + k * blk + (size_t)ent_slot[s] * c->npad;
+        for (int al = 0; al < npj; ++al) dst[al] = P[(size_t)s * npj + al];
+      }
+    std::vector<float> oPf(oP.size());
+    for (size_t i = 0; i < oP.size(); ++i) oPf[i] = (float)oP[i];
+    c->own_off.ensure(sizeof(int) * off.size(), &c->dev_bytes);
+    c->own_atom.ensure(sizeof(int) * std::max<size_t>(1, oatom.size()), &c->dev_bytes);
+    c->ownP64.ensure(sizeof(double) * std::max<size_t>(1, oP.size()), &c->dev_bytes);
+    c->ownP32.ensure(sizeof(float) * std::max<size_t>(1, oPf.size()), &c->dev_bytes);
+    PAW_CUDA(cudaMemcpy(c->own_off.ptr, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+    PAW_CUDA(cudaMemcpy(c->own_atom.ptr, oatom.data(), sizeof(int) * oatom.size(), cudaMemcpyHostToDevice));
+    PAW_CUDA(cudaMemcpy(c->ownP64.ptr, oP.data(), sizeof(double) * oP.size(), cudaMemcpyHostToDevice));
+    PAW_CUDA(cudaMemcpy(c->ownP32.ptr, oPf.data(), sizeof(float) * oPf.size(), cudaMemcpyHostToDevice));
 
-  // ---- node-major view for the expansion P W
-  std::vector<std::pair<int, int>> by_node((size_t)c->nent);   // (dof, entry)
-  std::vector<int> ent_atom(c->nent);
-  for (int a = 0; a < natoms; ++a)
-    for (int64_t s = c->ent_off[a]; s < c->ent_off[a + 1]; ++s) {
-      by_node[s] = {ent_dof[s], (int)s};
-      ent_atom[s] = a;
+    // atom-major index of the pairs (for the deterministic per-atom reduction)
+    {
+      std::vector<int> aoff(natoms + 1, 0), ap(keys.size());
+      for (size_t k = 0; k < keys.size(); ++k) aoff[oatom[k] + 1]++;
+      for (int a = 0; a < natoms; ++a) aoff[a + 1] += aoff[a];
+      std::vector<int> fill(aoff.begin(), aoff.end() - 1);
+      for (size_t k = 0; k < keys.size(); ++k) ap[fill[oatom[k]]++] = (int)k;
+      c->apair_off.ensure(sizeof(int) * aoff.size(), &c->dev_bytes);
+      c->apair.ensure(sizeof(int) * std::max<size_t>(1, ap.size()), &c->dev_bytes);
+      PAW_CUDA(cudaMemcpy(c->apair_off.ptr, aoff.data(), sizeof(int) * aoff.size(), cudaMemcpyHostToDevice));
+      PAW_CUDA(cudaMemcpy(c->apair.ptr, ap.data(), sizeof(int) * ap.size(), cudaMemcpyHostToDevice));
     }
-  std::sort(by_node.begin(), by_node.end());
-  std::vector<int> node_dof, node_off, node_ent, node_atom;
-  for (size_t i = 0; i < by_node.size(); ++i) {
-    if (i == 0 || by_node[i].first != by_node[i - 1].first) {
-      node_dof.push_back(by_node[i].first);
-      node_off.push_back((int)i);
+
+    // atom pairs sharing an owned node somewhere, and G_ab accumulated cell by cell
+    std::vector<std::vector<int>> nb(natoms);
+    for (int e = 0; e < c->ncells; ++e)
+      for (int k1 = off[e]; k1 < off[e + 1]; ++k1)
+        for (int k2 = off[e]; k2 < off[e + 1]; ++k2) nb[oatom[k1]].push_back(oatom[k2]);
+    std::vector<int> goff(natoms + 1, 0), gatom;
+    for (int a = 0; a < natoms; ++a) {
+      std::sort(nb[a].begin(), nb[a].end());
+      nb[a].erase(std::unique(nb[a].begin(), nb[a].end()), nb[a].end());
+      gatom.insert(gatom.end(), nb[a].begin(), nb[a].end());
+      goff[a + 1] = (int)gatom.size();
     }
-    node_ent.push_back(by_node[i].second);
-    node_atom.push_back(ent_atom[by_node[i].second]);
+    c->ngpairs = (int64_t)gatom.size();
+    const int np = c->npad;
+    std::vector<double> Gf((size_t)c->ngpairs * np * np, 0.0);
+    const int p3 = c->own;
+    for (int e = 0; e < c->ncells; ++e) {
+      std::vector<double> w(p3);
+      for (int o = 0; o < p3; ++o) {
+        const int a0 = o % p, b0 = (o / p) % p, c0 = o / (p * p);
+        const int cx = e % c->n, cy = (e / c->n) % c->n, cz = e / (c->n * c->n);
+        const int64_t d = (int64_t)(cx * p + a0) + (int64_t)N1 * ((cy * p + b0) + (int64_t)N1 * (cz * p + c0));
+        w[o] = c->mdinv_h[d];
+      }
+      for (int k1 = off[e]; k1 < off[e + 1]; ++k1)
+        for (int k2 = off[e]; k2 < off[e + 1]; ++k2) {
+          const int a1 = oatom[k1], a2 = oatom[k2];
+          const int slot = goff[a1] + (int)(std::lower_bound(nb[a1].begin(), nb[a1].end(), a2) - nb[a1].begin());
+          double *G = Gf.data() + (size_t)slot * np * np;
+          const double *P1 = oP.data() + (size_t)k1 * blk, *P2 = oP.data() + (size_t)k2 * blk;
+          for (int o = 0; o < p3; ++o) {
+            const double *r1 = P1 + (size_t)o * np, *r2 = P2 + (size_t)o * np;
+            for (int al = 0; al < npj; ++al) {
+              const double f = w[o] * r1[al];
+              if (f == 0.0) continue;
+              for (int be = 0; be < npj; ++be) G[al * np + be] += f * r2[be];
+            }
+          }
+        }
+    }
+    c->gnb_off.ensure(sizeof(int) * goff.size(), &c->dev_bytes);
+    c->gnb_atom.ensure(sizeof(int) * std::max<size_t>(1, gatom.size()), &c->dev_bytes);
+    c->Gfull.ensure(sizeof(double) * std::max<size_t>(1, Gf.size()), &c->dev_bytes);
+    PAW_CUDA(cudaMemcpy(c->gnb_off.ptr, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
+    PAW_CUDA(cudaMemcpy(c->gnb_atom.ptr, gatom.data(), sizeof(int) * gatom.size(), cudaMemcpyHostToDevice));
+    PAW_CUDA(cudaMemcpy(c->Gfull.ptr, Gf.data(), sizeof(double) * Gf.size(), cudaMemcpyHostToDevice));
   }
-  node_off.push_back((int)by_node.size());
-  c->nnodes = (int)node_dof.size();
-  c->node_dof.ensure(sizeof(int) * node_dof.size(), &c->dev_bytes);
-  c->node_off.ensure(sizeof(int) * node_off.size(), &c->dev_bytes);
-  c->node_ent.ensure(sizeof(int) * node_ent.size(), &c->dev_bytes);
-  c->node_atom.ensure(sizeof(int) * node_atom.size(), &c->dev_bytes);
-  PAW_CUDA(cudaMemcpy(c->node_dof.ptr, node_dof.data(), sizeof(int) * node_dof.size(), cudaMemcpyHostToDevice));
-  PAW_CUDA(cudaMemcpy(c->node_off.ptr, node_off.data(), sizeof(int) * node_off.size(), cudaMemcpyHostToDevice));
-  PAW_CUDA(cudaMemcpy(c->node_ent.ptr, node_ent.data(), sizeof(int) * node_ent.size(), cudaMemcpyHostToDevice));
-  PAW_CUDA(cudaMemcpy(c->node_atom.ptr, node_atom.data(), sizeof(int) * node_atom.size(), cudaMemcpyHostToDevice));
 
   // ---- G_a
   {
