@@ -171,6 +171,30 @@ paw_status paw_apply_S(paw_handle h, paw_precision prec, const void *X, void *Y,
 paw_status paw_apply_Sinv_approx(paw_handle h, paw_precision prec, const void *X,
                                  void *Y, int ncols, int ldx, int ldy, void *stream);
 
+/* Same result as paw_apply_Sinv_approx, but this call never allocates device
+ * memory.  It is meant for callers that cannot call cudaMalloc at the point of
+ * use: code running while a stream is being captured into a CUDA graph (where
+ * allocation calls are not permitted), real-time loops that must not block on
+ * the allocator, or hosts that hand the library a fixed memory budget.
+ * (Library-side engineering; the paper has no counterpart.)
+ *
+ * Its scratch (projector partial sums and coefficients) lives in one
+ * statically sized device array of PAW_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  It needs elem * npad * ncols * (owner pairs + 2 natoms) bytes
+ * (elem = 8 for PAW_FP64, 4 otherwise; npad = projectors per atom rounded up
+ * to 16); a larger request returns PAW_ERR_INVALID_ARG before any device work.
+ * The first call on a device looks the array up (cudaGetSymbolAddress, which
+ * may load the library's device code): make that first call before any stream
+ * capture begins.  All calls share the one array and leave their partial
+ * sums in it; every value a call reads it has first written itself, so
+ * nothing needs clearing, but calls whose GPU work overlaps (different
+ * streams, or different handles on one device) race on the array and must be
+ * serialised by the caller. */
+#define PAW_NOALLOC_SCRATCH_BYTES (32u << 20)
+paw_status paw_apply_Sinv_approx_noalloc(paw_handle h, paw_precision prec, const void *X,
+                                         void *Y, int ncols, int ldx, int ldy, void *stream);
+
 /* Algorithm 2: Psi_f = Shat^-1 R_m + Psi_in C_m(Lambda~) for one or more
  * blocks of columns (processed opts.block columns at a time).
  *   X_in      : device FP64 ndof x ncols (ld ldx), the block Psi_in

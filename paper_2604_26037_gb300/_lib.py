@@ -86,6 +86,7 @@ SIGNATURES = {
     "paw_apply_H": [_VP, _I, _VP, _VP, _I, _I, _I, _VP],
     "paw_apply_S": [_VP, _I, _VP, _VP, _I, _I, _I, _VP],
     "paw_apply_Sinv_approx": [_VP, _I, _VP, _VP, _I, _I, _I, _VP],
+    "paw_apply_Sinv_approx_noalloc": [_VP, _I, _VP, _VP, _I, _I, _I, _VP],
     "paw_cheb_filter": [_VP, _I, _VP, _I, _DP, _I, _I, _Bounds, _VP, _I, _VP],
     "paw_rayleigh_ritz": [_VP, _VP, _I, _I, _DP, _VP],
     "paw_residuals": [_VP, _VP, _I, _DP, _I, _DP, _VP],

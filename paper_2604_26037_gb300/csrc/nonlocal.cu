@@ -17,6 +17,9 @@
 // precision" without FP64 instructions: Y is split once per block into two
 // FP32 words (hi + lo) and the product and sum are formed with error-free
 // FP32 transformations (about 48 significant bits), then rounded once to FP32.
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 
 namespace pawfe {
@@ -657,3 +660,87 @@ template void nl_sinv_out<float>(paw_context *, const float *, int, const float 
                                  const float *, cudaStream_t);
 
 }  // namespace pawfe
+
+// ====================================================================== no-allocation variant
+// Shat^-1 X with every scratch buffer carved out of one static device array,
+// for callers that cannot allocate device memory at the point of use.
+namespace pawfe {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PAW_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device.  In host code the symbol itself is only a host-side handle.
+static void *noalloc_scratch() {
+  static std::mutex mu;
+  static void *addr[128] = {};
+  int dev = 0;
+  PAW_CUDA(cudaGetDevice(&dev));
+  PAW_REQUIRE(dev >= 0 && dev < 128, PAW_ERR_UNSUPPORTED, "device ordinal above 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    PAW_REQUIRE(e == cudaSuccess && p != nullptr, PAW_ERR_CUDA,
+                std::string("cudaGetSymbolAddress(no-allocation scratch): ") + cudaGetErrorString(e));
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+template <typename T>
+static void sinv_noalloc(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStream_t s) {
+  const T *mdinv = (sizeof(T) == 8) ? reinterpret_cast<const T *>(c->md_inv64.ptr)
+                                    : reinterpret_cast<const T *>(c->md_inv32.ptr);
+  if (c->nown_pairs == 0) {   // M_D^-1 X only
+    scale_rows<T>(X, ldx, Y, ldy, c->ndof, ncols, mdinv, s);
+    return;
+  }
+  const size_t need = sizeof(T) * (size_t)c->npad * ncols * ((size_t)c->nown_pairs + 2 * (size_t)c->natoms);
+  PAW_REQUIRE(need <= PAW_NOALLOC_SCRATCH_BYTES, PAW_ERR_INVALID_ARG,
+              "no-allocation scratch too small: " + std::to_string(need) + " bytes needed, " +
+                  std::to_string((size_t)PAW_NOALLOC_SCRATCH_BYTES) + " available (at most " +
+                  std::to_string(PAW_NOALLOC_SCRATCH_BYTES /
+                                 (sizeof(T) * (size_t)c->npad * ((size_t)c->nown_pairs + 2 * (size_t)c->natoms))) +
+                  " columns per call for this problem)");
+  T *PP = static_cast<T *>(noalloc_scratch());
+  T *U = PP + (size_t)c->nown_pairs * c->npad * ncols;
+  T *W = U + (size_t)c->natoms * c->npad * ncols;
+  // projection partials, fixed-order reduction per atom, coupling, expansion:
+  // every scratch value is written before it is read
+  if (c->npad == 16)
+    project_impl<T, 16>(c, X, ldx, ncols, mdinv, PP, s);
+  else
+    project_impl<T, 32>(c, X, ldx, ncols, mdinv, PP, s);
+  dim3 g((ncols + 31) / 32, c->npad, c->natoms);
+  k_pair_reduce<T><<<g, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
+  PAW_LAUNCH_CHECK("k_pair_reduce");
+  couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, W, ncols, s);
+  nl_sinv_out<T>(c, W, ncols, X, ldx, Y, ldy, mdinv, s);
+}
+
+}  // namespace pawfe
+
+extern "C" paw_status paw_apply_Sinv_approx_noalloc(paw_handle c, paw_precision prec, const void *X, void *Y,
+                                                    int ncols, int ldx, int ldy, void *stream) {
+  using namespace pawfe;
+  try {
+    PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+    PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16, PAW_ERR_INVALID_ARG,
+                "unknown precision");
+    PAW_REQUIRE(ncols >= 0, PAW_ERR_INVALID_ARG, "ncols < 0");
+    if (ncols == 0) return PAW_OK;
+    PAW_REQUIRE(X && Y, PAW_ERR_INVALID_ARG, "NULL X or Y");
+    PAW_REQUIRE(ldx >= ncols && ldy >= ncols, PAW_ERR_INVALID_ARG, "leading dimension smaller than ncols");
+    auto s = (cudaStream_t)stream;
+    c->last_stream = s;
+    if (prec == PAW_FP64)
+      sinv_noalloc<double>(c, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+    else
+      sinv_noalloc<float>(c, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+    return PAW_OK;
+  } catch (const Error &err) {
+    return fail(err.code, err.msg);
+  } catch (const std::exception &ex) {
+    return fail(PAW_ERR_CUDA, ex.what());
+  }
+}
