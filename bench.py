@@ -240,6 +240,7 @@ def run_ours(args, ws, rank, local):
     phases = {k: v for k, v in prof.items() if isinstance(v, dict)}
     dom = max(phases, key=lambda k: phases[k]["ms"])
     roof = roofline(dom, phases[dom], fe, sysd, cfg, args.prec, peaks, clocks)
+    all_roof = {k: roofline(k, v, fe, sysd, cfg, args.prec, peaks, clocks) for k, v in phases.items()}
     launches = prof["total_launches"] // args.steps
 
     res = {
@@ -256,6 +257,8 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
         "roofline": roof,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in phases.items()},
+        "phase_roofline": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "ms_per_launch")
+                               if kk in v} for k, v in all_roof.items()},
         "fp64_form": fp64,
         "speedup_vs_fp64": (round(value / fp64["value"], 3) if fp64 else None),
         "e2e": e2e,
@@ -269,27 +272,69 @@ def fe_np1(nc):
     return int(round(nc ** (1.0 / 3.0)))
 
 
-def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
-    """Roofline of one phase of the filter, per launch, from algorithmic bytes/flops."""
+# kernels that make up each profiled phase of the filter (library phase brackets)
+PHASE_KERNELS = {
+    "residual_local": "k_local_sf (FP64 sum-factorised 1/2 K + V - lambda M)",
+    "residual_nonlocal": "k_own_project + k_pair_reduce + k_own_couple + k_own_expand (FP64)",
+    "recurrence": "k_own_expand (fused Shat^-1 expansion + nonlocal H + recurrence update)",
+    "projection": "k_own_project + k_pair_reduce + k_own_couple + k_own_couple_h",
+    "cell_products": "k_cell_tc (tcgen05) or k_cell_simt",
+    "recovery": "Shat^-1 of R_m + FP64 combination",
+}
+
+
+def phase_model(phase, fe, cfg, prec):
+    """Algorithmic (flops, bytes, compute kind) of one launch of a phase for one block."""
     M, B = fe.ndof, cfg["block"]
     nc, ncells = fe.nodes_per_cell, fe.ncells
-    per_launch_ms = pinfo["ms"] / max(pinfo["intervals"], 1)
-    es = 8 if prec == "fp64" else 4
+    n1 = fe_np1(nc)
+    # algorithmic work counts the nproj projectors only (not the padding to 16)
+    own, npad, pairs = (n1 - 1) ** 3, fe.nproj, fe.owner_pairs
+    f32 = prec != "fp64"
+    es = 4 if f32 else 8
     if phase == "cell_products":
-        flops = 2.0 * ncells * nc * nc * B
         mat_es = {"bf16": 2, "tf32": 4, "fp32": 4, "fp64": 8}[prec]
-        byts = ncells * nc * nc * mat_es + M * B * es * 3        # H^e stream + gather + accumulate r/w
-    elif phase == "residual_local":
-        # sum-factorised (1/2 K + V - lambda M) per cell and vector, FP64 (see sumfac.cu)
-        n1, q1 = fe_np1(nc), fe_np1(nc) + 1
+        if prec == "fp64":   # sum-factorised local H in FP64
+            q1 = n1 + 1
+            fma_cell = 7 * n1 ** 4 + 2 * (q1 * n1 ** 3 + q1 * q1 * n1 ** 2 + q1 ** 3 * n1)
+            return 2.0 * fma_cell * ncells * B, M * B * 8 * 3, "fp64"
+        kind = {"tf32": "tf32", "bf16": "bf16", "fp32": "fp32"}[prec]
+        return 2.0 * ncells * nc * nc * B, ncells * nc * nc * mat_es + M * B * 4 * 3, kind
+    if phase == "residual_local":
+        q1 = n1 + 1
         fma_cell = 7 * n1 ** 4 + 2 * (q1 * n1 ** 3 + q1 * q1 * n1 ** 2 + q1 ** 3 * n1)
-        flops = 2.0 * fma_cell * ncells * B
-        byts = M * B * 8 * 3
-        es = 8
-    else:
-        flops = None
-        byts = None
-    if byts is None:
+        return 2.0 * fma_cell * ncells * B, M * B * 8 * 3, "fp64"
+    pbytes = pairs * own * npad * es
+    if phase == "projection":
+        return (2.0 * pairs * own * npad * B, M * B * es + pbytes + 2 * pairs * npad * B * es,
+                "fp32" if f32 else "fp64")
+    if phase == "recurrence":
+        # reads R_Y, R_X and Y (an FP32 hi/lo pair or FP64: 8 bytes), writes T and R_X
+        return (4.0 * pairs * own * npad * B, M * B * (es * 4 + 8) + pbytes,
+                "fp32" if f32 else "fp64")
+    if phase == "residual_nonlocal":
+        return (4.0 * pairs * own * npad * B, M * B * 8 * 3 + 2 * pairs * own * npad * 8, "fp64")
+    if phase == "recovery":
+        return (4.0 * pairs * own * npad * B, M * B * (es * 2 + 8 * 2), "fp32" if f32 else "fp64")
+    return None, None, None
+
+
+def compute_peak(kind, peaks, sm_mhz):
+    """TFLOP/s ceiling of a compute kind, from the measured bf16 peak or the unit counts."""
+    if kind == "tf32":
+        return peaks["bf16"] * (1.1 / 2.25), "tensor"          # nominal TF32/BF16 dense ratio
+    if kind == "bf16":
+        return peaks["bf16"], "tensor"
+    if kind == "fp64":
+        return 1.25 * sm_mhz / 2070.0, "alu"                   # GB300 FP64 1.25 TFLOP/s at 2070 MHz
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "alu"          # FP32 FFMA: 152 SMs x 128 lanes x 2
+
+
+def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
+    """Roofline of one phase of the filter, per launch, from algorithmic bytes/flops."""
+    per_launch_ms = pinfo["ms"] / max(pinfo["intervals"], 1)
+    flops, byts, kind = phase_model(phase, fe, cfg, prec)
+    if flops is None or per_launch_ms <= 0:
         return {"bound": "hbm", "achieved": None, "peak": peaks["hbm"], "unit": "GB/s", "frac": None,
                 "traffic": None, "kernel": phase}
     sec = per_launch_ms / 1e3
@@ -297,28 +342,16 @@ def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
     tfs = flops / sec / 1e12
     hbm_frac = gbs / peaks["hbm"]
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    if phase == "residual_local" or es == 8:
-        cpk = 1.25 * sm_mhz / 2070.0                              # FP64: 1.25 TFLOP/s at 2070 MHz
-        cunit, cbound = "TFLOP/s", "alu"
-    elif prec in ("tf32", "bf16"):
-        cpk = peaks["bf16"] * (0.5 if prec == "tf32" else 1.0)   # TF32 dense = bf16 x 1.1/2.25 nominal
-        cunit, cbound = "TFLOP/s", "tensor"
-    elif es == 8 or phase == "residual_local":
-        cpk = 1.25 * sm_mhz / 2070.0                              # FP64: 1.25 TFLOP/s at 2070 MHz
-        cunit, cbound = "TFLOP/s", "alu"
-    else:
-        cpk = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12                # FP32 FFMA: 152 SMs x 128 lanes x 2
-        cunit, cbound = "TFLOP/s", "alu"
+    cpk, cbound = compute_peak(kind, peaks, sm_mhz)
     c_frac = tfs / cpk
+    common = {"traffic": None, "kernel": phase, "kernels": PHASE_KERNELS.get(phase),
+              "ms_per_launch": round(per_launch_ms, 4), "algorithmic_bytes_per_launch": byts,
+              "algorithmic_flops_per_launch": flops, "peak_source": peaks["src"]}
     if c_frac >= hbm_frac:
-        return {"bound": cbound, "achieved": round(tfs, 3), "peak": round(cpk, 2), "unit": cunit,
-                "frac": round(c_frac, 4), "traffic": None, "kernel": phase,
-                "algorithmic_flops_per_launch": flops, "ms_per_launch": round(per_launch_ms, 4),
-                "hbm_frac": round(hbm_frac, 4), "peak_source": peaks["src"]}
+        return {"bound": cbound, "achieved": round(tfs, 3), "peak": round(cpk, 2), "unit": "TFLOP/s",
+                "frac": round(c_frac, 4), "hbm_frac": round(hbm_frac, 4), "compute": kind, **common}
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm"], "unit": "GB/s",
-            "frac": round(hbm_frac, 4), "traffic": None, "kernel": phase,
-            "algorithmic_bytes_per_launch": byts, "ms_per_launch": round(per_launch_ms, 4),
-            "compute_frac": round(c_frac, 4), "peak_source": peaks["src"]}
+            "frac": round(hbm_frac, 4), "compute_frac": round(c_frac, 4), "compute": kind, **common}
 
 
 # ----------------------------------------------------------------------------- reference arm

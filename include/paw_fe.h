@@ -124,6 +124,11 @@ typedef struct {
   int32_t degree;      /* p                                                  */
   int64_t support_pairs;   /* number of (cell, atom) pairs in projector supports */
   int64_t device_bytes;    /* device memory currently held by the handle       */
+  int64_t owner_pairs;     /* (cell, atom) pairs with P^a nonzero on a node the
+                              cell owns (local indices < p): the work unit of the
+                              projector contractions                          */
+  int32_t nproj_padded;    /* projectors per atom as stored (16 or 32)        */
+  int32_t reserved;
 } paw_info;
 
 /* Build every operator of the problem (Sec. 4.1): cell matrices

@@ -68,7 +68,8 @@ class _Bounds(C.Structure):
 class _Info(C.Structure):
     _fields_ = [("ndof", C.c_int64), ("ncells", C.c_int32), ("nodes_per_cell", C.c_int32),
                 ("quad_per_cell", C.c_int32), ("natoms", C.c_int32), ("nproj", C.c_int32),
-                ("degree", C.c_int32), ("support_pairs", C.c_int64), ("device_bytes", C.c_int64)]
+                ("degree", C.c_int32), ("support_pairs", C.c_int64), ("device_bytes", C.c_int64),
+                ("owner_pairs", C.c_int64), ("nproj_padded", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _Profile(C.Structure):
@@ -199,6 +200,8 @@ class PawFE:
         self.nodes_per_cell = int(info.nodes_per_cell)
         self.quad_per_cell = int(info.quad_per_cell)
         self.support_pairs = int(info.support_pairs)
+        self.owner_pairs = int(info.owner_pairs)
+        self.nproj_padded = int(info.nproj_padded)
         self.block = int(block)
 
     @classmethod

@@ -599,6 +599,9 @@ paw_status paw_get_info(paw_handle c, paw_info *out) {
   out->degree = c->p;
   out->support_pairs = c->npairs;
   out->device_bytes = c->dev_bytes;
+  out->owner_pairs = c->nown_pairs;
+  out->nproj_padded = c->npad;
+  out->reserved = 0;
   return PAW_OK;
 }
 
