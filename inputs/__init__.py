@@ -51,6 +51,12 @@ CONFIGS = {
                    shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
                    lattice=(2, 2, 2), jitter=0.3,
                    nvec=256, block=256, degree=4, iters=1, nwanted=256),
+    # moderate case for profiler captures: arrays of 128 vectors (191 MB) exceed L2,
+    # the whole problem holds a few GB on the device
+    "prof12": dict(index=6, L=30.0, ncell=12, p=6, natoms=27,
+                   shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
+                   lattice=(3, 3, 3), jitter=0.3,
+                   nvec=128, block=128, degree=4, iters=1, nwanted=128),
     "grad16": dict(index=4, L=40.0, ncell=16, p=4, natoms=64,
                    shells=[(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)],
                    lattice=(4, 4, 4), jitter=0.3,

@@ -154,7 +154,7 @@ static void residual_block(paw_context *c, const double *X, int ldx, const doubl
     c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
     double *W = c->ws_W2.as<double>();
     nl_project_residual<double>(c, X, ldx, ncols, negLam_dev, W, s);
-    nl_expand<double>(c, W, ncols, Y, ldy, nullptr, s);
+    nl_expand<double>(c, PAW_FP64, W, ncols, Y, ldy, nullptr, s);
   }
 }
 
@@ -251,12 +251,12 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
       // one projection gives the coefficients of Shat^-1 (W_S) and of the nonlocal H (W_H)
       {
         PhaseScope ps(c, 2, s);
-        nl_project_filter<TR>(c, RY, ldr, nb, mdinv, alpha, WS, WH, s);
+        nl_project_filter<TR>(c, prec, RY, ldr, nb, mdinv, alpha, WS, WH, s);
       }
       // T = Shat^-1 R_Y and the recurrence update with the nonlocal part of alpha H T
       PhaseScope ps(c, 1, s);
       if constexpr (f32)
-        nl_recurrence_f32(c, WS, WH, nb, RY, RX, T, ldr, mdinv, Yhi, Ylo, ldr, d_chi + ko, d_clo + ko, be_h[k],
+        nl_recurrence_f32(c, prec, WS, WH, nb, RY, RX, T, ldr, mdinv, Yhi, Ylo, ldr, d_chi + ko, d_clo + ko, be_h[k],
                           ga_h[k], s);
       else
         nl_recurrence_f64(c, WS, WH, nb, RY, RX, T, ldr, mdinv, Y0, nb, d_cf + ko, be_h[k], ga_h[k], s);
@@ -277,14 +277,16 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   // step 5: Psi_f = Shat^-1 R_Y + X Lambda_Y
   {
     PhaseScope ps(c, 5, s);
-    op_Sinv<TR>(c, RY, ldr, T, ldr, nb, s);
+    op_Sinv<TR>(c, prec, RY, ldr, T, ldr, nb, s);
     k_cheb_recover<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, T, ldr, X, ldx, d_lyfin, Xo, ldo);
     PAW_LAUNCH_CHECK("k_cheb_recover");
   }
   // keep host-side scalars alive until the async copies have been consumed
   PAW_CUDA(cudaStreamSynchronize(s));
-  if (prec == PAW_TF32 || prec == PAW_BF16)
-    PAW_REQUIRE(tc_read_status() == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+  if (prec == PAW_TF32 || prec == PAW_BF16) {
+    const int st_cell = tc_read_status(), st_nl = nltc_read_status();
+    PAW_REQUIRE(st_cell == 0 && st_nl == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+  }
 }
 
 // ============================================================== reductions
@@ -579,7 +581,8 @@ paw_status paw_destroy(paw_handle c) {
                     &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
                     &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
-                    &c->apair_off, &c->apair, &c->ws_pp};
+                    &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof,
+                    &c->nltc.eoff};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   if (c->cublas) cublasDestroy(c->cublas);
@@ -680,9 +683,9 @@ paw_status paw_apply_Sinv_approx(paw_handle c, paw_precision prec, const void *X
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
   if (prec == PAW_FP64)
-    op_Sinv<double>(c, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+    op_Sinv<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
   else
-    op_Sinv<float>(c, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+    op_Sinv<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
   return PAW_OK;
   PAW_TRY_END
 }
@@ -821,7 +824,7 @@ paw_status paw_lanczos_bounds(paw_handle c, int k, uint64_t seed, double *theta_
   double beta = 0.0;
   for (int j = 0; j < k; ++j) {
     op_H<double>(c, PAW_FP64, v, 1, Hv, 1, 1, s);
-    op_Sinv<double>(c, Hv, 1, w, 1, 1, s);
+    op_Sinv<double>(c, PAW_FP64, Hv, 1, w, 1, 1, s);
     op_S<double>(c, w, 1, Sw, 1, 1, s);
     const double a = column_reduce(c, true, v, 1, Sw, 1, nullptr, 1, s)[0];
     k_axpby<<<g, 256, 0, s>>>(M, 1.0, w, -a, v, -beta, vp, w);
@@ -897,11 +900,12 @@ paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int 
   if (c->nown_pairs > 0 && dE_dD) {
     if (prec == PAW_FP64) {
       c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
-      nl_project<double>(c, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
+      nl_project<double>(c, PAW_FP64, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
       k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N, dE_dD);
     } else {
       c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
-      nl_project<float>(c, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
+      // projector coefficients of the D_ij gradient stay in FP32 arithmetic
+      nl_project<float>(c, PAW_FP32, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
       k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N, dE_dD);
     }
     PAW_LAUNCH_CHECK("k_grad_D");
@@ -945,7 +949,8 @@ paw_status paw_sync_status(paw_handle c) {
   PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
   PAW_CUDA(cudaStreamSynchronize(c->last_stream));
   PAW_CUDA(cudaGetLastError());
-  PAW_REQUIRE(tc_read_status() == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+  const int st_cell = tc_read_status(), st_nl = nltc_read_status();
+  PAW_REQUIRE(st_cell == 0 && st_nl == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
   return PAW_OK;
   PAW_TRY_END
 }

@@ -21,7 +21,11 @@
 // records a status word, skips its epilogue, frees its tensor memory and exits.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
+#include "tc_ptx.cuh"
+#include "tc_stream.cuh"
 
 namespace pawfe {
 
@@ -34,144 +38,7 @@ constexpr int THREADS = 256;           // two gather threads per A row
 constexpr int STAGES = 2;
 constexpr uint32_t A_BYTES = MT * 128;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr uint64_t WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on the given phase parity: false after WAIT_NS nanoseconds.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (gtimer() - t0 > WAIT_NS) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-template <bool BF16>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                    uint32_t accum) {
-  if constexpr (BF16) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (SBO); LBO unused for this layout.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulate, A and B both TF32 (kind::tf32) or
-// both BF16 (kind::f16), both K-major, M x N.
-__host__ __device__ constexpr uint32_t make_idesc(bool bf16, int M, int N) {
-  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
+using namespace tcp;
 
 struct TcArgs {
   const uint8_t *Ht;       // tiled cell matrices
@@ -384,6 +251,68 @@ __global__ void k_tile_mats(const float *__restrict__ He, long long stride, int 
   *reinterpret_cast<uint4 *>(dst) = q;
 }
 
+// Persistent warp-specialised form (tc_stream.cuh) for 16-byte-aligned rows:
+// tile = (cell, 128 vectors), one accumulation round per N tile of H^e.
+template <bool BF>
+struct CellStream {
+  static constexpr int NW = 1, NEPI = 8;
+  static constexpr int S = BF ? 2 : 3;
+  static constexpr bool BF16 = BF;
+  static constexpr uint32_t B_MAX = 256u * 128u;
+  static constexpr int KR = BF ? 64 : 32;
+  int ntiles, ncols, vtiles, nc, ntile, ntiles_n, kchunks, ldx, ldy;
+  size_t cell_bytes;
+  const uint8_t *Ht;
+  const int *cell_dofs;
+  const float *X;
+  float *Y;
+  float alpha;
+  struct Tile {
+    int e, vt;
+  };
+  __device__ Tile tile(int t) const {
+    Tile T;
+    T.e = t / vtiles;
+    T.vt = t - T.e * vtiles;
+    return T;
+  }
+  __device__ int vt(const Tile &T) const { return T.vt; }
+  __device__ int nsub(const Tile &) const { return ntiles_n; }
+  __device__ int nchunks(const Tile &, int) const { return kchunks; }
+  __device__ int ncol(const Tile &, int) const { return ntile; }
+  __device__ uint32_t row_bytes(const Tile &T) const { return (uint32_t)min(MT, ncols - T.vt * MT) * 4u; }
+  __device__ const float *row(const Tile &T, int, int kc, int j, int) const {
+    const int k = kc * KR + j;
+    return k < nc ? X + (size_t)cell_dofs[(size_t)T.e * nc + k] * ldx + T.vt * MT : nullptr;
+  }
+  __device__ const uint8_t *bsrc(const Tile &T, int sub, int kc) const {
+    return Ht + (size_t)T.e * cell_bytes + ((size_t)sub * kchunks + kc) * ntile * 128;
+  }
+  __device__ uint32_t dcol(int) const { return 0; }
+  // Y[dof(n)][v] += alpha D[v][n]: coalesced FP32 reductions, one node row per warp instruction
+  __device__ void epilogue(const Tile &T, int sub, uint32_t tl, int q, int part, int lane, bool) const {
+    const int ng = ntile / 16, per = (ng + 1) / 2;
+    const int g_beg = part * per, g_end = min(ng, (part + 1) * per);
+    const int v = T.vt * MT + q * 32 + lane;
+    const int *dofs = cell_dofs + (size_t)T.e * nc + (size_t)sub * ntile;
+    const int nrem = nc - sub * ntile;   // nodes of this N tile that exist
+    for (int gi = g_beg; gi < g_end; ++gi) {
+      const int c0 = gi * 16;
+      int dd[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dd[j] = (c0 + j < nrem) ? dofs[c0 + j] : -1;
+      uint32_t rr[16];
+      tmem_ld16_nowait(tl + (uint32_t)c0, rr);
+      tmem_ld_wait();
+      if (v < ncols) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (dd[j] >= 0) atomicAdd(Y + (size_t)dd[j] * ldy + v, alpha * __uint_as_float(rr[j]));
+      }
+    }
+  }
+};
+
 }  // namespace
 
 static void tile_geometry(int nc, bool bf16, int &ntile, int &ntiles, int &kchunks) {
@@ -422,12 +351,54 @@ size_t tc_smem_bytes(int ntile, int kchunks, bool bf16) {
   return b < 80 * 1024 ? 80 * 1024 : b;
 }
 
+template <bool BF>
+static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx, float *Y, int ldy, int ncols,
+                        float alpha, cudaStream_t s) {
+  CellStream<BF> p;
+  p.vtiles = (ncols + MT - 1) / MT;
+  const int64_t nt = (int64_t)c->ncells * p.vtiles;
+  PAW_REQUIRE(nt < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many cell tiles");
+  p.ntiles = (int)nt;
+  p.ncols = ncols;
+  p.nc = c->nc;
+  p.ntile = T.ntile;
+  p.ntiles_n = T.ntiles;
+  p.kchunks = T.kchunks;
+  p.ldx = ldx;
+  p.ldy = ldy;
+  p.cell_bytes = T.cell_bytes;
+  p.Ht = T.He.as<uint8_t>();
+  p.cell_dofs = c->cell_dofs.as<int>();
+  p.X = X;
+  p.Y = Y;
+  p.alpha = alpha;
+  const size_t shm = tcs::Geo<CellStream<BF>>::SMEM;
+  PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<CellStream<BF>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)shm));
+  int dev = 0, nsm = 0;
+  PAW_CUDA(cudaGetDevice(&dev));
+  PAW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  void *st = nullptr;
+  PAW_CUDA(cudaGetSymbolAddress(&st, g_tc_status));
+  const int grid = std::max(1, std::min(p.ntiles, nsm));
+  tcs::k_tc_stream<CellStream<BF>><<<grid, tcs::threads_for(CellStream<BF>::NEPI), shm, s>>>(p, (int *)st);
+  PAW_LAUNCH_CHECK("k_tc_stream<cell>");
+}
+
 void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, float *Y, int ldy, int ncols,
                    float alpha, cudaStream_t s) {
   if (ncols <= 0) return;
   const bool bf16 = prec == PAW_BF16;
   tc_prepare(c, prec, s);
   TcMats &T = bf16 ? c->tc_bf16 : c->tc_tf32;
+  // rows of X copied with 16-byte cp.async: aligned base, pitch and vector range
+  if (reinterpret_cast<uintptr_t>(X) % 16 == 0 && ldx % 4 == 0 && ncols % 4 == 0 && T.ntile <= 256) {
+    if (bf16)
+      cell_stream<true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+    else
+      cell_stream<false>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+    return;
+  }
   TcArgs a;
   a.Ht = T.He.as<uint8_t>();
   a.cell_bytes = T.cell_bytes;

@@ -72,6 +72,24 @@ struct TcMats {
   size_t cell_bytes = 0;    // bytes of one cell (ntiles * kchunks chunks)
 };
 
+// Projector blocks pre-arranged for the tcgen05 nonlocal kernels (TF32,
+// 128-byte-swizzled K-major tiles, built once from the owner-cell values).
+struct NlTcMats {
+  DevBuf projB;     // projection B operand: per pair tile [K-chunk of owned nodes][pair x projector rows]
+  DevBuf projBs;    // the same with M_D^-1 of each node folded in
+  DevBuf expB;      // expansion B operand: per cell [node tile][K-chunk of pairs x projectors][node rows]
+  DevBuf eoff;      // int32 ncells+1: prefix of the expansion K-chunks of each cell
+  DevBuf mdo;       // M_D^-1 in owner order: nh * ntile floats per cell
+  DevBuf odof;      // DoF indices in owner order (int32, same layout)
+  int valid = 0;
+  int kc_own = 0;   // K-chunks (32 nodes) over the owned nodes
+  int ppt = 0;      // pairs per projection N tile (256 / npad)
+  int ppc = 0;      // pairs per expansion K-chunk (32 / npad)
+  int ntile = 0;    // owned nodes per expansion N tile (multiple of 16, <= 128)
+  int nh = 0;       // expansion N tiles per cell
+  int64_t exp_chunks = 0;
+};
+
 // Phase timing (paw_profile_enable / paw_profile_read)
 struct Profiler {
   bool on = false;
@@ -117,6 +135,7 @@ struct paw_context {
   pawfe::DevBuf wV;                           // ncells*nq: w_q detJ V_q (sum-factorised V^e)
   int wV_valid = 0;
   pawfe::TcMats tc_tf32, tc_bf16;
+  pawfe::NlTcMats nltc;
 
   // projectors: atom-major support entries
   int64_t nent = 0;                           // sum_a |supp_a| (node entries)
@@ -138,7 +157,7 @@ struct paw_context {
   // atom-pair Gram blocks G_ab = P^a^T M_D^-1 P^b for atoms with common support
   // nodes (CSR over atoms, a included); lets P^T Shat^-1 R follow from P^T M_D^-1 R
   pawfe::DevBuf gnb_off, gnb_atom;            // int32 natoms+1, ngpairs
-  pawfe::DevBuf Gfull;                        // FP64 ngpairs * npad * npad
+  pawfe::DevBuf Gfull, Gfull32;               // FP64 / FP32 ngpairs * npad * npad
   int64_t ngpairs = 0;
   std::vector<double> mdinv_h;                // 1 / M_D on the host
   // couplings (FP64, natoms*npj*npj)
@@ -171,17 +190,19 @@ void cell_apply_simt(paw_context *c, const T *mats, long long stride, const T *X
                      T *Y, int ldy, int ncols, double alpha, const double *colscale,
                      cudaStream_t s);
 // W[a] = coup_scale * coup[a] * P^a^T (rowscale .* X); W is natoms x npad x ncols
+// prec PAW_TF32 / PAW_BF16 with T = float: tensor-core (tcgen05, TF32 operands)
+// projection and expansion; otherwise SIMT in the arithmetic of T.
 template <typename T>
-void nl_project(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale,
+void nl_project(paw_context *c, paw_precision prec, const T *X, int ldx, int ncols, const T *rowscale,
                 const double *coup, double coup_scale, T *W, cudaStream_t s);
 // Y[dof] += colscale[j] * sum_a P^a W[a]   (owner-cell expansion, no atomics)
 template <typename T>
-void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, const double *colscale,
-               cudaStream_t s);
+void nl_expand(paw_context *c, paw_precision prec, const T *W, int ncols, T *Y, int ldy,
+               const double *colscale, cudaStream_t s);
 // Y = M_D^-1 (X - sum_a P^a W[a])
 template <typename T>
-void nl_sinv_out(paw_context *c, const T *W, int ncols, const T *X, int ldx, T *Y, int ldy,
-                 const T *mdinv, cudaStream_t s);
+void nl_sinv_out(paw_context *c, paw_precision prec, const T *W, int ncols, const T *X, int ldx, T *Y,
+                 int ldy, const T *mdinv, cudaStream_t s);
 // W[a] = (D_H[a] + cs[j] dS[a]) P^a^T X  (nonlocal part of H X - S X Lambda, cs = -Lambda)
 template <typename T>
 void nl_project_residual(paw_context *c, const T *X, int ldx, int ncols, const double *cs, T *W,
@@ -189,19 +210,30 @@ void nl_project_residual(paw_context *c, const T *X, int ldx, int ncols, const d
 // One projection per filter step: U = P^T M_D^-1 R_Y, W_S = Dsinv U and
 // W_H = alpha D_H (U - G W_S) = alpha D_H P^T Shat^-1 R_Y (G: atom-pair Gram blocks)
 template <typename T>
-void nl_project_filter(paw_context *c, const T *RY, int ldr, int ncols, const T *mdinv, double alpha,
-                       T *WS, T *WH, cudaStream_t s);
+void nl_project_filter(paw_context *c, paw_precision prec, const T *RY, int ldr, int ncols, const T *mdinv,
+                       double alpha, T *WS, T *WH, cudaStream_t s);
 // T = M_D^-1 (R_Y - sum_a P^a W_S[a]);
 // R_X = [-beta R_Y - gamma R_X + sum_a P^a W_H[a]] + c_j Y   with c_j = alpha Lambda_Y[j]
 // FP32: Y given as hi/lo FP32 words (lo may be NULL), c_j as chi + clo, exact-product sum.
-void nl_recurrence_f32(paw_context *c, const float *WS, const float *WH, int ncols, const float *RY,
-                       float *RX, float *Tout, int ldr, const float *mdinv, const float *Y0hi,
-                       const float *Y0lo, int ldy0, const float *chi, const float *clo, double beta,
-                       double gamma, cudaStream_t s);
+void nl_recurrence_f32(paw_context *c, paw_precision prec, const float *WS, const float *WH, int ncols,
+                       const float *RY, float *RX, float *Tout, int ldr, const float *mdinv,
+                       const float *Y0hi, const float *Y0lo, int ldy0, const float *chi, const float *clo,
+                       double beta, double gamma, cudaStream_t s);
 void nl_recurrence_f64(paw_context *c, const double *WS, const double *WH, int ncols,
                        const double *RY, double *RX, double *Tout, int ldr, const double *mdinv,
                        const double *Y0, int ldy0, const double *c64, double beta, double gamma,
                        cudaStream_t s);
+// tensor-core owner-cell kernels (nonlocal_tc.cu), T = float, TF32 operands
+bool nltc_supported(const paw_context *c);
+void nltc_prepare(paw_context *c, cudaStream_t s);
+// per-pair partials PP[k][al][v] = sum_o P[k][o][al] rowscale[o] X[o][v]
+void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
+                  cudaStream_t s);
+// expansion with the output stage of mode (EXP_ADD / EXP_SINV / EXP_RECURRENCE)
+struct ExpArgs;
+void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, const float *W2, cudaStream_t s);
+// 0: no bounded wait expired since the last read; 1: one did (cleared on read)
+int nltc_read_status();
 // FP64 sum-factorised local operator (sumfac.cu):
 // Y += alpha * (cK K^e + cV V^e + (cM + cMcol[j]) M^e) X, cell by cell with assembly
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
@@ -224,7 +256,7 @@ template <typename T>
 void op_S(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols,
           cudaStream_t s);
 template <typename T>
-void op_Sinv(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols,
+void op_Sinv(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols,
              cudaStream_t s);
 
 // tensor-core cell products (cell_tc.cu)

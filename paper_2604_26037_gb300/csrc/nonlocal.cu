@@ -5,7 +5,8 @@
 // block handles the p^3 owned nodes of one cell for a tile of vectors and the
 // (cell, atom) pairs k whose P^a is nonzero on those nodes (assembled values
 // P[k][o][al], padded to npad projectors):
-//   projection  U[a][al][v] += sum_o P[k][o][al] s(o) X[o][v]       (block-reduced, FP atomics)
+//   projection  U[k][al][v]  = sum_o P[k][o][al] s(o) X[o][v]       (per-pair partials,
+//               then a fixed-order sum over the pairs of each atom)
 //   coupling    W[a] = C[a] U[a]                                    (small dense npj x npj)
 //   expansion   S[o][v]      = sum_k sum_al P[k][o][al] W[a_k][al][v] (no atomics: rows are owned)
 // so each owned row is read once per pass instead of once per atom whose
@@ -21,6 +22,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "nonlocal_common.cuh"
 
 namespace pawfe {
 
@@ -49,12 +51,8 @@ constexpr int OWN_MAX = 512;   // p <= 8
 
 // Offsets of the owned nodes of cell e relative to its first owned DoF.
 __device__ __forceinline__ int64_t owned_table(int e, int n, int p, int N1, int *ooff, int own) {
-  for (int o = threadIdx.x; o < own; o += blockDim.x) {
-    const int a = o % p, b = (o / p) % p, cc = o / (p * p);
-    ooff[o] = a + N1 * (b + N1 * cc);
-  }
-  const int cx = e % n, cy = (e / n) % n, cz = e / (n * n);
-  return (int64_t)cx * p + (int64_t)N1 * ((int64_t)cy * p + (int64_t)N1 * ((int64_t)cz * p));
+  for (int o = threadIdx.x; o < own; o += blockDim.x) ooff[o] = owned_offset(o, p, N1);
+  return owned_base(e, n, p, N1);
 }
 
 // 4 consecutive elements, 16-byte aligned (one 16-byte access for float, two for double)
@@ -214,76 +212,44 @@ __global__ void k_own_couple(int npj, const T *__restrict__ U, const double *__r
 }
 
 // W_H[a] = scale * D_H[a] (U[a] - sum_b G_ab W_S[b])  (= scale D_H P^a^T Shat^-1 R)
+// accumulated in the arithmetic of T (FP32 for the FP32 / TF32 / BF16 filter)
 template <typename T, int NPAD>
 __global__ void k_own_couple_h(int npj, const int *__restrict__ goff, const int *__restrict__ gatom,
-                               const double *__restrict__ G, const T *__restrict__ U, const T *__restrict__ WS,
+                               const T *__restrict__ G, const T *__restrict__ U, const T *__restrict__ WS,
                                const double *__restrict__ DH, double scale, T *__restrict__ WH, int ncols) {
   const int a = blockIdx.x;
   const int v = blockIdx.y * blockDim.x + threadIdx.x;
   if (v >= ncols) return;
-  double u[NPAD];
+  T u[NPAD];
 #pragma unroll
-  for (int be = 0; be < NPAD; ++be) u[be] = (be < npj) ? (double)U[((size_t)a * NPAD + be) * ncols + v] : 0.0;
+  for (int be = 0; be < NPAD; ++be) u[be] = (be < npj) ? U[((size_t)a * NPAD + be) * ncols + v] : T(0);
   for (int s = goff[a]; s < goff[a + 1]; ++s) {
     const int b = gatom[s];
-    const double *Gs = G + (size_t)s * NPAD * NPAD;
-    double w[NPAD];
+    const T *Gs = G + (size_t)s * NPAD * NPAD;
+    T w[NPAD];
 #pragma unroll
-    for (int ga = 0; ga < NPAD; ++ga) w[ga] = (ga < npj) ? (double)WS[((size_t)b * NPAD + ga) * ncols + v] : 0.0;
+    for (int ga = 0; ga < NPAD; ++ga) w[ga] = (ga < npj) ? WS[((size_t)b * NPAD + ga) * ncols + v] : T(0);
 #pragma unroll
     for (int be = 0; be < NPAD; ++be) {
-      double t = 0.0;
+      T t = T(0);
 #pragma unroll
-      for (int ga = 0; ga < NPAD; ++ga) t += Gs[be * NPAD + ga] * w[ga];
+      for (int ga = 0; ga < NPAD; ++ga) t = fma(Gs[be * NPAD + ga], w[ga], t);
       u[be] -= t;
     }
   }
   const double *Da = DH + (size_t)a * npj * npj;
   for (int al = 0; al < NPAD; ++al) {
-    double w = 0.0;
+    T w = T(0);
     if (al < npj) {
 #pragma unroll
       for (int be = 0; be < NPAD; ++be)
-        if (be < npj) w += Da[al * npj + be] * u[be];
+        if (be < npj) w = fma(T(Da[al * npj + be]), u[be], w);
     }
-    WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * w);
+    WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * (double)w);
   }
 }
 
 // ------------------------------------------------------------------ expansion
-// fl32(b + c y) for c = ch + cl, y = yh + yl, with error-free FP32 steps.
-__device__ __forceinline__ float add_product_df(float b, float ch, float cl, float yh, float yl) {
-  // explicit round-to-nearest operations: no contraction into FMA may alter the two-sum
-  const float th = __fmul_rn(ch, yh);
-  const float te = fmaf(ch, yh, -th);                    // exact error of ch * yh
-  const float tl = fmaf(ch, yl, fmaf(cl, yh, te));
-  const float s = __fadd_rn(b, th);                      // two-sum of b and th
-  const float bp = __fsub_rn(s, b);
-  const float err = __fadd_rn(__fsub_rn(b, __fsub_rn(s, bp)), __fsub_rn(th, bp));
-  return __fadd_rn(s, __fadd_rn(err, tl));
-}
-
-constexpr int EXP_ADD = 0, EXP_SINV = 1, EXP_RECURRENCE = 2;
-
-struct ExpArgs {
-  int n, p, N1;
-  const int *own_off, *own_atom;
-  int ncols;
-  const double *cs;              // ADD: per-column factor (may be NULL)
-  const void *Xin;               // SINV: X; RECURRENCE: R_Y
-  int ldx;
-  void *Y;                       // ADD/SINV output; RECURRENCE: T
-  int ldy;
-  const void *mdinv;
-  void *RX;                      // RECURRENCE: R_X (ld = ldx)
-  const void *Y0, *Y0lo;         // RECURRENCE: Y (FP64) or its FP32 hi/lo split
-  int ldy0;
-  const double *c64;             // FP64 path: alpha * Lambda_Y per column
-  const float *chi, *clo;        // FP32 path: the same, split in two FP32 words
-  double beta, gamma;
-  int vec_ok;                    // every row pointer above 16-byte aligned (set by own_expand)
-};
-
 // Expansion with a fused output stage.  W of every pair of the cell is staged
 // in shared memory (at most 48 pairs); a thread owns 4 vectors of one node row
 // at a time.
@@ -486,12 +452,28 @@ static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T
 
 // U = P^T (rowscale .* X) into c->ws_partial (natoms x npad x ncols): per-pair
 // partials, then a fixed-order sum per atom (deterministic, no atomics)
+// tensor-core form: FP32 data, TF32 or BF16 filter precision, supported layout
 template <typename T>
-static T *project_U(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, cudaStream_t s) {
+static bool use_tc(const paw_context *c, paw_precision prec) {
+  return sizeof(T) == 4 && (prec == PAW_TF32 || prec == PAW_BF16) && nltc_supported(c);
+}
+
+template <typename T>
+static T *project_U(paw_context *c, paw_precision prec, const T *X, int ldx, int ncols, const T *rowscale,
+                    cudaStream_t s) {
   const size_t ub = sizeof(T) * (size_t)c->natoms * c->npad * ncols;
   c->ws_partial.ensure(ub, &c->dev_bytes);
   c->ws_pp.ensure(sizeof(T) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
   T *U = c->ws_partial.as<T>(), *PP = c->ws_pp.as<T>();
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc<T>(c, prec)) {
+      nltc_project(c, X, ldx, ncols, rowscale, PP, s);
+      dim3 g((ncols + 31) / 32, c->npad, c->natoms);
+      k_pair_reduce<T><<<g, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
+      PAW_LAUNCH_CHECK("k_pair_reduce");
+      return U;
+    }
+  }
   if (c->npad == 16)
     project_impl<T, 16>(c, X, ldx, ncols, rowscale, PP, s);
   else
@@ -514,38 +496,53 @@ static void couple(paw_context *c, const T *U, const double *C, const double *C2
 }
 
 template <typename T>
-void nl_project(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, const double *coup,
-                double coup_scale, T *W, cudaStream_t s) {
+void nl_project(paw_context *c, paw_precision prec, const T *X, int ldx, int ncols, const T *rowscale,
+                const double *coup, double coup_scale, T *W, cudaStream_t s) {
   if (c->nown_pairs == 0 || ncols <= 0) return;
-  const T *U = project_U<T>(c, X, ldx, ncols, rowscale, s);
+  const T *U = project_U<T>(c, prec, X, ldx, ncols, rowscale, s);
   couple<T>(c, U, coup, nullptr, nullptr, coup_scale, W, ncols, s);
 }
 
 template <typename T>
 void nl_project_residual(paw_context *c, const T *X, int ldx, int ncols, const double *cs, T *W, cudaStream_t s) {
   if (c->nown_pairs == 0 || ncols <= 0) return;
-  const T *U = project_U<T>(c, X, ldx, ncols, nullptr, s);
+  const T *U = project_U<T>(c, PAW_FP64, X, ldx, ncols, nullptr, s);
   couple<T>(c, U, c->DH64.as<double>(), c->DS64.as<double>(), cs, 1.0, W, ncols, s);
 }
 
+// atom-pair Gram blocks in the element type of the filter
 template <typename T>
-void nl_project_filter(paw_context *c, const T *RY, int ldr, int ncols, const T *mdinv, double alpha, T *WS, T *WH,
-                       cudaStream_t s) {
+static const T *gram(paw_context *c);
+template <>
+const double *gram<double>(paw_context *c) { return c->Gfull.as<double>(); }
+template <>
+const float *gram<float>(paw_context *c) { return c->Gfull32.as<float>(); }
+
+template <typename T>
+void nl_project_filter(paw_context *c, paw_precision prec, const T *RY, int ldr, int ncols, const T *mdinv,
+                       double alpha, T *WS, T *WH, cudaStream_t s) {
   if (c->nown_pairs == 0 || ncols <= 0) return;
-  const T *U = project_U<T>(c, RY, ldr, ncols, mdinv, s);
+  const T *U = project_U<T>(c, prec, RY, ldr, ncols, mdinv, s);
   couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, WS, ncols, s);
   dim3 g2(c->natoms, (ncols + 63) / 64);
+  const T *G = gram<T>(c);
   if (c->npad == 16)
-    k_own_couple_h<T, 16><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(),
-                                             c->Gfull.as<double>(), U, WS, c->DH64.as<double>(), alpha, WH, ncols);
+    k_own_couple_h<T, 16><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), G, U, WS,
+                                             c->DH64.as<double>(), alpha, WH, ncols);
   else
-    k_own_couple_h<T, 32><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(),
-                                             c->Gfull.as<double>(), U, WS, c->DH64.as<double>(), alpha, WH, ncols);
+    k_own_couple_h<T, 32><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), G, U, WS,
+                                             c->DH64.as<double>(), alpha, WH, ncols);
   PAW_LAUNCH_CHECK("k_own_couple_h");
 }
 
 template <typename T, int MODE>
-static void own_expand(paw_context *c, ExpArgs A, const T *W1, const T *W2, cudaStream_t s) {
+static void own_expand(paw_context *c, paw_precision prec, ExpArgs A, const T *W1, const T *W2, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc<T>(c, prec)) {
+      nltc_expand(c, MODE, A, W1, W2, s);
+      return;
+    }
+  }
   constexpr int VT = ExpCfg<T>::VT;
   const size_t y0e = (sizeof(T) == 4) ? sizeof(float) : sizeof(double);
   A.vec_ok = aligned16(A.Y, A.ldy * sizeof(T)) && aligned16(A.Xin, A.ldx * sizeof(T)) &&
@@ -580,7 +577,8 @@ static ExpArgs exp_args(paw_context *c, int ncols) {
 }
 
 template <typename T>
-void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, const double *colscale, cudaStream_t s) {
+void nl_expand(paw_context *c, paw_precision prec, const T *W, int ncols, T *Y, int ldy, const double *colscale,
+               cudaStream_t s) {
   if (c->nown_pairs == 0 || ncols <= 0) return;
   ExpArgs A = exp_args(c, ncols);
   A.Y = Y;
@@ -588,12 +586,12 @@ void nl_expand(paw_context *c, const T *W, int ncols, T *Y, int ldy, const doubl
   A.ldx = ldy;
   A.ldy0 = 4;
   A.cs = colscale;
-  own_expand<T, EXP_ADD>(c, A, W, nullptr, s);
+  own_expand<T, EXP_ADD>(c, prec, A, W, nullptr, s);
 }
 
 template <typename T>
-void nl_sinv_out(paw_context *c, const T *W, int ncols, const T *X, int ldx, T *Y, int ldy, const T *mdinv,
-                 cudaStream_t s) {
+void nl_sinv_out(paw_context *c, paw_precision prec, const T *W, int ncols, const T *X, int ldx, T *Y, int ldy,
+                 const T *mdinv, cudaStream_t s) {
   ExpArgs A = exp_args(c, ncols);
   A.Xin = X;
   A.ldx = ldx;
@@ -601,12 +599,13 @@ void nl_sinv_out(paw_context *c, const T *W, int ncols, const T *X, int ldx, T *
   A.ldy = ldy;
   A.ldy0 = 4;
   A.mdinv = mdinv;
-  own_expand<T, EXP_SINV>(c, A, W, nullptr, s);
+  own_expand<T, EXP_SINV>(c, prec, A, W, nullptr, s);
 }
 
-void nl_recurrence_f32(paw_context *c, const float *WS, const float *WH, int ncols, const float *RY, float *RX,
-                       float *Tout, int ldr, const float *mdinv, const float *Y0hi, const float *Y0lo, int ldy0,
-                       const float *chi, const float *clo, double beta, double gamma, cudaStream_t s) {
+void nl_recurrence_f32(paw_context *c, paw_precision prec, const float *WS, const float *WH, int ncols,
+                       const float *RY, float *RX, float *Tout, int ldr, const float *mdinv, const float *Y0hi,
+                       const float *Y0lo, int ldy0, const float *chi, const float *clo, double beta, double gamma,
+                       cudaStream_t s) {
   ExpArgs A = exp_args(c, ncols);
   A.Xin = RY;
   A.ldx = ldr;
@@ -621,7 +620,7 @@ void nl_recurrence_f32(paw_context *c, const float *WS, const float *WH, int nco
   A.clo = clo;
   A.beta = beta;
   A.gamma = gamma;
-  own_expand<float, EXP_RECURRENCE>(c, A, WS, WH, s);
+  own_expand<float, EXP_RECURRENCE>(c, prec, A, WS, WH, s);
 }
 
 void nl_recurrence_f64(paw_context *c, const double *WS, const double *WH, int ncols, const double *RY, double *RX,
@@ -639,24 +638,26 @@ void nl_recurrence_f64(paw_context *c, const double *WS, const double *WH, int n
   A.c64 = c64;
   A.beta = beta;
   A.gamma = gamma;
-  own_expand<double, EXP_RECURRENCE>(c, A, WS, WH, s);
+  own_expand<double, EXP_RECURRENCE>(c, PAW_FP64, A, WS, WH, s);
 }
 
-template void nl_project<double>(paw_context *, const double *, int, int, const double *, const double *,
-                                 double, double *, cudaStream_t);
-template void nl_project<float>(paw_context *, const float *, int, int, const float *, const double *,
-                                double, float *, cudaStream_t);
+template void nl_project<double>(paw_context *, paw_precision, const double *, int, int, const double *,
+                                 const double *, double, double *, cudaStream_t);
+template void nl_project<float>(paw_context *, paw_precision, const float *, int, int, const float *,
+                                const double *, double, float *, cudaStream_t);
 template void nl_project_residual<double>(paw_context *, const double *, int, int, const double *, double *,
                                           cudaStream_t);
-template void nl_project_filter<double>(paw_context *, const double *, int, int, const double *, double, double *,
-                                        double *, cudaStream_t);
-template void nl_project_filter<float>(paw_context *, const float *, int, int, const float *, double, float *,
-                                       float *, cudaStream_t);
-template void nl_expand<double>(paw_context *, const double *, int, double *, int, const double *, cudaStream_t);
-template void nl_expand<float>(paw_context *, const float *, int, float *, int, const double *, cudaStream_t);
-template void nl_sinv_out<double>(paw_context *, const double *, int, const double *, int, double *, int,
-                                  const double *, cudaStream_t);
-template void nl_sinv_out<float>(paw_context *, const float *, int, const float *, int, float *, int,
+template void nl_project_filter<double>(paw_context *, paw_precision, const double *, int, int, const double *,
+                                        double, double *, double *, cudaStream_t);
+template void nl_project_filter<float>(paw_context *, paw_precision, const float *, int, int, const float *,
+                                       double, float *, float *, cudaStream_t);
+template void nl_expand<double>(paw_context *, paw_precision, const double *, int, double *, int, const double *,
+                                cudaStream_t);
+template void nl_expand<float>(paw_context *, paw_precision, const float *, int, float *, int, const double *,
+                               cudaStream_t);
+template void nl_sinv_out<double>(paw_context *, paw_precision, const double *, int, const double *, int, double *,
+                                  int, const double *, cudaStream_t);
+template void nl_sinv_out<float>(paw_context *, paw_precision, const float *, int, const float *, int, float *, int,
                                  const float *, cudaStream_t);
 
 }  // namespace pawfe
@@ -715,7 +716,7 @@ static void sinv_noalloc(paw_context *c, const T *X, int ldx, T *Y, int ldy, int
   k_pair_reduce<T><<<g, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
   PAW_LAUNCH_CHECK("k_pair_reduce");
   couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, W, ncols, s);
-  nl_sinv_out<T>(c, W, ncols, X, ldx, Y, ldy, mdinv, s);
+  nl_sinv_out<T>(c, (sizeof(T) == 8) ? PAW_FP64 : PAW_FP32, W, ncols, X, ldx, Y, ldy, mdinv, s);
 }
 
 }  // namespace pawfe

@@ -198,8 +198,8 @@ void op_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy
   local_H<T>(c, prec, X, ldx, Y, ldy, ncols, 1.0, s);
   if (c->nown_pairs > 0) {
     c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
-    nl_project<T>(c, X, ldx, ncols, nullptr, c->DH64.as<double>(), 1.0, c->ws_W.as<T>(), s);
-    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, nullptr, s);
+    nl_project<T>(c, prec, X, ldx, ncols, nullptr, c->DH64.as<double>(), 1.0, c->ws_W.as<T>(), s);
+    nl_expand<T>(c, prec, c->ws_W.as<T>(), ncols, Y, ldy, nullptr, s);
   }
 }
 
@@ -212,20 +212,21 @@ void op_S(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStr
     cell_apply_simt<T>(c, MeMats<T>(c), 0, X, ldx, Y, ldy, ncols, 1.0, nullptr, s);
   if (c->nown_pairs > 0) {
     c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
-    nl_project<T>(c, X, ldx, ncols, nullptr, c->DS64.as<double>(), 1.0, c->ws_W.as<T>(), s);
-    nl_expand<T>(c, c->ws_W.as<T>(), ncols, Y, ldy, nullptr, s);
+    const paw_precision prec = sizeof(T) == 8 ? PAW_FP64 : PAW_FP32;
+    nl_project<T>(c, prec, X, ldx, ncols, nullptr, c->DS64.as<double>(), 1.0, c->ws_W.as<T>(), s);
+    nl_expand<T>(c, prec, c->ws_W.as<T>(), ncols, Y, ldy, nullptr, s);
   }
 }
 
 template <typename T>
-void op_Sinv(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStream_t s) {
+void op_Sinv(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStream_t s) {
   if (c->nown_pairs == 0) {
     scale_rows<T>(X, ldx, Y, ldy, c->ndof, ncols, MdInv<T>(c), s);
     return;
   }
   c->ws_W.ensure(sizeof(T) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
-  nl_project<T>(c, X, ldx, ncols, MdInv<T>(c), c->DSinv64.as<double>(), 1.0, c->ws_W.as<T>(), s);
-  nl_sinv_out<T>(c, c->ws_W.as<T>(), ncols, X, ldx, Y, ldy, MdInv<T>(c), s);
+  nl_project<T>(c, prec, X, ldx, ncols, MdInv<T>(c), c->DSinv64.as<double>(), 1.0, c->ws_W.as<T>(), s);
+  nl_sinv_out<T>(c, prec, c->ws_W.as<T>(), ncols, X, ldx, Y, ldy, MdInv<T>(c), s);
 }
 
 template void local_H<double>(paw_context *, paw_precision, const double *, int, double *, int, int, double,
@@ -236,7 +237,8 @@ template void op_H<double>(paw_context *, paw_precision, const double *, int, do
 template void op_H<float>(paw_context *, paw_precision, const float *, int, float *, int, int, cudaStream_t);
 template void op_S<double>(paw_context *, const double *, int, double *, int, int, cudaStream_t);
 template void op_S<float>(paw_context *, const float *, int, float *, int, int, cudaStream_t);
-template void op_Sinv<double>(paw_context *, const double *, int, double *, int, int, cudaStream_t);
-template void op_Sinv<float>(paw_context *, const float *, int, float *, int, int, cudaStream_t);
+template void op_Sinv<double>(paw_context *, paw_precision, const double *, int, double *, int, int,
+                              cudaStream_t);
+template void op_Sinv<float>(paw_context *, paw_precision, const float *, int, float *, int, int, cudaStream_t);
 
 }  // namespace pawfe

@@ -617,6 +617,9 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
     PAW_CUDA(cudaMemcpy(c->gnb_off.ptr, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
     PAW_CUDA(cudaMemcpy(c->gnb_atom.ptr, gatom.data(), sizeof(int) * gatom.size(), cudaMemcpyHostToDevice));
     PAW_CUDA(cudaMemcpy(c->Gfull.ptr, Gf.data(), sizeof(double) * Gf.size(), cudaMemcpyHostToDevice));
+    std::vector<float> Gf32(Gf.begin(), Gf.end());
+    c->Gfull32.ensure(sizeof(float) * std::max<size_t>(1, Gf32.size()), &c->dev_bytes);
+    PAW_CUDA(cudaMemcpy(c->Gfull32.ptr, Gf32.data(), sizeof(float) * Gf32.size(), cudaMemcpyHostToDevice));
   }
 
   // ---- G_a

@@ -1,0 +1,360 @@
+// Persistent, warp-specialised tcgen05 pipeline for the dense contractions of
+// the filter (projector blocks, cell matrices).
+//
+// One CTA per SM walks a static list of tiles (tile t, t + gridDim.x, ...).
+// A tile is one or more accumulation rounds
+//     D (128 vectors x N) = A (128 vectors x K) . B (N x K)^T
+// into a double-buffered FP32 accumulator in tensor memory (2 x 256 columns),
+// so the epilogue of one round overlaps the MMAs of the next.
+//
+// The rows of A are contiguous 128-vector slices of a row-major block (a node
+// row of a DoF-major multivector, or a projector row of the atom-major
+// coefficients).  Roles:
+//   warp 0        loader: the K rows of a chunk with warp-wide cp.async (lane l
+//                 copies bytes 16 l .. 16 l + 15 of every row) into a raw
+//                 [K][128] FP32 stage, the pre-arranged B chunk with one
+//                 cp.async.bulk (small bulk copies issued by one warp cap the
+//                 bandwidth far below HBM; 16-byte cp.async from one warp does not)
+//   warp 1        MMA: lane 0 issues tcgen05.mma (4 per 128-byte K-chunk);
+//                 the warp allocates and frees the tensor memory
+//   warps 2..5    transposers: thread = vector row; raw FP32 -> K-major
+//                 128-byte-swizzled A operand (TF32 or BF16)
+//   warps 6..     epilogue: warp w reads TMEM lane quarter w % 4
+// Barriers per stage s: full[s] (copies landed: 32 cp.async arrivals, one
+// arrival with the B byte count), afull[s] (A written by
+// the 128 transposer threads), empty[s] (MMAs done, tcgen05.commit); per
+// accumulator b: accf[b] (commit) and acce[b] (one arrival per epilogue warp).
+//
+// Every wait is bounded (2 s) and gives up early once another role has given
+// up (a shared abort word).  The CTA then lets its bulk copies land, drains
+// its MMAs, frees the tensor memory and records the failure in *status.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "tc_ptx.cuh"
+
+namespace pawfe {
+namespace tcs {
+
+using namespace tcp;
+
+constexpr int MT = 128;                       // vectors per tile = MMA M
+constexpr uint32_t ROW_BYTES = MT * 4;        // one raw A row
+constexpr uint32_t A_BYTES = MT * 128;        // one swizzled A chunk
+constexpr uint32_t TMEM_COLS = 512;           // two accumulators of 256 columns
+constexpr int WARP_LOAD = 0, WARP_MMA = 1, WARP_XP0 = 2, NXP = 4, WARP_EPI0 = 6;
+
+__host__ __device__ constexpr int threads_for(int nepi) { return 32 * (WARP_EPI0 + nepi); }
+
+struct Shared {
+  uint64_t full[4], afull[4], empty[4], accf[2], acce[2], drain;
+  uint64_t mask[4][2];   // live A rows of each stage and operand (bit j: row j copied)
+  uint32_t taddr;
+  int abort;
+};
+
+template <class P>
+struct Geo {
+  static constexpr int KR = P::BF16 ? 64 : 32;                  // A rows (K elements) per chunk
+  static constexpr uint32_t RAW = KR * ROW_BYTES;               // raw rows of one operand
+  static constexpr uint32_t STAGE = P::NW * (RAW + A_BYTES) + P::B_MAX;
+  // at least 120 KB: one CTA per SM, so that its 512 TMEM columns are always free
+  static constexpr size_t SMEM0 = 1024 + (size_t)P::S * STAGE + sizeof(Shared);
+  static constexpr size_t SMEM = SMEM0 < 120 * 1024 ? 120 * 1024 : SMEM0;
+  static_assert(P::B_MAX % 1024 == 0, "B stage must keep 1024-byte alignment");
+  static_assert(P::S >= 2 && P::S <= 4 && P::NW >= 1 && P::NW <= 2, "stage / operand counts");
+  static_assert(P::NEPI % 4 == 0, "epilogue warps come in lane-quarter groups");
+};
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+  return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// Bounded wait that also returns false as soon as another role has given up.
+// Warps that go on to warp-collective instructions call warp_wait instead,
+// so that all 32 lanes take the same decision.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (gtimer() - t0 > WAIT_NS) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// lane 0 waits, the warp follows its result
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = wait_or_abort(bar, parity, abort) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <class P>
+__device__ __forceinline__ uint8_t *stage_raw(uint8_t *base, int s, int w) {
+  return base + (size_t)s * Geo<P>::STAGE + (size_t)w * Geo<P>::RAW;
+}
+template <class P>
+__device__ __forceinline__ uint8_t *stage_A(uint8_t *base, int s, int w) {
+  return base + (size_t)s * Geo<P>::STAGE + (size_t)P::NW * Geo<P>::RAW + (size_t)w * A_BYTES;
+}
+template <class P>
+__device__ __forceinline__ uint8_t *stage_B(uint8_t *base, int s) {
+  return base + (size_t)s * Geo<P>::STAGE + (size_t)P::NW * (Geo<P>::RAW + A_BYTES);
+}
+
+// ------------------------------------------------------------------ roles
+template <class P>
+__device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane) {
+  constexpr int KR = Geo<P>::KR, S = P::S;
+  volatile int *abort = &sh->abort;
+  uint32_t g = 0;
+  bool run = __shfl_sync(0xffffffffu, *abort, 0) == 0;   // warp-uniform
+  for (int t = blockIdx.x; run && t < p.ntiles; t += gridDim.x) {
+    const auto T = p.tile(t);
+    const int ns = p.nsub(T);
+    const uint32_t rbytes = p.row_bytes(T);
+    for (int sub = 0; run && sub < ns; ++sub) {
+      const int nk = p.nchunks(T, sub);
+      const uint32_t bbytes = (uint32_t)p.ncol(T, sub) * 128u;
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = (int)(g % S);
+        const uint32_t u = g / S;
+        if (g >= (uint32_t)S && !warp_wait(smem_u32(&sh->empty[s]), (u - 1) & 1u, abort, lane)) {
+          run = false;
+          break;
+        }
+        const float *src[P::NW][KR / 32];
+#pragma unroll
+        for (int w = 0; w < P::NW; ++w) {
+          uint64_t m = 0;
+#pragma unroll
+          for (int jj = 0; jj < KR / 32; ++jj) {
+            src[w][jj] = p.row(T, sub, kc, jj * 32 + lane, w);
+            const uint32_t b = __ballot_sync(0xffffffffu, src[w][jj] != nullptr);
+            m |= (uint64_t)b << (32 * jj);
+          }
+          if (lane == 0) sh->mask[s][w] = m;
+        }
+        const uint32_t full = smem_u32(&sh->full[s]);
+        if (lane == 0) {
+          mbar_arrive_tx(full, bbytes);   // release: the masks above
+          bulk_g2s(smem_u32(stage_B<P>(base, s)), p.bsrc(T, sub, kc), bbytes, full);
+        }
+        const bool lok = (uint32_t)lane * 16u < rbytes;   // this lane's 16 bytes lie inside the vector range
+#pragma unroll
+        for (int w = 0; w < P::NW; ++w)
+#pragma unroll
+          for (int jj = 0; jj < KR / 32; ++jj) {
+            const uint32_t dst0 = smem_u32(stage_raw<P>(base, s, w)) + (uint32_t)(jj * 32) * ROW_BYTES + lane * 16u;
+            for (int j = 0; j < 32; ++j) {
+              const float *rp = reinterpret_cast<const float *>(
+                  __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(src[w][jj]), j));
+              if (rp != nullptr && lok)
+                cp_async16(dst0 + (uint32_t)j * ROW_BYTES, reinterpret_cast<const uint8_t *>(rp) + lane * 16);
+            }
+          }
+        cp_async_arrive(full);
+      }
+    }
+  }
+  // let every copy in flight land before the CTA can exit
+  cp_async_wait_all();
+  if (lane == 0) {
+    const uint32_t issued = g;
+    for (int s = 0; s < S; ++s) {
+      if ((uint32_t)s >= issued) break;
+      const uint32_t last = ((issued - 1 - (uint32_t)s) / S) * S + (uint32_t)s;   // last chunk on stage s
+      mbar_wait(smem_u32(&sh->full[s]), (last / S) & 1u);
+    }
+  }
+  __syncwarp();
+}
+
+template <class P>
+__device__ void role_transpose(const P &p, uint8_t *base, Shared *sh, int r) {
+  constexpr int S = P::S;
+  volatile int *abort = &sh->abort;
+  uint32_t g = 0;
+  bool run = !*abort;
+  for (int t = blockIdx.x; run && t < p.ntiles; t += gridDim.x) {
+    const auto T = p.tile(t);
+    const int ns = p.nsub(T);
+    const bool vok = p.vt(T) * MT + r < p.ncols;
+    for (int sub = 0; run && sub < ns; ++sub) {
+      const int nk = p.nchunks(T, sub);
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = (int)(g % S);
+        const uint32_t u = g / S;
+        if (!wait_or_abort(smem_u32(&sh->full[s]), u & 1u, abort)) {
+          run = false;
+          break;
+        }
+#pragma unroll
+        for (int w = 0; w < P::NW; ++w) {
+          const uint64_t m = vok ? sh->mask[s][w] : 0ull;
+          const float *raw = reinterpret_cast<const float *>(stage_raw<P>(base, s, w));
+          uint8_t *A = stage_A<P>(base, s, w);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint4 q;
+            if constexpr (P::BF16) {
+              uint32_t h[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int j = c * 8 + 2 * i;
+                const float x0 = ((m >> j) & 1ull) ? raw[j * MT + r] : 0.f;
+                const float x1 = ((m >> (j + 1)) & 1ull) ? raw[(j + 1) * MT + r] : 0.f;
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+                h[i] = *reinterpret_cast<uint32_t *>(&b2);
+              }
+              q = make_uint4(h[0], h[1], h[2], h[3]);
+            } else {
+              uint32_t h[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int j = c * 4 + i;
+                h[i] = to_tf32(((m >> j) & 1ull) ? raw[j * MT + r] : 0.f);
+              }
+              q = make_uint4(h[0], h[1], h[2], h[3]);
+            }
+            *reinterpret_cast<uint4 *>(A + sw128_off(r, c)) = q;
+          }
+        }
+        fence_proxy_async();
+        mbar_arrive(smem_u32(&sh->afull[s]));
+      }
+    }
+  }
+}
+
+template <class P>
+__device__ void role_mma(const P &p, uint8_t *base, Shared *sh, uint32_t tmem) {
+  constexpr int S = P::S;
+  volatile int *abort = &sh->abort;
+  uint32_t g = 0, tc = 0;
+  bool run = !*abort;
+  for (int t = blockIdx.x; run && t < p.ntiles; t += gridDim.x) {
+    const auto T = p.tile(t);
+    const int ns = p.nsub(T);
+    for (int sub = 0; run && sub < ns; ++sub, ++tc) {
+      const int b = (int)(tc & 1u);
+      const uint32_t ub = tc >> 1;
+      if (tc >= 2 && !wait_or_abort(smem_u32(&sh->acce[b]), (ub - 1) & 1u, abort)) {
+        run = false;
+        break;
+      }
+      tc_fence_after();
+      const int nk = p.nchunks(T, sub);
+      const uint32_t idesc = make_idesc(P::BF16, MT, p.ncol(T, sub));
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = (int)(g % S);
+        const uint32_t u = g / S;
+        if (!wait_or_abort(smem_u32(&sh->afull[s]), u & 1u, abort)) {
+          run = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t bd = sw128_desc(smem_u32(stage_B<P>(base, s)));
+#pragma unroll
+        for (int w = 0; w < P::NW; ++w) {
+          const uint64_t ad = sw128_desc(smem_u32(stage_A<P>(base, s, w)));
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            mma<P::BF16>(tmem + (uint32_t)(b * 256) + p.dcol(w), ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j),
+                         idesc, (kc | j) != 0);
+        }
+        mma_commit(smem_u32(&sh->empty[s]));
+      }
+      if (!run) break;
+      mma_commit(smem_u32(&sh->accf[b]));
+    }
+  }
+  // no MMA may still be writing the tensor memory when it is freed
+  mma_commit(smem_u32(&sh->drain));
+  mbar_wait(smem_u32(&sh->drain), 0);
+}
+
+template <class P>
+__device__ void role_epilogue(const P &p, Shared *sh, uint32_t tmem, int warp, int lane) {
+  volatile int *abort = &sh->abort;
+  const int q = warp & 3, part = (warp - WARP_EPI0) >> 2;
+  uint32_t tc = 0;
+  bool run = __shfl_sync(0xffffffffu, *abort, 0) == 0;   // warp-uniform
+  for (int t = blockIdx.x; run && t < p.ntiles; t += gridDim.x) {
+    const auto T = p.tile(t);
+    const int ns = p.nsub(T);
+    for (int sub = 0; sub < ns; ++sub, ++tc) {
+      const int b = (int)(tc & 1u);
+      const uint32_t ub = tc >> 1;
+      if (!warp_wait(smem_u32(&sh->accf[b]), ub & 1u, abort, lane)) {
+        run = false;
+        break;
+      }
+      tc_fence_after();
+      p.epilogue(T, sub, tmem + (uint32_t)(b * 256) + ((uint32_t)(q * 32) << 16), q, part, lane,
+                 p.nchunks(T, sub) > 0);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sh->acce[b]));
+    }
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const P p, int *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = align1024(smem_raw);
+  Shared *sh = reinterpret_cast<Shared *>(base + (size_t)P::S * Geo<P>::STAGE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P::S; ++s) {
+      mbar_init(smem_u32(&sh->full[s]), 33);   // 32 cp.async arrivals + the B byte count
+      mbar_init(smem_u32(&sh->afull[s]), NXP * 32);
+      mbar_init(smem_u32(&sh->empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&sh->accf[b]), 1);
+      mbar_init(smem_u32(&sh->acce[b]), P::NEPI);
+    }
+    mbar_init(smem_u32(&sh->drain), 1);
+    sh->abort = (*reinterpret_cast<volatile int *>(status) != 0) ? 1 : 0;   // an earlier CTA gave up
+    fence_barrier_init();
+    fence_proxy_async();
+  }
+  if (warp == WARP_MMA) {
+    __syncwarp();
+    tmem_alloc(smem_u32(&sh->taddr), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh->taddr;
+
+  if (warp == WARP_LOAD) {
+    role_loader<P>(p, base, sh, lane);
+  } else if (warp == WARP_MMA) {
+    if (lane == 0) role_mma<P>(p, base, sh, tmem);
+    __syncwarp();
+  } else if (warp < WARP_EPI0) {
+    role_transpose<P>(p, base, sh, threadIdx.x - 32 * WARP_XP0);
+  } else {
+    role_epilogue<P>(p, sh, tmem, warp, lane);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == WARP_MMA) {
+    __syncwarp();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && sh->abort) atomicExch(status, 1);
+}
+
+}  // namespace tcs
+}  // namespace pawfe
