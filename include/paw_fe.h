@@ -215,6 +215,74 @@ paw_status paw_cheb_filter(paw_handle h, paw_precision prec, const double *X_in,
                            int ldx, const double *lambda_in, int ncols, int degree,
                            paw_bounds bounds, double *X_out, int ldo, void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Algorithm 2 for many independent instances at once (uneven meshes, FE
+ * degrees, atom counts and block widths; the paper filters blocks of one
+ * problem independently, Sec. 4.4 compute-communication overlap, and this
+ * extends the same independence to separate problems).  Every launch of every
+ * instance is captured once into a single CUDA graph: instances run on up to
+ * `streams` concurrent branches of the graph, and each call replays the whole
+ * batch with one cudaGraphLaunch.  The graph is recaptured when a problem's
+ * pointers, sizes, degree, bounds or the precision change; eigenvalue
+ * estimates (lambda_in) may change freely between calls.
+ *
+ * Autotuning (options.autotune = 1) happens on the first call and after a
+ * recapture: for every instance the tensor-core kernel family (persistent
+ * warp-specialised vs one CTA per tile) is timed on a short filter of its
+ * first block; then the branch count (1, 2, 4, 8 up to `streams`) is timed on
+ * the whole captured graph, the CTAs of persistent launches being capped at
+ * SMs / branches.  The fastest combination is kept (paw_batch_tuning).
+ *
+ * The handles are not owned by the batch; they must stay valid until
+ * paw_batch_destroy and must not be used concurrently by other calls. */
+typedef struct paw_batch_s *paw_batch;
+
+typedef struct {
+  const double *X_in;       /* device FP64 ndof x ncols (ld ldx)                 */
+  int32_t ldx;
+  const double *lambda_in;  /* host FP64 ncols                                  */
+  int32_t ncols;            /* 0: the instance is skipped                       */
+  int32_t degree;           /* m >= 1                                           */
+  paw_bounds bounds;        /* a0 < bW < bU                                     */
+  double *X_out;            /* device FP64 ndof x ncols (ld ldo), no aliasing   */
+  int32_t ldo;
+} paw_batch_problem;
+
+typedef struct {
+  int32_t streams;      /* concurrent graph branches at most (0: 4)          */
+  int32_t autotune;     /* 1: tune kernel family and branch count            */
+  int32_t reserved[6];
+} paw_batch_options;
+
+typedef struct {
+  int32_t tc_variant;   /* 0 persistent warp-specialised, 1 one CTA per tile */
+  int32_t grid_cap;     /* CTAs of a persistent launch (0: all SMs)          */
+  int32_t branch;       /* graph branch (stream) the instance runs on        */
+  int32_t branches;     /* branches of the graph                             */
+  int32_t graph_nodes;  /* nodes of the captured graph                       */
+  int32_t captures;     /* graphs captured so far by this batch              */
+  double tuned_ms[2];   /* timed short filter per kernel family (0: untimed) */
+} paw_batch_tuning;
+
+/* handles: count instance handles created by paw_fe_create (same device).
+ * Errors: INVALID_ARG (count < 1, NULL handle, handle repeated), CUDA. */
+paw_status paw_batch_create(const paw_handle *handles, int count, const paw_batch_options *options,
+                            paw_batch *out);
+
+/* problems: count entries (host).  status_out (host, count entries, may be
+ * NULL) receives each instance's status: OK, INVALID_ARG / NONFINITE for a
+ * rejected problem (that instance is skipped, the others run), TIMEOUT when a
+ * tensor-core kernel of the instance gave up on a bounded wait.  The call
+ * returns the first non-OK instance status, or a call-level error (CUDA,
+ * NO_MEMORY).  Synchronises `stream` before returning. */
+paw_status paw_batch_cheb_filter(paw_batch b, paw_precision prec, const paw_batch_problem *problems,
+                                 paw_status *status_out, void *stream);
+
+/* Tuning result and graph facts for instance i (after a filter call). */
+paw_status paw_batch_tuning_get(paw_batch b, int i, paw_batch_tuning *out);
+
+paw_status paw_batch_destroy(paw_batch b);
+
 /* Rayleigh-Ritz (Algorithm 1 steps 4-6) in FP64:
  * H^p = X^T H X, S^p = X^T S X, H^p Q = S^p Q Lambda, X <- X Q.
  *   X          : device FP64 ndof x N (ld), overwritten by the S-orthonormal

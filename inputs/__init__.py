@@ -19,6 +19,10 @@ Workloads (periodic cubes with uniform hexahedral cells):
               Chebyshev degree 40.
 * ``grad16``  the ``mid`` atom set at the ``tiny`` resolution (h = 2.5 bohr,
               degree 4): 16^3 cells, 64^3 DoFs, 16 vectors.
+* batched     ``batch_systems()``: independent instances of uneven size, cell
+              size h = 2.5 bohr (L = 2.5 n, n drawn from a range), degree drawn
+              from a set, seeded uniform atom positions, block widths drawn
+              from {32, ..., 512}; see its docstring for the caps.
 
 The local potential is a sum of attractive Gaussians
 V(r) = -A exp(-r^2 / (2 w^2)) (A = 2 Ha, w = 1 bohr), one per atom.
@@ -116,7 +120,10 @@ def _sym(rng, n, sigma, count):
 
 def make_system(name: str, seed: int = BASE_SEED) -> dict:
     """Return the seeded description of one workload (no vectors)."""
-    cfg = dict(CONFIGS[name])
+    return _build(dict(CONFIGS[name]), name, seed)
+
+
+def _build(cfg: dict, name: str, seed: int) -> dict:
     idx = cfg["index"]
     pos = _positions(cfg, _rng(idx, _S_POS, seed=seed))
     npj = nproj_of(cfg["shells"])
@@ -134,6 +141,54 @@ def make_system(name: str, seed: int = BASE_SEED) -> dict:
         ndof=(cfg["ncell"] * cfg["p"]) ** 3,
     )
     return cfg
+
+
+BASE_SHELLS = [(0, 0.6), (0, 1.2), (1, 0.75), (1, 1.05), (2, 0.9)]
+_TRUNC = float(np.sqrt(2.0 * np.log(1e8)))   # projector cutoff radius / width
+
+
+def batch_systems(count: int = 32, n_range=(4, 12), degrees=(4, 5, 6), atoms_range=(8, 64),
+                  widths=(32, 64, 128, 256, 512), degree: int = 25,
+                  seed: int = BASE_SEED) -> list:
+    """Seeded independent instances for the batched filter.
+
+    Instance i: n ~ U{n_range}, L = 2.5 n, p ~ U(degrees), the five projector
+    shells of the mid workload (13 projectors), B ~ U(widths) vectors, filter
+    degree `degree`.  Atoms are placed uniformly with a minimum periodic
+    separation of 2.5 bohr.  Two caps keep every instance valid for the
+    discretisation: the shell widths are scaled by min(1, 0.45 L / r_c,max)
+    so that every cutoff radius stays below L/2 (minimum image), and the atom
+    count is drawn up to min(atoms_range[1], L^3 / 40, 40 / f) with f the
+    fraction of the box within reach of one atom's projectors (so that at
+    most about 40 atoms touch one cell).
+    """
+    rng = _rng(99, 0, seed=seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        p = int(rng.choice(np.asarray(degrees)))
+        L = 2.5 * n
+        rc_max = max(w for _, w in BASE_SHELLS) * _TRUNC
+        scale = min(1.0, 0.45 * L / rc_max)
+        shells = [(l, w * scale) for l, w in BASE_SHELLS]
+        reach = 4.0 / 3.0 * np.pi * (rc_max * scale + 2.5 * np.sqrt(3.0) / 2.0) ** 3 / L ** 3
+        cap = int(min(atoms_range[1], L ** 3 / 40.0, 40.0 / min(1.0, reach)))
+        natoms = int(rng.integers(atoms_range[0], max(atoms_range[0], cap) + 1))
+        B = int(rng.choice(np.asarray(widths)))
+        cfg = dict(index=100 + i, L=L, ncell=n, p=p, natoms=natoms, shells=shells, lattice=None,
+                   min_sep=2.5, nvec=B, block=B, degree=degree, iters=1, nwanted=B)
+        out.append(_build(cfg, f"batch{i}", seed))
+    return out
+
+
+def columns_of(sysd: dict, cols, seed: int = BASE_SEED) -> np.ndarray:
+    """start_columns for a system description (also the batched instances)."""
+    ndof = sysd["ndof"]
+    cols = list(cols)
+    out = np.empty((ndof, len(cols)))
+    for j, c in enumerate(cols):
+        out[:, j] = _rng(sysd["index"], _S_X, int(c), seed=seed).standard_normal(ndof)
+    return out
 
 
 def start_columns(name: str, cols, ndof: int | None = None,

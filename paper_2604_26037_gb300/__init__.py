@@ -6,8 +6,8 @@ Rayleigh-Ritz projection and gradient runs in the library's CUDA kernels.
 PyTorch supplies device memory and the current CUDA stream.  There is no
 CPU fallback: importing this package fails if the library is missing.
 """
-from ._lib import (PawError, PawFE, Precision, build_library, lib_path, load_library,
+from ._lib import (PawBatch, PawError, PawFE, Precision, build_library, lib_path, load_library,
                    SubspaceEnergy)
 
-__all__ = ["PawError", "PawFE", "Precision", "build_library", "lib_path", "load_library",
+__all__ = ["PawBatch", "PawError", "PawFE", "Precision", "build_library", "lib_path", "load_library",
            "SubspaceEnergy"]

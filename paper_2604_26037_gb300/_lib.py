@@ -77,6 +77,22 @@ class _Profile(C.Structure):
                 ("total_launches", C.c_int64)]
 
 
+class _BatchProblem(C.Structure):
+    _fields_ = [("X_in", C.c_void_p), ("ldx", C.c_int32), ("lambda_in", C.POINTER(C.c_double)),
+                ("ncols", C.c_int32), ("degree", C.c_int32), ("bounds", _Bounds),
+                ("X_out", C.c_void_p), ("ldo", C.c_int32)]
+
+
+class _BatchOpts(C.Structure):
+    _fields_ = [("streams", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class _BatchTuning(C.Structure):
+    _fields_ = [("tc_variant", C.c_int32), ("grid_cap", C.c_int32), ("branch", C.c_int32),
+                ("branches", C.c_int32), ("graph_nodes", C.c_int32), ("captures", C.c_int32),
+                ("tuned_ms", C.c_double * 2)]
+
+
 _VP, _I, _D, _DP = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)
 SIGNATURES = {
     "paw_fe_create": [C.POINTER(_Mesh), _I, C.POINTER(_Atoms), C.POINTER(_Proj), _DP, _DP,
@@ -89,6 +105,10 @@ SIGNATURES = {
     "paw_apply_Sinv_approx": [_VP, _I, _VP, _VP, _I, _I, _I, _VP],
     "paw_apply_Sinv_approx_noalloc": [_VP, _I, _VP, _VP, _I, _I, _I, _VP],
     "paw_cheb_filter": [_VP, _I, _VP, _I, _DP, _I, _I, _Bounds, _VP, _I, _VP],
+    "paw_batch_create": [C.POINTER(_VP), _I, C.POINTER(_BatchOpts), C.POINTER(_VP)],
+    "paw_batch_cheb_filter": [_VP, _I, C.POINTER(_BatchProblem), C.POINTER(C.c_int), _VP],
+    "paw_batch_tuning_get": [_VP, _I, C.POINTER(_BatchTuning)],
+    "paw_batch_destroy": [_VP],
     "paw_rayleigh_ritz": [_VP, _VP, _I, _I, _DP, _VP],
     "paw_residuals": [_VP, _VP, _I, _DP, _I, _DP, _VP],
     "paw_lanczos_bounds": [_VP, _I, C.c_uint64, _DP, _DP, _VP],
@@ -333,6 +353,72 @@ class PawFE:
         _check(self._lib.paw_energy_grad(self._h, prec, xp, ld, n, C.c_void_p(dV.data_ptr()),
                                          C.c_void_p(dD.data_ptr()), _stream(X)))
         return dV, dD[: self.natoms]
+
+
+class PawBatch:
+    """Many PawFE instances filtered by one CUDA-graph launch per call
+    (paw_batch_create / paw_batch_cheb_filter).  The instances stay owned by
+    the caller and must outlive the batch."""
+
+    def __init__(self, instances, streams=4, autotune=True):
+        self._lib = load_library()
+        self.instances = list(instances)
+        hs = (_VP * len(self.instances))(*[fe._h for fe in self.instances])
+        opts = _BatchOpts(int(streams), 1 if autotune else 0)
+        h = _VP()
+        _check(self._lib.paw_batch_create(hs, len(self.instances), C.byref(opts), C.byref(h)))
+        self._h = h
+        self._keep = ()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.paw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cheb_filter(self, problems, prec="tf32", raise_on_error=True):
+        """problems: one (X, lam, degree, (a0, bW, bU), out) tuple per instance,
+        or None to skip it.  Returns the list of per-instance status codes."""
+        import torch
+        n = len(self.instances)
+        if len(problems) != n:
+            raise ValueError("one problem per instance")
+        arr = (_BatchProblem * n)()
+        keep = []
+        stream = None
+        for i, q in enumerate(problems):
+            if q is None:
+                arr[i].ncols = 0
+                continue
+            X, lam, degree, bounds, out = q
+            xp, _, nc, ldx = _mat(X, torch.float64)
+            op, _, nc2, ldo = _mat(out, torch.float64)
+            lam = np.ascontiguousarray(np.asarray(lam, float).reshape(-1))
+            keep.append(lam)
+            arr[i].X_in, arr[i].ldx = xp.value, ldx
+            arr[i].lambda_in = _dptr(lam)
+            arr[i].ncols, arr[i].degree = nc, int(degree)
+            arr[i].bounds = _Bounds(*bounds)
+            arr[i].X_out, arr[i].ldo = op.value, ldo
+            stream = stream or _stream(X)
+        st = (C.c_int * n)()
+        code = self._lib.paw_batch_cheb_filter(self._h, Precision.of(prec), arr, st,
+                                               stream if stream is not None else C.c_void_p(0))
+        if code != 0 and raise_on_error:
+            _check(code)
+        return list(st)
+
+    def tuning(self, i) -> dict:
+        t = _BatchTuning()
+        _check(self._lib.paw_batch_tuning_get(self._h, int(i), C.byref(t)))
+        d = {k: getattr(t, k) for k, _ in _BatchTuning._fields_ if k != "tuned_ms"}
+        d["tuned_ms"] = list(t.tuned_ms)
+        return d
 
 
 def _subspace_energy_cls():

@@ -47,6 +47,16 @@ paw_status fail(paw_status code, const std::string &msg) {
   return code;
 }
 
+int read_status(paw_context *c) {
+  if (!c->status_dev.ptr) return 0;
+  int v = 0;
+  if (cudaMemcpyAsync(&v, c->status_dev.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->last_stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->last_stream) != cudaSuccess)
+    return -1;
+  if (v != 0 && cudaMemsetAsync(c->status_dev.ptr, 0, sizeof(int), c->last_stream) != cudaSuccess) return -1;
+  return v;
+}
+
 void DevBuf::ensure(size_t nbytes, int64_t *counter) {
   if (nbytes <= bytes && ptr) return;
   if (ptr) {
@@ -166,26 +176,35 @@ template <>
 const float *mdinv_of<float>(paw_context *c) { return c->md_inv32.as<float>(); }
 
 // One block of Algorithm 2 in working precision TR.
-template <typename TR>
-static void cheb_block(paw_context *c, paw_precision prec, const double *X, int ldx, const double *lam,
-                       int nb, int m, paw_bounds bd, double *Xo, int ldo, cudaStream_t s) {
-  const int64_t M = c->ndof;
+// Host-side scalars of one block (Algorithm 2 steps 1, 3, 4): the recurrence
+// coefficients alpha_k, beta_k, gamma_k of every loop step and the device
+// scalar image hd = [-Lambda (nb)][Lambda_Y final (nb)][cf (nsteps nb)],
+// cf[k][j] = alpha_k Lambda_Y[j], plus its FP32 split hf = [hi (..)][lo (..)].
+size_t cheb_nd(int nb, int m) { return 2 * (size_t)nb + (size_t)std::max(0, m - 1) * nb; }
+size_t cheb_nf(int nb, int m) { return 2 * (size_t)std::max(0, m - 1) * nb + 2; }
+
+void cheb_plan(int nb, int m, paw_bounds bd, const double *lam, ChebScalars &S, double *hd, float *hf) {
   const double e = (bd.bU - bd.bW) / 2.0;
   const double cc = (bd.bU + bd.bW) / 2.0;
   double zeta = e / (bd.a0 - cc);
   double zeta1 = zeta;
   const double gam = 2.0 / zeta1;
-  // scalar recurrences on the host (Algorithm 2 steps 1, 3, 4); cf[k][j] = alpha_k Lambda_Y[j]
-  std::vector<double> LX(nb, 1.0), LY(nb), cf;
-  std::vector<double> be_h, ga_h, al_h;
+  std::vector<double> LX(nb, 1.0), LY(nb);
+  S.al.clear();
+  S.be.clear();
+  S.ga.clear();
+  S.nsteps = m - 1;
+  S.nd = cheb_nd(nb, m);
+  S.nf = cheb_nf(nb, m);
+  double *cf = hd + 2 * (size_t)nb;
   for (int j = 0; j < nb; ++j) LY[j] = (zeta1 / e) * (lam[j] - cc);
-  for (int th = 2; th <= m; ++th) {
+  for (int th = 2, k = 0; th <= m; ++th, ++k) {
     zeta1 = 1.0 / (gam - zeta);
     const double alpha = 2.0 * zeta1 / e, beta = alpha * cc, gk = zeta * zeta1;
-    al_h.push_back(alpha);
-    be_h.push_back(beta);
-    ga_h.push_back(gk);
-    for (int j = 0; j < nb; ++j) cf.push_back(alpha * LY[j]);
+    S.al.push_back(alpha);
+    S.be.push_back(beta);
+    S.ga.push_back(gk);
+    for (int j = 0; j < nb; ++j) cf[(size_t)k * nb + j] = alpha * LY[j];
     for (int j = 0; j < nb; ++j) {
       const double nx = alpha * LY[j] * lam[j] - beta * LY[j] - gk * LX[j];
       LX[j] = LY[j];
@@ -193,27 +212,37 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
     }
     zeta = zeta1;
   }
-  const int nsteps = m - 1;
-  // device scalars: [-Lambda (nb)][Lambda_Y final (nb)][cf (nsteps*nb)] and the FP32 split of cf
-  std::vector<double> hd(2 * (size_t)nb + cf.size());
   for (int j = 0; j < nb; ++j) {
     hd[j] = -lam[j];
     hd[nb + j] = LY[j];
   }
-  std::copy(cf.begin(), cf.end(), hd.begin() + 2 * nb);
-  std::vector<float> hf(2 * cf.size() + 2);
-  for (size_t i = 0; i < cf.size(); ++i) {
+  const size_t ncf = (size_t)S.nsteps * nb;
+  for (size_t i = 0; i < ncf; ++i) {
     const float h = (float)cf[i];
     hf[i] = h;
-    hf[cf.size() + i] = (float)(cf[i] - (double)h);
+    hf[ncf + i] = (float)(cf[i] - (double)h);
   }
-  c->ws_lam.ensure(sizeof(double) * hd.size(), &c->dev_bytes);
-  c->ws_cf.ensure(sizeof(float) * hf.size(), &c->dev_bytes);
+  hf[2 * ncf] = hf[2 * ncf + 1] = 0.f;
+}
+
+// Algorithm 2 for one block of nb columns: stream-ordered copies of the
+// scalar images (hd, hf: host memory that stays valid until the stream has
+// consumed it) and kernel launches only, no host synchronisation, so that the
+// sequence can also be captured into a CUDA graph.
+template <typename TR>
+static void cheb_block_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, double a0,
+                             double cc, const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo,
+                             cudaStream_t s) {
+  const int64_t M = c->ndof;
+  const int nsteps = S.nsteps;
+  c->ws_lam.ensure(sizeof(double) * S.nd, &c->dev_bytes);
+  c->ws_cf.ensure(sizeof(float) * S.nf, &c->dev_bytes);
   double *d_neglam = c->ws_lam.as<double>();
   const double *d_lyfin = d_neglam + nb, *d_cf = d_neglam + 2 * nb;
-  const float *d_chi = c->ws_cf.as<float>(), *d_clo = d_chi + cf.size();
-  PAW_CUDA(cudaMemcpyAsync(d_neglam, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice, s));
-  PAW_CUDA(cudaMemcpyAsync(c->ws_cf.ptr, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, s));
+  const size_t ncf = (size_t)nsteps * nb;
+  const float *d_chi = c->ws_cf.as<float>(), *d_clo = d_chi + ncf;
+  PAW_CUDA(cudaMemcpyAsync(d_neglam, hd, sizeof(double) * S.nd, cudaMemcpyHostToDevice, s));
+  PAW_CUDA(cudaMemcpyAsync(c->ws_cf.ptr, hf, sizeof(float) * S.nf, cudaMemcpyHostToDevice, s));
 
   const int ldr = nb;
   constexpr bool f32 = sizeof(TR) == 4;
@@ -239,13 +268,13 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   const dim3 blk(32, 8);
   {
     PhaseScope ps(c, 1, s);
-    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, 1.0 / (bd.a0 - cc), RY, RX, ldr, Yhi, Ylo);
+    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, 1.0 / (a0 - cc), RY, RX, ldr, Yhi, Ylo);
     PAW_LAUNCH_CHECK("k_cheb_init");
   }
   const TR *mdinv = mdinv_of<TR>(c);
   // step 4: R_X <- alpha H Shat^-1 R_Y - beta R_Y - gamma R_X + alpha Y Lambda_Y
   for (int k = 0; k < nsteps; ++k) {
-    const double alpha = al_h[k];
+    const double alpha = S.al[k];
     const size_t ko = (size_t)k * nb;
     if (c->nown_pairs > 0) {
       // one projection gives the coefficients of Shat^-1 (W_S) and of the nonlocal H (W_H)
@@ -256,15 +285,15 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
       // T = Shat^-1 R_Y and the recurrence update with the nonlocal part of alpha H T
       PhaseScope ps(c, 1, s);
       if constexpr (f32)
-        nl_recurrence_f32(c, prec, WS, WH, nb, RY, RX, T, ldr, mdinv, Yhi, Ylo, ldr, d_chi + ko, d_clo + ko, be_h[k],
-                          ga_h[k], s);
+        nl_recurrence_f32(c, prec, WS, WH, nb, RY, RX, T, ldr, mdinv, Yhi, Ylo, ldr, d_chi + ko, d_clo + ko, S.be[k],
+                          S.ga[k], s);
       else
-        nl_recurrence_f64(c, WS, WH, nb, RY, RX, T, ldr, mdinv, Y0, nb, d_cf + ko, be_h[k], ga_h[k], s);
+        nl_recurrence_f64(c, WS, WH, nb, RY, RX, T, ldr, mdinv, Y0, nb, d_cf + ko, S.be[k], S.ga[k], s);
     } else {
       PhaseScope ps(c, 1, s);
       k_cheb_base<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, RY, RX, T, ldr, f32 ? (const void *)Yhi : (const void *)Y0,
-                                                     Ylo, nb, d_cf + ko, d_chi + ko, d_clo + ko, (TR)be_h[k],
-                                                     (TR)ga_h[k], mdinv);
+                                                     Ylo, nb, d_cf + ko, d_chi + ko, d_clo + ko, (TR)S.be[k],
+                                                     (TR)S.ga[k], mdinv);
       PAW_LAUNCH_CHECK("k_cheb_base");
     }
     // R_X += alpha H_loc T (cell products with extraction and assembly)
@@ -281,12 +310,29 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
     k_cheb_recover<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, T, ldr, X, ldx, d_lyfin, Xo, ldo);
     PAW_LAUNCH_CHECK("k_cheb_recover");
   }
+}
+
+void cheb_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, paw_bounds bd,
+                const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s) {
+  const double cc = (bd.bU + bd.bW) / 2.0;
+  if (prec == PAW_FP64)
+    cheb_block_issue<double>(c, prec, X, ldx, nb, bd.a0, cc, S, hd, hf, Xo, ldo, s);
+  else
+    cheb_block_issue<float>(c, prec, X, ldx, nb, bd.a0, cc, S, hd, hf, Xo, ldo, s);
+}
+
+// One block, synchronous: scalars in host memory, launches, wait, device status.
+static void cheb_block(paw_context *c, paw_precision prec, const double *X, int ldx, const double *lam, int nb,
+                       int m, paw_bounds bd, double *Xo, int ldo, cudaStream_t s) {
+  ChebScalars S;
+  std::vector<double> hd(cheb_nd(nb, m));
+  std::vector<float> hf(cheb_nf(nb, m));
+  cheb_plan(nb, m, bd, lam, S, hd.data(), hf.data());
+  cheb_issue(c, prec, X, ldx, nb, bd, S, hd.data(), hf.data(), Xo, ldo, s);
   // keep host-side scalars alive until the async copies have been consumed
   PAW_CUDA(cudaStreamSynchronize(s));
-  if (prec == PAW_TF32 || prec == PAW_BF16) {
-    const int st_cell = tc_read_status(), st_nl = nltc_read_status();
-    PAW_REQUIRE(st_cell == 0 && st_nl == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
-  }
+  if (prec == PAW_TF32 || prec == PAW_BF16)
+    PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
 }
 
 // ============================================================== reductions
@@ -554,6 +600,8 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
     if (opts) c->opts = *opts;
     if (c->opts.block <= 0) c->opts.block = 256;
     if (npj == 0) c->natoms = 0;   // atoms without projectors carry no nonlocal term
+    c->status_dev.ensure(sizeof(int), &c->dev_bytes);
+    PAW_CUDA(cudaMemset(c->status_dev.ptr, 0, sizeof(int)));
     build_tables(c);
     build_operators(c, vloc);
     build_couplings(c);
@@ -581,7 +629,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
                     &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
-                    &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof,
+                    &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev,
                     &c->nltc.eoff};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -708,10 +756,7 @@ paw_status paw_cheb_filter(paw_handle c, paw_precision prec, const double *X_in,
   const int B = c->opts.block;
   for (int j0 = 0; j0 < ncols; j0 += B) {
     const int nb = std::min(B, ncols - j0);
-    if (prec == PAW_FP64)
-      cheb_block<double>(c, prec, X_in + j0, ldx, lambda_in + j0, nb, degree, b, X_out + j0, ldo, s);
-    else
-      cheb_block<float>(c, prec, X_in + j0, ldx, lambda_in + j0, nb, degree, b, X_out + j0, ldo, s);
+    cheb_block(c, prec, X_in + j0, ldx, lambda_in + j0, nb, degree, b, X_out + j0, ldo, s);
   }
   return PAW_OK;
   PAW_TRY_END
@@ -949,8 +994,7 @@ paw_status paw_sync_status(paw_handle c) {
   PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
   PAW_CUDA(cudaStreamSynchronize(c->last_stream));
   PAW_CUDA(cudaGetLastError());
-  const int st_cell = tc_read_status(), st_nl = nltc_read_status();
-  PAW_REQUIRE(st_cell == 0 && st_nl == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+  PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
   return PAW_OK;
   PAW_TRY_END
 }

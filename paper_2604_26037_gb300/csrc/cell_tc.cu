@@ -29,8 +29,6 @@
 
 namespace pawfe {
 
-__device__ int g_tc_status = 0;
-
 namespace {
 
 constexpr int MT = 128;            // vectors per CTA = MMA M
@@ -50,6 +48,7 @@ struct TcArgs {
   float *Y;
   int ldy, ncols;
   float alpha;
+  int *status;             // set to 1 when a bounded wait expires
 };
 
 template <bool BF16>
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(TcArgs a) {
       }
     }
   } else if (lane == 0) {
-    atomicExch(&g_tc_status, 1);
+    atomicExch(a.status, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -378,10 +377,9 @@ static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx
   int dev = 0, nsm = 0;
   PAW_CUDA(cudaGetDevice(&dev));
   PAW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  void *st = nullptr;
-  PAW_CUDA(cudaGetSymbolAddress(&st, g_tc_status));
-  const int grid = std::max(1, std::min(p.ntiles, nsm));
-  tcs::k_tc_stream<CellStream<BF>><<<grid, tcs::threads_for(CellStream<BF>::NEPI), shm, s>>>(p, (int *)st);
+  const int cap = c->grid_cap > 0 ? std::min(c->grid_cap, nsm) : nsm;
+  const int grid = std::max(1, std::min(p.ntiles, cap));
+  tcs::k_tc_stream<CellStream<BF>><<<grid, tcs::threads_for(CellStream<BF>::NEPI), shm, s>>>(p, c->status_dev.as<int>());
   PAW_LAUNCH_CHECK("k_tc_stream<cell>");
 }
 
@@ -392,7 +390,8 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, 
   tc_prepare(c, prec, s);
   TcMats &T = bf16 ? c->tc_bf16 : c->tc_tf32;
   // rows of X copied with 16-byte cp.async: aligned base, pitch and vector range
-  if (reinterpret_cast<uintptr_t>(X) % 16 == 0 && ldx % 4 == 0 && ncols % 4 == 0 && T.ntile <= 256) {
+  if (c->tc_variant == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 && ldx % 4 == 0 && ncols % 4 == 0 &&
+      T.ntile <= 256) {
     if (bf16)
       cell_stream<true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
     else
@@ -414,6 +413,7 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, 
   a.ldy = ldy;
   a.ncols = ncols;
   a.alpha = alpha;
+  a.status = c->status_dev.as<int>();
   const size_t shm = tc_smem_bytes(T.ntile, T.kchunks, bf16);
   const int64_t blocks = (int64_t)c->ncells * T.ntiles * a.vtiles;
   PAW_REQUIRE(blocks < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many cell tiles");
@@ -425,16 +425,6 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, 
     k_cell_tc<false><<<(unsigned)blocks, THREADS, shm, s>>>(a);
   }
   PAW_LAUNCH_CHECK("k_cell_tc");
-}
-
-int tc_read_status() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) return -1;
-  if (v) {
-    int z = 0;
-    cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int));
-  }
-  return v;
 }
 
 }  // namespace pawfe

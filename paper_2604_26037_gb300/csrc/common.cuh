@@ -169,6 +169,12 @@ struct paw_context {
   pawfe::DevBuf ws_pp;                        // per-pair projection partials
   pawfe::DevBuf ws_HX, ws_SX, ws_Hp, ws_Sp, ws_eig, ws_solver, ws_info, ws_rot;
 
+  // tensor-core kernel family: 0 persistent warp-specialised where the layout
+  // allows it, 1 one-CTA-per-tile kernels; grid_cap > 0 limits the CTAs of a
+  // persistent launch (instances sharing the GPU)
+  int tc_variant = 0, grid_cap = 0;
+  pawfe::DevBuf status_dev;                   // int: set by a kernel whose bounded wait expired
+
   cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t cusolver = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -232,8 +238,6 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
 // expansion with the output stage of mode (EXP_ADD / EXP_SINV / EXP_RECURRENCE)
 struct ExpArgs;
 void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, const float *W2, cudaStream_t s);
-// 0: no bounded wait expired since the last read; 1: one did (cleared on read)
-int nltc_read_status();
 // FP64 sum-factorised local operator (sumfac.cu):
 // Y += alpha * (cK K^e + cV V^e + (cM + cMcol[j]) M^e) X, cell by cell with assembly
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
@@ -263,8 +267,26 @@ void op_Sinv(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int 
 void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s);
 void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
                    float *Y, int ldy, int ncols, float alpha, cudaStream_t s);
-// 0: no bounded wait expired since the last read; 1: one did (cleared on read)
-int tc_read_status();
+// device status word of the instance: 0 when no bounded wait of a tensor-core
+// kernel expired since the last read, 1 when one did (read on the last stream,
+// then cleared); -1 when it cannot be read
+int read_status(paw_context *c);
+
+// Algorithm 2 for one block of nb columns (api.cu).  cheb_plan fills the host
+// scalar images hd (cheb_nd entries) and hf (cheb_nf entries); cheb_issue
+// enqueues the copies of those images and all kernels on stream s without any
+// host synchronisation (capturable into a CUDA graph; hd and hf must stay
+// valid until the stream has consumed them).
+struct ChebScalars {
+  std::vector<double> al, be, ga;
+  int nsteps = 0;
+  size_t nd = 0, nf = 0;
+};
+size_t cheb_nd(int nb, int m);
+size_t cheb_nf(int nb, int m);
+void cheb_plan(int nb, int m, paw_bounds bd, const double *lam, ChebScalars &S, double *hd, float *hf);
+void cheb_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, paw_bounds bd,
+                const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s);
 
 // RAII bracket of one phase of the filter (records events only when enabled)
 struct PhaseScope {

@@ -31,8 +31,6 @@
 
 namespace pawfe {
 
-__device__ int g_nltc_status = 0;
-
 namespace {
 
 using namespace tcp;
@@ -79,6 +77,7 @@ struct ProjTcArgs {
   const float *X;
   const float *rowscale;
   float *PP;
+  int *status;   // set to 1 when a bounded wait expires
 };
 
 __global__ void __launch_bounds__(THREADS, 2) k_nl_project_tc(ProjTcArgs a) {
@@ -95,7 +94,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_nl_project_tc(ProjTcArgs a) {
   const int k0 = a.own_off[e], k1 = a.own_off[e + 1];
   // uniform over the CTA, before any barrier or TMEM use: no pairs, or an
   // earlier CTA gave up on a bounded wait (the launch is reported as failed)
-  if (k0 == k1 || *reinterpret_cast<volatile int *>(&g_nltc_status) != 0) return;
+  if (k0 == k1 || *reinterpret_cast<volatile int *>(a.status) != 0) return;
   const int64_t cb = owned_base(e, a.n, a.p, a.N1);
   for (int o = tid; o < a.own; o += THREADS) {
     const int off = owned_offset(o, a.p, a.N1);
@@ -198,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_nl_project_tc(ProjTcArgs a) {
     tc_fence_after();
     if (!ok) break;
   }
-  if (!ok && lane == 0) atomicExch(&g_nltc_status, 1);
+  if (!ok && lane == 0) atomicExch(a.status, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -212,6 +211,7 @@ struct ExpTcArgs {
   int npad, ppc, ntile, nh, vtiles, own;
   const uint8_t *B;
   const int *eoff;
+  int *status;
 };
 
 template <int MODE>
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_nl_expand_tc(ExpArgs A, ExpTcArg
   const int k0 = A.own_off[e], k1 = A.own_off[e + 1];
   const int np = k1 - k0;
   if (MODE == EXP_ADD && np == 0) return;   // nothing to add (uniform, before any barrier)
-  if (*reinterpret_cast<volatile int *>(&g_nltc_status) != 0) return;   // an earlier CTA gave up
+  if (*reinterpret_cast<volatile int *>(a.status) != 0) return;   // an earlier CTA gave up
   const int KC = a.eoff[e + 1] - a.eoff[e];
   const int ncols = A.ncols;
   const int o_beg = h * a.ntile;
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_nl_expand_tc(ExpArgs A, ExpTcArg
       }
     }
   } else if (lane == 0) {
-    atomicExch(&g_nltc_status, 1);
+    atomicExch(a.status, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -1007,25 +1007,21 @@ void nltc_prepare(paw_context *c, cudaStream_t s) {
   N.valid = 1;
 }
 
-// device address of the status word and the SM count of the current device
-static int *status_ptr() {
-  void *p = nullptr;
-  PAW_CUDA(cudaGetSymbolAddress(&p, g_nltc_status));
-  return static_cast<int *>(p);
-}
-static int sm_count() {
+// CTAs of a persistent launch: the SM count of the current device, capped by
+// the instance's grid limit (set when instances share the GPU)
+static int persistent_grid(const paw_context *c) {
   int dev = 0, n = 0;
   PAW_CUDA(cudaGetDevice(&dev));
   PAW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-  return n;
+  return c->grid_cap > 0 ? std::min(c->grid_cap, n) : n;
 }
 
 template <class P>
-static void launch_stream(const P &p, cudaStream_t s, const char *what) {
+static void launch_stream(const paw_context *c, const P &p, cudaStream_t s, const char *what) {
   const size_t shm = tcs::Geo<P>::SMEM;
   PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  const int grid = std::max(1, std::min(p.ntiles, sm_count()));
-  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, status_ptr());
+  const int grid = std::max(1, std::min(p.ntiles, persistent_grid(c)));
+  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>());
   PAW_LAUNCH_CHECK(what);
 }
 
@@ -1040,7 +1036,7 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
   const NlTcMats &N = c->nltc;
   const int vtiles = (ncols + MT - 1) / MT;
   const bool scaled = rowscale != nullptr && rowscale == c->md_inv32.as<float>();
-  if ((rowscale == nullptr || scaled) && rows16(X, ldx) && ncols % 4 == 0) {
+  if (c->tc_variant == 0 && (rowscale == nullptr || scaled) && rows16(X, ldx) && ncols % 4 == 0) {
     ProjStream p;
     p.ntiles = c->ncells * vtiles;
     p.ncols = ncols;
@@ -1057,7 +1053,7 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
     p.B = scaled ? N.projBs.as<uint8_t>() : N.projB.as<uint8_t>();
     p.X = X;
     p.PP = PP;
-    launch_stream(p, s, "k_tc_stream<projection>");
+    launch_stream(c, p, s, "k_tc_stream<projection>");
     return;
   }
   ProjTcArgs a;
@@ -1076,6 +1072,7 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
   a.X = X;
   a.rowscale = rowscale;
   a.PP = PP;
+  a.status = c->status_dev.as<int>();
   const int64_t blocks = (int64_t)c->ncells * a.vtiles;
   PAW_REQUIRE(blocks < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many projection tiles");
   const size_t shm = proj_smem();
@@ -1106,8 +1103,8 @@ static void expand_stream(paw_context *c, const ExpArgs &A, const float *W1, con
   p.odof = N.odof.as<int>();
   const size_t shm = xs::smem_bytes<MODE>();
   PAW_CUDA(cudaFuncSetAttribute(xs::k_exp_stream<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  const int grid = std::max(1, std::min(p.ntiles, sm_count()));
-  xs::k_exp_stream<MODE><<<grid, xs::THREADS, shm, s>>>(p, status_ptr());
+  const int grid = std::max(1, std::min(p.ntiles, persistent_grid(c)));
+  xs::k_exp_stream<MODE><<<grid, xs::THREADS, shm, s>>>(p, c->status_dev.as<int>());
   PAW_LAUNCH_CHECK("k_exp_stream");
 }
 
@@ -1116,7 +1113,7 @@ void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, co
   nltc_prepare(c, s);
   const NlTcMats &N = c->nltc;
   // bulk-copied rows (output-stage operands) must start on 16-byte boundaries
-  bool rows_ok = A.ncols % 4 == 0;
+  bool rows_ok = c->tc_variant == 0 && A.ncols % 4 == 0;
   if (mode == EXP_RECURRENCE)
     rows_ok = rows_ok && rows16(A.Xin, A.ldx) && rows16(A.RX, A.ldx) && rows16(A.Y0, A.ldy0) &&
               (A.Y0lo == nullptr || rows16(A.Y0lo, A.ldy0));
@@ -1142,6 +1139,7 @@ void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, co
   a.own = c->own;
   a.B = N.expB.as<uint8_t>();
   a.eoff = N.eoff.as<int>();
+  a.status = c->status_dev.as<int>();
   const int64_t blocks = (int64_t)c->ncells * N.nh * a.vtiles;
   PAW_REQUIRE(blocks < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many expansion tiles");
   const size_t shm = exp_smem(mode == EXP_RECURRENCE ? 2 : 1);
@@ -1162,16 +1160,6 @@ void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, co
       break;
   }
   PAW_LAUNCH_CHECK("k_nl_expand_tc");
-}
-
-int nltc_read_status() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_nltc_status, sizeof(int)) != cudaSuccess) return -1;
-  if (v) {
-    int z = 0;
-    cudaMemcpyToSymbol(g_nltc_status, &z, sizeof(int));
-  }
-  return v;
 }
 
 }  // namespace pawfe
