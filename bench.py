@@ -378,13 +378,105 @@ def run_reference(args, ws, rank):
                                         "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------- batched instances
+def run_batch(args, ws, rank, local):
+    """32 independent uneven instances (cells 4^3..12^3, degree 4-6, 8-64 atoms,
+    block widths 32-512, Chebyshev degree 25) filtered by one CUDA-graph launch
+    per step.  Throughput = sum_i M_i B_i m / t."""
+    import torch
+    import paper_2604_26037_gb300 as P
+
+    torch.cuda.set_device(local)
+    systems = inputs.batch_systems()
+    fes, probs, units = [], [], 0.0
+    for k, sd in enumerate(systems):
+        fe = P.PawFE.from_system(sd, block=sd["block"], y0_fp32=args.y0_fp32)
+        g = torch.Generator(device="cuda").manual_seed(4321 + 97 * k + rank)
+        X = torch.randn((fe.ndof, sd["nvec"]), dtype=torch.float64, device="cuda", generator=g)
+        lam = fe.rayleigh_ritz(X)
+        tmin, bU = fe.lanczos_bounds(20, 7)
+        probs.append((X, lam, sd["degree"], (min(lam[0], tmin), float(lam[-1]), bU), torch.empty_like(X)))
+        units += float(fe.ndof) * sd["nvec"] * sd["degree"]
+        fes.append(fe)
+    stream = torch.cuda.current_stream()
+    batch = P.PawBatch(fes, streams=4, autotune=True)
+    for _ in range(args.warmup):
+        batch.cheb_filter(probs, prec=args.prec)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.cheb_filter(probs, prec=args.prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+    value = units * ws / (ms / 1e3) / 1e9
+    tun = [batch.tuning(i) for i in range(len(fes))]
+    # the same instances one after another through paw_cheb_filter (no graph, no concurrency)
+    for (X, lam, m, bd, out), fe in zip(probs, fes):
+        fe.cheb_filter(X, lam, m, bd, prec=args.prec, out=out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for (X, lam, m, bd, out), fe in zip(probs, fes):
+        fe.cheb_filter(X, lam, m, bd, prec=args.prec, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_serial = e0.elapsed_time(e1)
+    # end to end: host (pinned) inputs and outputs of every instance, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hosts = [(X.cpu().pin_memory(), torch.empty_like(out, device="cpu").pin_memory()) for X, _, _, _, out in probs]
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for (Xh, _), (X, _, _, _, _) in zip(hosts, probs):
+                X.copy_(Xh, non_blocking=True)
+            batch.cheb_filter(probs, prec=args.prec)
+            for (_, Oh), (_, _, _, _, out) in zip(hosts, probs):
+                Oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
+        e2e = {"value": units * ws / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h[0].numel() * 8 for h in hosts)),
+               "d2h_bytes_per_step": int(sum(h[1].numel() * 8 for h in hosts))}
+    res = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"tf32": "tf32", "fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.prec],
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"batch32: {len(fes)} independent instances, cells n^3 with n in 4..12 "
+                               f"(h = 2.5 bohr), degree 4-6, 8-64 atoms x 13 projectors, block widths "
+                               f"32-512, Chebyshev degree 25; one CUDA-graph launch per step",
+                   "precision": args.prec, "parallelism": f"replicas x{ws}",
+                   "dofs_vec_per_degree": units / 25.0},
+        "gpu_launches": int(tun[0]["kernel_nodes"]),
+        "graph": {"nodes": tun[0]["graph_nodes"], "kernel_nodes": tun[0]["kernel_nodes"],
+                  "branches": tun[0]["branches"], "captures": tun[0]["captures"]},
+        "tuning": {"persistent": sum(1 for t in tun if t["tc_variant"] == 0),
+                   "one_cta_per_tile": sum(1 for t in tun if t["tc_variant"] == 1),
+                   "grid_cap": tun[0]["grid_cap"]},
+        "serial_calls_ms": round(ms_serial, 3),
+        "speedup_vs_serial_calls": round(ms_serial / ms, 3),
+        "clocks": clk.summary(),
+        "roofline": None,
+        "e2e": e2e,
+    }
+    batch.close()
+    for fe in fes:
+        fe.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(inputs.CONFIGS))
+    ap.add_argument("--workload", default="mid", choices=sorted(inputs.CONFIGS) + ["batch32"])
     ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "bf16", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--y0-fp32", action="store_true")
@@ -399,6 +491,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         res = run_reference(args, ws, rank)
+    elif args.workload == "batch32":
+        res = run_batch(args, ws, rank, local)
     else:
         res = run_ours(args, ws, rank, local)
         if rank == 0 and not args.no_cpu_baseline:

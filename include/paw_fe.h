@@ -63,9 +63,11 @@ typedef enum {
 typedef enum {
   PAW_FP64 = 0,  /* every step in FP64: the plain method                      */
   PAW_FP32 = 1,  /* filter bracket in FP32 storage and FP32 FMA arithmetic     */
-  PAW_TF32 = 2,  /* FP32 storage; cell products on tcgen05 tensor cores (TF32  */
-                 /* operands, FP32 accumulation in tensor memory)              */
-  PAW_BF16 = 3   /* as PAW_TF32 with BF16 cell-matrix and vector operands      */
+  PAW_TF32 = 2,  /* FP32 storage; cell products and projector contractions   */
+                 /* on tcgen05 tensor cores (TF32 operands, FP32 accumulation */
+                 /* in tensor memory)                                          */
+  PAW_BF16 = 3   /* as PAW_TF32 with BF16 cell-matrix and vector operands of  */
+                 /* the cell products (projector contractions stay TF32)       */
 } paw_precision;
 
 /* Periodic cubic box: L[0] = L[1] = L[2] and n_cells equal, periodic = 1. */
@@ -260,6 +262,7 @@ typedef struct {
   int32_t branch;       /* graph branch (stream) the instance runs on        */
   int32_t branches;     /* branches of the graph                             */
   int32_t graph_nodes;  /* nodes of the captured graph                       */
+  int32_t kernel_nodes; /* of which kernel launches                          */
   int32_t captures;     /* graphs captured so far by this batch              */
   double tuned_ms[2];   /* timed short filter per kernel family (0: untimed) */
 } paw_batch_tuning;

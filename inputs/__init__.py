@@ -175,10 +175,42 @@ def batch_systems(count: int = 32, n_range=(4, 12), degrees=(4, 5, 6), atoms_ran
         cap = int(min(atoms_range[1], L ** 3 / 40.0, 40.0 / min(1.0, reach)))
         natoms = int(rng.integers(atoms_range[0], max(atoms_range[0], cap) + 1))
         B = int(rng.choice(np.asarray(widths)))
-        cfg = dict(index=100 + i, L=L, ncell=n, p=p, natoms=natoms, shells=shells, lattice=None,
-                   min_sep=2.5, nvec=B, block=B, degree=degree, iters=1, nwanted=B)
-        out.append(_build(cfg, f"batch{i}", seed))
+        while True:
+            cfg = dict(index=100 + i, L=L, ncell=n, p=p, natoms=natoms, shells=shells, lattice=None,
+                       min_sep=2.5, nvec=B, block=B, degree=degree, iters=1, nwanted=B)
+            sysd = _build(cfg, f"batch{i}", seed)
+            if natoms <= 2 or _atoms_per_cell(sysd["positions"], L, n, rc_max * scale) <= 40:
+                break
+            natoms -= 2
+        out.append(sysd)
     return out
+
+
+def _atoms_per_cell(pos, L, n, rc):
+    """Largest number of atoms whose projectors reach the owned nodes of one cell.
+
+    A cell carries an atom's projector block when its centre lies within
+    rc + h sqrt(3)/2 of the atom (periodic); the nodes a cell owns (local
+    indices < p) are shared with its neighbours in the -x, -y, -z directions,
+    so the count runs over the support cells shifted by 0 or 1 cell per axis.
+    """
+    h = L / n
+    idx = np.arange(n)
+    cz, cy, cx = np.meshgrid(idx, idx, idx, indexing="ij")
+    centers = np.stack([cx, cy, cz], -1).reshape(-1, 3) * h + h / 2
+    count = np.zeros((n, n, n), int)
+    reach = rc + h * np.sqrt(3.0) / 2.0
+    for x in np.asarray(pos):
+        d = centers - x
+        d -= L * np.round(d / L)
+        sup = (np.sqrt((d ** 2).sum(1)) < reach).reshape(n, n, n)   # [cz][cy][cx]
+        own = np.zeros_like(sup)
+        for sz in (0, 1):
+            for sy in (0, 1):
+                for sx in (0, 1):
+                    own |= np.roll(sup, (sz, sy, sx), axis=(0, 1, 2))
+        count += own
+    return int(count.max())
 
 
 def columns_of(sysd: dict, cols, seed: int = BASE_SEED) -> np.ndarray:

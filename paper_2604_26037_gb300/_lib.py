@@ -89,8 +89,8 @@ class _BatchOpts(C.Structure):
 
 class _BatchTuning(C.Structure):
     _fields_ = [("tc_variant", C.c_int32), ("grid_cap", C.c_int32), ("branch", C.c_int32),
-                ("branches", C.c_int32), ("graph_nodes", C.c_int32), ("captures", C.c_int32),
-                ("tuned_ms", C.c_double * 2)]
+                ("branches", C.c_int32), ("graph_nodes", C.c_int32), ("kernel_nodes", C.c_int32),
+                ("captures", C.c_int32), ("tuned_ms", C.c_double * 2)]
 
 
 _VP, _I, _D, _DP = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)

@@ -41,7 +41,7 @@ struct paw_batch_s {
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
   cudaGraphExec_t exec = nullptr;
-  size_t graph_nodes = 0;
+  size_t graph_nodes = 0, kernel_nodes = 0;
   int captures = 0;
   int branches = 1;
   std::vector<double> sig;               // signature of the captured graph
@@ -139,11 +139,20 @@ void capture(paw_batch_s *b, paw_precision prec, const paw_batch_problem *pr, co
   PAW_CUDA(cudaStreamEndCapture(s, &g));
   for (size_t i = 0; i < b->inst.size(); ++i) b->inst[i]->prof.on = prof_on[i] != 0;
   const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
-  size_t n = 0;
+  size_t n = 0, nk = 0;
   cudaGraphGetNodes(g, nullptr, &n);
+  if (n > 0) {
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(g, nodes.data(), &n);
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+    }
+  }
   cudaGraphDestroy(g);
   PAW_CUDA(e);
   b->graph_nodes = n;
+  b->kernel_nodes = nk;
   b->branches = branches;
   ++b->captures;
 }
@@ -379,6 +388,7 @@ paw_status paw_batch_tuning_get(paw_batch b, int i, paw_batch_tuning *out) {
   out->branches = b->branches;
   out->branch = b->branch_of[i];
   out->graph_nodes = (int32_t)b->graph_nodes;
+  out->kernel_nodes = (int32_t)b->kernel_nodes;
   out->captures = b->captures;
   out->tuned_ms[0] = b->tuned_ms[i][0];
   out->tuned_ms[1] = b->tuned_ms[i][1];
