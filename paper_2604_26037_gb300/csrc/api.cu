@@ -482,20 +482,34 @@ __global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__res
 
 // dD[a][al][be] = sum_v U[a][al][v] U[a][be][v]
 template <typename T>
-__global__ void k_grad_D(int npj, int npad, const T *__restrict__ U, int ldu, int ncols, double *__restrict__ dD) {
+// dD[a][ext(al)][ext(be)] = sum_v U[a][al][v] U[a][be][v]  (ext: internal -> caller's projector index)
+__global__ void k_grad_D(int npj, int npad, const T *__restrict__ U, int ldu, int ncols, const int *__restrict__ ext,
+                         double *__restrict__ dD) {
   const int a = blockIdx.x;
   for (int o = threadIdx.x; o < npj * npj; o += blockDim.x) {
     const int al = o / npj, be = o % npj;
     double s = 0.0;
     for (int v = 0; v < ncols; ++v)
       s += (double)U[((size_t)a * npad + al) * ldu + v] * (double)U[((size_t)a * npad + be) * ldu + v];
-    dD[(size_t)a * npj * npj + o] = s;
+    dD[(size_t)a * npj * npj + (size_t)ext[al] * npj + ext[be]] = s;
   }
 }
 
 }  // namespace pawfe
 
 using namespace pawfe;
+
+// natoms x npj x npj blocks from the caller's projector order to the internal one
+static std::vector<double> to_internal(const paw_context *c, const double *ext) {
+  const int n = c->npj;
+  std::vector<double> out((size_t)c->natoms * n * n);
+  for (int a = 0; a < c->natoms; ++a)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        out[((size_t)a * n + i) * n + j] = ext[((size_t)a * n + c->proj_ext[i]) * n + c->proj_ext[j]];
+  return out;
+}
+
 
 // ============================================================== C ABI
 #define PAW_TRY_BEGIN try {
@@ -583,14 +597,25 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
     c->detJ = std::pow(c->h / 2.0, 3);
     c->natoms = natoms;
     c->npj = npj;
-    for (int s = 0; s < nsh; ++s) {
-      c->shell_l.push_back(proj->l[s]);
-      c->shell_w.push_back(proj->width[s]);
+    // Internal projector order: shells by decreasing width (stable).  The
+    // cutoff radius grows with the width, so the projectors of an atom that
+    // reach a cell form a prefix and the kernels skip the all-zero rest.
+    {
+      std::vector<int> order(nsh), ext_off(nsh + 1, 0);
+      for (int s = 0; s < nsh; ++s) ext_off[s + 1] = ext_off[s] + 2 * proj->l[s] + 1;
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return proj->width[x] > proj->width[y]; });
+      for (int s : order) {
+        c->shell_l.push_back(proj->l[s]);
+        c->shell_w.push_back(proj->width[s]);
+        for (int m = 0; m < 2 * proj->l[s] + 1; ++m) c->proj_ext.push_back(ext_off[s] + m);
+      }
     }
     if (natoms > 0) c->pos.assign(atoms->positions, atoms->positions + 3 * natoms);
     if (natoms > 0 && npj > 0) {
-      c->D.assign(D_ij, D_ij + (size_t)natoms * npj * npj);
-      c->dS.assign(dS_ij, dS_ij + (size_t)natoms * npj * npj);
+      c->D = to_internal(c, D_ij);
+      c->dS = to_internal(c, dS_ij);
     }
     if (vloc && vloc->ngauss > 0) {
       c->vg_c.assign(vloc->centers, vloc->centers + 3 * vloc->ngauss);
@@ -602,6 +627,10 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
     if (npj == 0) c->natoms = 0;   // atoms without projectors carry no nonlocal term
     c->status_dev.ensure(sizeof(int), &c->dev_bytes);
     PAW_CUDA(cudaMemset(c->status_dev.ptr, 0, sizeof(int)));
+    if (npj > 0) {
+      c->proj_ext_dev.ensure(sizeof(int) * npj, &c->dev_bytes);
+      PAW_CUDA(cudaMemcpy(c->proj_ext_dev.ptr, c->proj_ext.data(), sizeof(int) * npj, cudaMemcpyHostToDevice));
+    }
     build_tables(c);
     build_operators(c, vloc);
     build_couplings(c);
@@ -629,7 +658,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
                     &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
-                    &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev,
+                    &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
                     &c->nltc.eoff};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -670,7 +699,7 @@ paw_status paw_set_dij(paw_handle c, const double *D_ij) {
   PAW_REQUIRE(c && D_ij, PAW_ERR_INVALID_ARG, "NULL handle or D_ij");
   if (c->natoms == 0) return PAW_OK;
   check_sym(D_ij, c->natoms, c->npj, "D_ij");
-  c->D.assign(D_ij, D_ij + (size_t)c->natoms * c->npj * c->npj);
+  c->D = to_internal(c, D_ij);
   PAW_CUDA(cudaDeviceSynchronize());
   PAW_CUDA(cudaMemcpy(c->DH64.ptr, c->D.data(), sizeof(double) * c->D.size(), cudaMemcpyHostToDevice));
   return PAW_OK;
@@ -946,12 +975,14 @@ paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int 
     if (prec == PAW_FP64) {
       c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
       nl_project<double>(c, PAW_FP64, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
-      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N, dE_dD);
+      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N,
+                                                 c->proj_ext_dev.as<int>(), dE_dD);
     } else {
       c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
       // projector coefficients of the D_ij gradient stay in FP32 arithmetic
       nl_project<float>(c, PAW_FP32, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
-      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N, dE_dD);
+      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N,
+                                                c->proj_ext_dev.as<int>(), dE_dD);
     }
     PAW_LAUNCH_CHECK("k_grad_D");
   }

@@ -113,8 +113,10 @@ struct paw_context {
   int64_t ndof = 0;
   double L = 0, h = 0, detJ = 0;
   int natoms = 0, npj = 0;
-  std::vector<int> shell_l;
+  std::vector<int> shell_l;                   // shells in internal order (decreasing width)
   std::vector<double> shell_w;
+  std::vector<int> proj_ext;                  // internal projector -> caller's projector index
+  pawfe::DevBuf proj_ext_dev;
   std::vector<double> pos, D, dS, G, Dsinv;   // host copies
   std::vector<double> vg_c, vg_A, vg_w;       // local potential Gaussians
   paw_options opts{};
@@ -153,6 +155,7 @@ struct paw_context {
   pawfe::DevBuf own_off;                      // int32 ncells+1
   pawfe::DevBuf own_atom;                     // int32 nown_pairs
   pawfe::DevBuf ownP64, ownP32;               // nown_pairs * own * npad
+  pawfe::DevBuf own_ngrp;                     // int32 per pair: projector groups of 4 with a nonzero value
   pawfe::DevBuf apair_off, apair;             // atom-major list of the pairs (int32)
   // atom-pair Gram blocks G_ab = P^a^T M_D^-1 P^b for atoms with common support
   // nodes (CSR over atoms, a included); lets P^T Shat^-1 R follow from P^T M_D^-1 R

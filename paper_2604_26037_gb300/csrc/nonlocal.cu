@@ -84,7 +84,7 @@ __device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
 // thread groups whose partial sums are reduced through shared memory.
 template <typename T, int NPAD>
 __global__ void __launch_bounds__(256) k_own_project(int n, int p, int N1, const int *__restrict__ own_off,
-                                                     const int *__restrict__ own_atom, const T *__restrict__ oP,
+                                                     const int *__restrict__ own_ngrp, const T *__restrict__ oP,
                                                      const T *__restrict__ X, int ldx, int ncols,
                                                      const T *__restrict__ rowscale, int npj, T *__restrict__ U,
                                                      int x_aligned) {
@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(256) k_own_project(int n, int p, int N1, const
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int o = og; o < own; o += OG) {
+    // projector groups past the pair's last nonzero one contribute zeros
+    const int olim = (aq < own_ngrp[k]) ? own : 0;
+    for (int o = og; o < olim; o += OG) {
       T pv[4], xv[4];
       ld4(Pk + (size_t)o * NPAD, pv);
       ld4(Xs + (size_t)o * VT + vq * 4, xv);
@@ -391,8 +393,10 @@ __global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__res
       const T *Pb = oP + (size_t)(k0 + kk) * own * NPAD;
       const T *W1k = Ws + (size_t)kk * NPAD * VT + g * 4;
       const T *W2k = Ws + ((size_t)np + kk) * NPAD * VT + g * 4;
+      const int ng = A.own_ngrp[k0 + kk];   // the remaining projector groups are zero on this pair
 #pragma unroll
       for (int aq = 0; aq < NPAD / 4; ++aq) {
+        if (aq >= ng) break;
         T pv[RB][4];
 #pragma unroll
         for (int r = 0; r < RB; ++r) ld4(Pb + (size_t)orr[r] * NPAD + aq * 4, pv[r]);
@@ -445,7 +449,7 @@ static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T
   PAW_CUDA(cudaFuncSetAttribute(k_own_project<T, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 g1((ncols + VT - 1) / VT, c->ncells);
   const int xa = aligned16(X, ldx * sizeof(T)) ? 1 : 0;
-  k_own_project<T, NPAD><<<g1, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_atom.as<int>(),
+  k_own_project<T, NPAD><<<g1, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_ngrp.as<int>(),
                                               ownP<T>(c), X, ldx, ncols, rowscale, c->npj, U, xa);
   PAW_LAUNCH_CHECK("k_own_project");
 }
@@ -572,6 +576,7 @@ static ExpArgs exp_args(paw_context *c, int ncols) {
   A.N1 = c->N1;
   A.own_off = c->own_off.as<int>();
   A.own_atom = c->own_atom.as<int>();
+  A.own_ngrp = c->own_ngrp.as<int>();
   A.ncols = ncols;
   return A;
 }

@@ -23,6 +23,7 @@ constexpr int EXP_ADD = 0, EXP_SINV = 1, EXP_RECURRENCE = 2;
 struct ExpArgs {
   int n, p, N1;
   const int *own_off, *own_atom;
+  const int *own_ngrp;           // per pair: groups of 4 projectors with nonzero values
   int ncols;
   const double *cs;              // ADD: per-column factor (may be NULL)
   const void *Xin;               // SINV: X; RECURRENCE: R_Y

@@ -549,6 +549,20 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
       }
     std::vector<float> oPf(oP.size());
     for (size_t i = 0; i < oP.size(); ++i) oPf[i] = (float)oP[i];
+    // groups of 4 projectors up to the last one with a nonzero value on the pair
+    std::vector<int> ngrp(std::max<size_t>(1, keys.size()), 0);
+    for (size_t k = 0; k < keys.size(); ++k) {
+      int last = -1;
+      for (int o = 0; o < c->own; ++o)
+        for (int al = c->npad - 1; al > last; --al)
+          if (oP[k * blk + (size_t)o * c->npad + al] != 0.0) {
+            last = al;
+            break;
+          }
+      ngrp[k] = (last + 4) / 4;
+    }
+    c->own_ngrp.ensure(sizeof(int) * ngrp.size(), &c->dev_bytes);
+    PAW_CUDA(cudaMemcpy(c->own_ngrp.ptr, ngrp.data(), sizeof(int) * ngrp.size(), cudaMemcpyHostToDevice));
     c->own_off.ensure(sizeof(int) * off.size(), &c->dev_bytes);
     c->own_atom.ensure(sizeof(int) * std::max<size_t>(1, oatom.size()), &c->dev_bytes);
     c->ownP64.ensure(sizeof(double) * std::max<size_t>(1, oP.size()), &c->dev_bytes);
