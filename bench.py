@@ -274,7 +274,7 @@ def fe_np1(nc):
 
 # kernels that make up each profiled phase of the filter (library phase brackets)
 PHASE_KERNELS = {
-    "residual_local": "k_local_sf (FP64 sum-factorised 1/2 K + V - lambda M)",
+    "residual_local": "k_local_sf (FP64 even/odd sum-factorised 1/2 K + V - lambda M)",
     "residual_nonlocal": "k_own_project + k_pair_reduce + k_own_couple + k_own_expand (FP64)",
     "recurrence": "k_own_expand (fused Shat^-1 expansion + nonlocal H + recurrence update)",
     "projection": "k_own_project + k_pair_reduce + k_own_couple + k_own_couple_h",
@@ -283,39 +283,62 @@ PHASE_KERNELS = {
 }
 
 
+def sf_flops_per_cell_vec(n1):
+    """FP64 flops of the even/odd sum-factorised (1/2 K + V - lambda M) x per cell and vector
+    (n1 nodes and n1 + 1 Gauss points per direction; FMA = 2 flops, add or multiply = 1)."""
+    q1 = n1 + 1
+
+    def eo(m, n):       # FMAs of one centro-symmetric m x n line product
+        return ((m + 1) // 2) * ((n + 1) // 2) + (m // 2) * (n // 2)
+
+    def split(n):       # adds forming the even/odd halves of a line
+        return 2 * (n // 2)
+
+    def outs(m):        # adds recombining the halves
+        return m - (m & 1)
+
+    lines = n1 * n1
+    fl = 0
+    fl += lines * (split(n1) + 2 * 2 * eo(n1, n1) + 2 * outs(n1))                  # P, Q
+    fl += lines * (2 * split(n1) + 3 * 2 * eo(n1, n1) + n1 * (2 + 1 + 2))        # S, R
+    fl += lines * (2 * split(n1) + 2 * 2 * eo(n1, n1) + n1 * (2 + 2))            # y
+    fl += n1 * n1 * (split(n1) + 2 * eo(q1, n1) + outs(q1))                      # U1
+    fl += q1 * n1 * (split(n1) + 2 * eo(q1, n1) + outs(q1))                      # U2
+    fl += q1 * q1 * (split(n1) + 2 * eo(q1, n1) + outs(q1) + q1)                 # U3 (times w V)
+    fl += q1 * q1 * (split(q1) + 2 * eo(n1, q1) + outs(n1))                      # B2
+    fl += q1 * n1 * (split(q1) + 2 * eo(n1, q1) + outs(n1))                      # B1
+    fl += n1 * n1 * (split(q1) + 2 * eo(n1, q1) + outs(n1) + n1)                 # y += ...
+    return fl
+
+
 def phase_model(phase, fe, cfg, prec):
     """Algorithmic (flops, bytes, compute kind) of one launch of a phase for one block."""
     M, B = fe.ndof, cfg["block"]
     nc, ncells = fe.nodes_per_cell, fe.ncells
     n1 = fe_np1(nc)
-    # algorithmic work counts the nproj projectors only (not the padding to 16)
-    own, npad, pairs = (n1 - 1) ** 3, fe.nproj, fe.owner_pairs
+    # algorithmic projector work: the nonzero entries of P^a on owned nodes
+    # (no padding to 16 projectors, no all-zero projector of a pair)
+    own, pairs, nnz = (n1 - 1) ** 3, fe.owner_pairs, fe.proj_nnz
     f32 = prec != "fp64"
     es = 4 if f32 else 8
     if phase == "cell_products":
         mat_es = {"bf16": 2, "tf32": 4, "fp32": 4, "fp64": 8}[prec]
         if prec == "fp64":   # sum-factorised local H in FP64
-            q1 = n1 + 1
-            fma_cell = 7 * n1 ** 4 + 2 * (q1 * n1 ** 3 + q1 * q1 * n1 ** 2 + q1 ** 3 * n1)
-            return 2.0 * fma_cell * ncells * B, M * B * 8 * 3, "fp64"
+            return float(sf_flops_per_cell_vec(n1)) * ncells * B, M * B * 8 * 3, "fp64"
         kind = {"tf32": "tf32", "bf16": "bf16", "fp32": "fp32"}[prec]
         return 2.0 * ncells * nc * nc * B, ncells * nc * nc * mat_es + M * B * 4 * 3, kind
     if phase == "residual_local":
-        q1 = n1 + 1
-        fma_cell = 7 * n1 ** 4 + 2 * (q1 * n1 ** 3 + q1 * q1 * n1 ** 2 + q1 ** 3 * n1)
-        return 2.0 * fma_cell * ncells * B, M * B * 8 * 3, "fp64"
-    pbytes = pairs * own * npad * es
+        return float(sf_flops_per_cell_vec(n1)) * ncells * B, M * B * 8 * 3, "fp64"
+    pbytes = nnz * es
     if phase == "projection":
-        return (2.0 * pairs * own * npad * B, M * B * es + pbytes + 2 * pairs * npad * B * es,
-                "fp32" if f32 else "fp64")
+        return (2.0 * nnz * B, M * B * es + pbytes + 2 * pairs * fe.nproj * B * es, "fp32" if f32 else "fp64")
     if phase == "recurrence":
         # reads R_Y, R_X and Y (an FP32 hi/lo pair or FP64: 8 bytes), writes T and R_X
-        return (4.0 * pairs * own * npad * B, M * B * (es * 4 + 8) + pbytes,
-                "fp32" if f32 else "fp64")
+        return (4.0 * nnz * B, M * B * (es * 4 + 8) + pbytes, "fp32" if f32 else "fp64")
     if phase == "residual_nonlocal":
-        return (4.0 * pairs * own * npad * B, M * B * 8 * 3 + 2 * pairs * own * npad * 8, "fp64")
+        return (4.0 * nnz * B, M * B * 8 * 3 + 2 * nnz * 8, "fp64")
     if phase == "recovery":
-        return (4.0 * pairs * own * npad * B, M * B * (es * 2 + 8 * 2), "fp32" if f32 else "fp64")
+        return (4.0 * nnz * B, M * B * (es * 2 + 8 * 2), "fp32" if f32 else "fp64")
     return None, None, None
 
 

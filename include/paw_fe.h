@@ -131,6 +131,9 @@ typedef struct {
                               projector contractions                          */
   int32_t nproj_padded;    /* projectors per atom as stored (16 or 32)        */
   int32_t reserved;
+  int64_t proj_nnz;        /* nonzero entries of the assembled P^a on owned nodes,
+                              summed over atoms: the algorithmic size of one
+                              projector contraction (per vector)              */
 } paw_info;
 
 /* Build every operator of the problem (Sec. 4.1): cell matrices

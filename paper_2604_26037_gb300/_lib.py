@@ -69,7 +69,8 @@ class _Info(C.Structure):
     _fields_ = [("ndof", C.c_int64), ("ncells", C.c_int32), ("nodes_per_cell", C.c_int32),
                 ("quad_per_cell", C.c_int32), ("natoms", C.c_int32), ("nproj", C.c_int32),
                 ("degree", C.c_int32), ("support_pairs", C.c_int64), ("device_bytes", C.c_int64),
-                ("owner_pairs", C.c_int64), ("nproj_padded", C.c_int32), ("reserved", C.c_int32)]
+                ("owner_pairs", C.c_int64), ("nproj_padded", C.c_int32), ("reserved", C.c_int32),
+                ("proj_nnz", C.c_int64)]
 
 
 class _Profile(C.Structure):
@@ -222,6 +223,7 @@ class PawFE:
         self.support_pairs = int(info.support_pairs)
         self.owner_pairs = int(info.owner_pairs)
         self.nproj_padded = int(info.nproj_padded)
+        self.proj_nnz = int(info.proj_nnz)
         self.block = int(block)
 
     @classmethod

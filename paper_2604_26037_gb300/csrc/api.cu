@@ -681,6 +681,7 @@ paw_status paw_get_info(paw_handle c, paw_info *out) {
   out->device_bytes = c->dev_bytes;
   out->owner_pairs = c->nown_pairs;
   out->nproj_padded = c->npad;
+  out->proj_nnz = c->proj_nnz;
   out->reserved = 0;
   return PAW_OK;
 }

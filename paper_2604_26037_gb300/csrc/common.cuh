@@ -156,6 +156,7 @@ struct paw_context {
   pawfe::DevBuf own_atom;                     // int32 nown_pairs
   pawfe::DevBuf ownP64, ownP32;               // nown_pairs * own * npad
   pawfe::DevBuf own_ngrp;                     // int32 per pair: projector groups of 4 with a nonzero value
+  int64_t proj_nnz = 0;                       // nonzero (owned node, projector) entries over all pairs
   pawfe::DevBuf apair_off, apair;             // atom-major list of the pairs (int32)
   // atom-pair Gram blocks G_ab = P^a^T M_D^-1 P^b for atoms with common support
   // nodes (CSR over atoms, a included); lets P^T Shat^-1 R follow from P^T M_D^-1 R

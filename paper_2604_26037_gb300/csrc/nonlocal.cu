@@ -122,8 +122,13 @@ __global__ void __launch_bounds__(256) k_own_project(int n, int p, int N1, const
     st4(Xs + (size_t)o * VT + 4 * q, x);
   }
   __syncthreads();
-  const int og = tid / TPG, r = tid - og * TPG;
-  const int aq = r / (VT / 4), vq = r - aq * (VT / 4);
+  // vector quad fastest, then node group, projector quad slowest: the threads of
+  // one projector quad form whole warps, so a quad that is zero on a pair is
+  // skipped by entire warps
+  const int vq = tid % (VT / 4);
+  const int og = (tid / (VT / 4)) % OG;
+  const int aq = tid / ((VT / 4) * OG);
+  static_assert(((VT / 4) * OG) % 32 == 0, "one projector quad must cover whole warps");
   for (int k = k0; k < k1; ++k) {
     const T *Pk = oP + (size_t)k * own * NPAD + aq * 4;
     T acc[4][4];

@@ -551,6 +551,8 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
     for (size_t i = 0; i < oP.size(); ++i) oPf[i] = (float)oP[i];
     // groups of 4 projectors up to the last one with a nonzero value on the pair
     std::vector<int> ngrp(std::max<size_t>(1, keys.size()), 0);
+    c->proj_nnz = 0;
+    for (size_t i = 0; i < oP.size(); ++i) c->proj_nnz += (oP[i] != 0.0) ? 1 : 0;
     for (size_t k = 0; k < keys.size(); ++k) {
       int last = -1;
       for (int o = 0; o < c->own; ++o)

@@ -15,8 +15,13 @@
 // GB300 has little FP64 throughput, so the FP64 paths (Y = H X - S X Lambda,
 // the FP64 filter form, Rayleigh-Ritz products, residuals) use this form.
 //
-// Block: one cell, VT vectors, 256 threads.  Shared-memory tensors are stored
-// [node][vector] so that consecutive threads touch consecutive words.
+// Block: one cell, VT vectors, 256 threads; each 1D contraction handles one
+// line (all points along the contracted direction) per thread, in the even/odd
+// split of the centro-symmetric 1D matrices (about 25.7k FP64 operations per
+// cell and vector at p = 6 instead of 35.7k).  Shared-memory tensors are
+// stored [node][vector] so that consecutive threads touch consecutive words.
+#include <vector>
+
 #include "common.cuh"
 
 namespace pawfe {
@@ -26,9 +31,73 @@ namespace {
 template <int NP>
 constexpr int sf_vt() { return NP >= 9 ? 4 : 8; }
 
+// Even/odd halves of a centro-symmetric 1D matrix A (m x n, A[m-1-i][n-1-j] = A[i][j]):
+//   Ae[i][j] = (A[i][j] + A[i][n-1-j]) / 2   (j < n/2),  Ae[i][n/2] = A[i][n/2] for odd n,
+//   Ao[i][j] = (A[i][j] - A[i][n-1-j]) / 2   (i < m/2, j < n/2),
+// so that with e[j] = x[j] + x[n-1-j] (e[n/2] = x[n/2]) and o[j] = x[j] - x[n-1-j]:
+//   y[i] = E[i] + O[i],  y[m-1-i] = E[i] - O[i],  E = Ae e,  O = Ao o   (y[m/2] = E[m/2] for odd m).
+// The GLL nodes and Gauss points are symmetric about the cell centre, so the 1D mass and
+// stiffness matrices and the Lagrange values at the Gauss points are all of this form.
+constexpr int EOMAX = 5;   // ceil(10 / 2): up to 10 points per direction
+struct EoMat {
+  double e[EOMAX * EOMAX];   // [i < ceil(m/2)][j < ceil(n/2)]
+  double o[EOMAX * EOMAX];   // [i < m/2][j < n/2]
+};
+
 struct SfTables {
-  double M1[81], D1[81], phi[90];   // M1, D1: [np1][np1]; phi: [nq1][np1]
+  EoMat M, D, phi, phit;   // M, D: np1 x np1; phi: nq1 x np1 (Lagrange at Gauss points); phit = phi^T
   double kfac, mfac;
+};
+
+template <int N>
+struct Split {
+  static constexpr int NE = (N + 1) / 2, NO = N / 2;
+  double e[NE], o[NO > 0 ? NO : 1];
+};
+
+// split the line x[0], x[s], ..., x[(N-1) s]
+template <int N>
+__device__ __forceinline__ Split<N> split_line(const double *x, int s) {
+  Split<N> r;
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) {
+    const double a = x[j * s], b = x[(N - 1 - j) * s];
+    r.e[j] = a + b;
+    r.o[j] = a - b;
+  }
+  if (N & 1) r.e[N / 2] = x[(N / 2) * s];
+  return r;
+}
+
+// E[i] += sum_j Ae[i][j] e[j],  O[i] += sum_j Ao[i][j] o[j]  for A of size M x N (in shared memory)
+template <int M, int N>
+__device__ __forceinline__ void eo_acc(const EoMat &A, const Split<N> &x, double (&E)[(M + 1) / 2],
+                                       double (&O)[M / 2 > 0 ? M / 2 : 1]) {
+  constexpr int NE = (N + 1) / 2, NO = N / 2;
+#pragma unroll
+  for (int i = 0; i < (M + 1) / 2; ++i)
+#pragma unroll
+    for (int j = 0; j < NE; ++j) E[i] = fma(A.e[i * NE + j], x.e[j], E[i]);
+#pragma unroll
+  for (int i = 0; i < M / 2; ++i)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) O[i] = fma(A.o[i * NO + j], x.o[j], O[i]);
+}
+
+template <int M>
+struct Half {
+  double E[(M + 1) / 2], O[M / 2 > 0 ? M / 2 : 1];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < (M + 1) / 2; ++i) E[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < (M / 2 > 0 ? M / 2 : 1); ++i) O[i] = 0.0;
+  }
+  // output i of the line
+  __device__ __forceinline__ double out(int i) const {
+    if (2 * i + 1 == M) return E[i];
+    return (i < M / 2) ? E[i] + O[i] : E[M - 1 - i] - O[M - 1 - i];
+  }
 };
 
 template <int NP>
@@ -43,7 +112,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
   constexpr int S1 = (NQ * NP * NP > N3) ? NQ * NP * NP : N3;
   constexpr int S2 = (NQ * NQ * NP > N3) ? NQ * NQ * NP : N3;
   constexpr int S3 = (NQ * NQ * NQ > N3) ? NQ * NQ * NQ : N3;
-  __shared__ double sM[NP * NP], sD[NP * NP], sphi[NQ * NP];
+  __shared__ SfTables st;
   __shared__ int dofs[N3];
   extern __shared__ double sm[];
   double *A0 = sm;                 // x                  [N3][VT]
@@ -53,11 +122,11 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
   double *A4 = A3 + S2 * VT;       // R, then U3         [S3][VT]
   double *sw = A4 + S3 * VT;       // w_q V_q            [NQ^3]
   const int e = blockIdx.x, v0 = blockIdx.y * VT, tid = threadIdx.x;
-  for (int i = tid; i < NP * NP; i += 256) {
-    sM[i] = tab.M1[i];
-    sD[i] = tab.D1[i];
+  {
+    const double *src = reinterpret_cast<const double *>(&tab);
+    double *dst = reinterpret_cast<double *>(&st);
+    for (int i = tid; i < (int)(sizeof(SfTables) / sizeof(double)); i += 256) dst[i] = src[i];
   }
-  for (int i = tid; i < NQ * NP; i += 256) sphi[i] = tab.phi[i];
   for (int i = tid; i < N3; i += 256) dofs[i] = cell_dofs[(size_t)e * N3 + i];
   const bool doV = cV != 0.0;
   if (doV)
@@ -68,113 +137,127 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     A0[idx] = (v0 + v < ncols) ? X[(size_t)dofs[r] * ldx + v0 + v] : 0.0;
   }
   __syncthreads();
-  const double kf = cK * tab.kfac, mf = tab.mfac;
-  // c-contractions: P = M_c x, Q = D_c x
-  for (int idx = tid; idx < N3 * VT; idx += 256) {
-    const int r = idx / VT, v = idx - r * VT;
-    const int ab = r % (NP * NP), c2 = r / (NP * NP);
-    double p = 0.0, q = 0.0;
+  const double kf = cK * st.kfac, mf = st.mfac;
+  // c-contractions, one (a, b) line per thread: P = M_c x, Q = D_c x
+  for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+    const int ab = idx / VT, v = idx - ab * VT;
+    const Split<NP> x = split_line<NP>(A0 + ab * VT + v, NP * NP * VT);
+    Half<NP> P, Q;
+    P.zero();
+    Q.zero();
+    eo_acc<NP, NP>(st.M, x, P.E, P.O);
+    eo_acc<NP, NP>(st.D, x, Q.E, Q.O);
 #pragma unroll
-    for (int c = 0; c < NP; ++c) {
-      const double xv = A0[(c * NP * NP + ab) * VT + v];
-      p = fma(sM[c2 * NP + c], xv, p);
-      q = fma(sD[c2 * NP + c], xv, q);
+    for (int c2 = 0; c2 < NP; ++c2) {
+      A1[(c2 * NP * NP + ab) * VT + v] = P.out(c2);
+      A2[(c2 * NP * NP + ab) * VT + v] = Q.out(c2);
     }
-    A1[idx] = p;
-    A2[idx] = q;
   }
   __syncthreads();
-  // b-contractions: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S
-  for (int idx = tid; idx < N3 * VT; idx += 256) {
-    const int r = idx / VT, v = idx - r * VT;
-    const int a = r % NP, b2 = (r / NP) % NP, c = r / (NP * NP);
-    double s = 0.0, t = 0.0;
+  // b-contractions, one (a, c) line per thread: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S
+  for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+    const int ac = idx / VT, v = idx - ac * VT;
+    const int a = ac % NP, c = ac / NP;
+    const int base = (c * NP * NP + a) * VT + v;
+    const Split<NP> p = split_line<NP>(A1 + base, NP * VT);
+    const Split<NP> q = split_line<NP>(A2 + base, NP * VT);
+    Half<NP> S, T;
+    S.zero();
+    T.zero();
+    eo_acc<NP, NP>(st.M, p, S.E, S.O);
+    eo_acc<NP, NP>(st.D, p, T.E, T.O);
+    eo_acc<NP, NP>(st.M, q, T.E, T.O);
+    const double cmv = (cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0)) * mf;
 #pragma unroll
-    for (int b = 0; b < NP; ++b) {
-      const int src = ((c * NP + b) * NP + a) * VT + v;
-      const double pv = A1[src];
-      s = fma(sM[b2 * NP + b], pv, s);
-      t = fma(sD[b2 * NP + b], pv, t);
-      t = fma(sM[b2 * NP + b], A2[src], t);
+    for (int b2 = 0; b2 < NP; ++b2) {
+      const double sv = S.out(b2);
+      A3[base + b2 * NP * VT] = sv;
+      A4[base + b2 * NP * VT] = fma(kf, T.out(b2), cmv * sv);
     }
-    const double cmv = cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0);
-    A3[idx] = s;
-    A4[idx] = kf * t + cmv * mf * s;
   }
   __syncthreads();
-  // a-contractions: y = kf D_a S + M_a R
-  for (int idx = tid; idx < N3 * VT; idx += 256) {
-    const int r = idx / VT, v = idx - r * VT;
-    const int a2 = r % NP, bc = r / NP;
-    double y = 0.0;
+  // a-contractions, one (b, c) line per thread: y = kf D_a S + M_a R
+  for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+    const int bc = idx / VT, v = idx - bc * VT;
+    const int base = bc * NP * VT + v;
+    const Split<NP> sl = split_line<NP>(A3 + base, VT);
+    const Split<NP> rl = split_line<NP>(A4 + base, VT);
+    Half<NP> YD, YM;
+    YD.zero();
+    YM.zero();
+    eo_acc<NP, NP>(st.D, sl, YD.E, YD.O);
+    eo_acc<NP, NP>(st.M, rl, YM.E, YM.O);
 #pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      const int src = (bc * NP + a) * VT + v;
-      y = fma(kf * sD[a2 * NP + a], A3[src], y);
-      y = fma(sM[a2 * NP + a], A4[src], y);
-    }
-    A1[idx] = y;
+    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = fma(kf, YD.out(a2), YM.out(a2));
   }
   if (doV) {
     __syncthreads();
-    // U1[c][b][i] = sum_a phi[i][a] x[c][b][a]
-    for (int idx = tid; idx < NQ * NP * NP * VT; idx += 256) {
-      const int r = idx / VT, v = idx - r * VT;
-      const int i = r % NQ, bc = r / NQ;
-      double u = 0.0;
+    // U1[c][b][i] = sum_a phi[i][a] x[c][b][a]            (line (b, c), NP -> NQ)
+    for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+      const int bc = idx / VT, v = idx - bc * VT;
+      const Split<NP> x = split_line<NP>(A0 + bc * NP * VT + v, VT);
+      Half<NQ> U;
+      U.zero();
+      eo_acc<NQ, NP>(st.phi, x, U.E, U.O);
 #pragma unroll
-      for (int a = 0; a < NP; ++a) u = fma(sphi[i * NP + a], A0[(bc * NP + a) * VT + v], u);
-      A2[idx] = u;
+      for (int i = 0; i < NQ; ++i) A2[(bc * NQ + i) * VT + v] = U.out(i);
     }
     __syncthreads();
-    // U2[c][j][i] = sum_b phi[j][b] U1[c][b][i]
-    for (int idx = tid; idx < NQ * NQ * NP * VT; idx += 256) {
-      const int r = idx / VT, v = idx - r * VT;
-      const int i = r % NQ, j = (r / NQ) % NQ, c = r / (NQ * NQ);
-      double u = 0.0;
+    // U2[c][j][i] = sum_b phi[j][b] U1[c][b][i]           (line (i, c))
+    for (int idx = tid; idx < NQ * NP * VT; idx += 256) {
+      const int ic = idx / VT, v = idx - ic * VT;
+      const int i = ic % NQ, c = ic / NQ;
+      const Split<NP> x = split_line<NP>(A2 + (c * NP * NQ + i) * VT + v, NQ * VT);
+      Half<NQ> U;
+      U.zero();
+      eo_acc<NQ, NP>(st.phi, x, U.E, U.O);
 #pragma unroll
-      for (int b = 0; b < NP; ++b) u = fma(sphi[j * NP + b], A2[((c * NP + b) * NQ + i) * VT + v], u);
-      A3[idx] = u;
+      for (int j = 0; j < NQ; ++j) A3[((c * NQ + j) * NQ + i) * VT + v] = U.out(j);
     }
     __syncthreads();
-    // U3[k][j][i] = w_q V_q sum_c phi[k][c] U2[c][j][i]
-    for (int idx = tid; idx < NQ * NQ * NQ * VT; idx += 256) {
-      const int r = idx / VT, v = idx - r * VT;
-      const int ji = r % (NQ * NQ), k = r / (NQ * NQ);
-      double u = 0.0;
+    // U3[k][j][i] = w_q V_q sum_c phi[k][c] U2[c][j][i]    (line (i, j))
+    for (int idx = tid; idx < NQ * NQ * VT; idx += 256) {
+      const int ji = idx / VT, v = idx - ji * VT;
+      const Split<NP> x = split_line<NP>(A3 + ji * VT + v, NQ * NQ * VT);
+      Half<NQ> U;
+      U.zero();
+      eo_acc<NQ, NP>(st.phi, x, U.E, U.O);
 #pragma unroll
-      for (int c = 0; c < NP; ++c) u = fma(sphi[k * NP + c], A3[(c * NQ * NQ + ji) * VT + v], u);
-      A4[idx] = u * sw[r];
+      for (int k = 0; k < NQ; ++k) A4[(k * NQ * NQ + ji) * VT + v] = U.out(k) * sw[k * NQ * NQ + ji];
     }
     __syncthreads();
-    // B2[c][j][i] = sum_k phi[k][c] U3[k][j][i]
-    for (int idx = tid; idx < NQ * NQ * NP * VT; idx += 256) {
-      const int r = idx / VT, v = idx - r * VT;
-      const int ji = r % (NQ * NQ), c = r / (NQ * NQ);
-      double u = 0.0;
+    // B2[c][j][i] = sum_k phi[k][c] U3[k][j][i]            (line (i, j), NQ -> NP)
+    for (int idx = tid; idx < NQ * NQ * VT; idx += 256) {
+      const int ji = idx / VT, v = idx - ji * VT;
+      const Split<NQ> x = split_line<NQ>(A4 + ji * VT + v, NQ * NQ * VT);
+      Half<NP> B;
+      B.zero();
+      eo_acc<NP, NQ>(st.phit, x, B.E, B.O);
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) u = fma(sphi[k * NP + c], A4[(k * NQ * NQ + ji) * VT + v], u);
-      A3[idx] = u;
+      for (int c = 0; c < NP; ++c) A3[(c * NQ * NQ + ji) * VT + v] = B.out(c);
     }
     __syncthreads();
-    // B1[c][b][i] = sum_j phi[j][b] B2[c][j][i]
-    for (int idx = tid; idx < NQ * NP * NP * VT; idx += 256) {
-      const int r = idx / VT, v = idx - r * VT;
-      const int i = r % NQ, b = (r / NQ) % NP, c = r / (NQ * NP);
-      double u = 0.0;
+    // B1[c][b][i] = sum_j phi[j][b] B2[c][j][i]            (line (i, c))
+    for (int idx = tid; idx < NQ * NP * VT; idx += 256) {
+      const int ic = idx / VT, v = idx - ic * VT;
+      const int i = ic % NQ, c = ic / NQ;
+      const Split<NQ> x = split_line<NQ>(A3 + (c * NQ * NQ + i) * VT + v, NQ * VT);
+      Half<NP> B;
+      B.zero();
+      eo_acc<NP, NQ>(st.phit, x, B.E, B.O);
 #pragma unroll
-      for (int j = 0; j < NQ; ++j) u = fma(sphi[j * NP + b], A3[((c * NQ + j) * NQ + i) * VT + v], u);
-      A2[idx] = u;
+      for (int b = 0; b < NP; ++b) A2[((c * NP + b) * NQ + i) * VT + v] = B.out(b);
     }
     __syncthreads();
-    // y[c][b][a] += sum_i phi[i][a] B1[c][b][i]
-    for (int idx = tid; idx < N3 * VT; idx += 256) {
-      const int r = idx / VT, v = idx - r * VT;
-      const int a = r % NP, bc = r / NP;
-      double u = 0.0;
+    // y[c][b][a] += sum_i phi[i][a] B1[c][b][i]            (line (b, c))
+    for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+      const int bc = idx / VT, v = idx - bc * VT;
+      const Split<NQ> x = split_line<NQ>(A2 + bc * NQ * VT + v, VT);
+      Half<NP> B;
+      B.zero();
+      eo_acc<NP, NQ>(st.phit, x, B.E, B.O);
 #pragma unroll
-      for (int i = 0; i < NQ; ++i) u = fma(sphi[i * NP + a], A2[(bc * NQ + i) * VT + v], u);
-      A1[idx] += u;
+      for (int a = 0; a < NP; ++a) A1[(bc * NP + a) * VT + v] += B.out(a);
     }
   }
   __syncthreads();
@@ -213,16 +296,32 @@ __global__ void k_wV(int64_t n, int nq, const double *__restrict__ wq, const dou
 
 }  // namespace
 
+// even/odd halves of a row-major m x n matrix (see EoMat); the matrix is
+// centro-symmetric up to rounding, and the halves use its symmetrised form
+static void eo_halves(const double *A, int m, int n, EoMat &out) {
+  const int ne = (n + 1) / 2, no = n / 2;
+  for (int i = 0; i < (m + 1) / 2; ++i) {
+    for (int j = 0; j < no; ++j)
+      out.e[i * ne + j] = 0.5 * (A[(size_t)i * n + j] + A[(size_t)i * n + (n - 1 - j)]);
+    if (n & 1) out.e[i * ne + no] = A[(size_t)i * n + no];
+  }
+  for (int i = 0; i < m / 2; ++i)
+    for (int j = 0; j < no; ++j)
+      out.o[i * no + j] = 0.5 * (A[(size_t)i * n + j] - A[(size_t)i * n + (n - 1 - j)]);
+}
+
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha, double cK,
               double cV, double cM, const double *cMcol, cudaStream_t s) {
   if (ncols <= 0) return;
   SfTables t{};
   const int np1 = c->np1, nq1 = c->nq1;
-  for (int i = 0; i < np1 * np1; ++i) {
-    t.M1[i] = c->M1[i];
-    t.D1[i] = c->D1[i];
-  }
-  for (int i = 0; i < nq1 * np1; ++i) t.phi[i] = c->phiq[i];
+  std::vector<double> phit((size_t)np1 * nq1);
+  for (int q = 0; q < nq1; ++q)
+    for (int a = 0; a < np1; ++a) phit[(size_t)a * nq1 + q] = c->phiq[(size_t)q * np1 + a];
+  eo_halves(c->M1.data(), np1, np1, t.M);
+  eo_halves(c->D1.data(), np1, np1, t.D);
+  eo_halves(c->phiq.data(), nq1, np1, t.phi);
+  eo_halves(phit.data(), np1, nq1, t.phit);
   const double hh = c->h / 2.0;
   t.kfac = 0.5 * hh;
   t.mfac = hh * hh * hh;
