@@ -106,7 +106,9 @@ typedef struct {
   int32_t block;       /* vector block width B of paw_cheb_filter (0: 256)      */
   int32_t pp_overlap;  /* 1: use G_a = <p|p> (Sec. 3.1, third approximation)     */
   int32_t y0_fp32;     /* 1: store Y = H X - S X Lambda in FP32 in mixed modes   */
-  int32_t reserved;
+  int32_t rr_mixed;    /* 1: paw_rayleigh_ritz rotates with the diagonal of Q in
+                          FP64 and its off-diagonal part in FP32 (Sec. 4.4,
+                          mixed-precision subspace rotation)                    */
 } paw_options;
 
 /* Filter bounds (Algorithm 2 inputs): a0 lower end of the wanted spectrum,
@@ -295,8 +297,11 @@ paw_status paw_batch_destroy(paw_batch b);
  *                Ritz vectors in ascending order of Ritz value
  *   lambda_out : host FP64 N
  * H X and S X are formed block by block (opts.block columns) with the FP64
- * cell kernels; the projections and the rotation use cuBLAS DGEMM and the
- * projected problem cuSOLVER dsygvd.
+ * cell kernels; only the lower triangle of H^p and S^p is projected (column
+ * block j0 gives rows j0..N-1, cuBLAS DGEMM), the projected problem is solved
+ * by cuSOLVER dsygvd.  The rotation is a DGEMM over row chunks, or with
+ * opts.rr_mixed = 1: X <- X diag(Q) in FP64 plus fl32(X) (Q - diag(Q)) as an
+ * FP32 GEMM (Sec. 4.4: the off-diagonal part of Q is small near convergence).
  * Errors: NOT_SPD (S^p not positive definite), LIBRARY, NO_MEMORY. */
 paw_status paw_rayleigh_ritz(paw_handle h, double *X, int ld, int N,
                              double *lambda_out, void *stream);

@@ -58,7 +58,7 @@ class _Vloc(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("block", C.c_int32), ("pp_overlap", C.c_int32), ("y0_fp32", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("rr_mixed", C.c_int32)]
 
 
 class _Bounds(C.Structure):
@@ -186,7 +186,7 @@ class PawFE:
     """One PAW finite-element problem on the current CUDA device."""
 
     def __init__(self, L, ncell, degree, positions=(), shells=(), D=None, dS=None,
-                 vloc=None, block=256, pp_overlap=False, y0_fp32=False):
+                 vloc=None, block=256, pp_overlap=False, y0_fp32=False, rr_mixed=False):
         self._lib = load_library()
         pos = np.ascontiguousarray(np.asarray(positions, float).reshape(-1, 3))
         na = pos.shape[0]
@@ -208,7 +208,7 @@ class PawFE:
             wid = np.ascontiguousarray(np.asarray(vloc["width"], float))
             keep += [cen, dep, wid]
             vp = C.pointer(_Vloc(cen.shape[0], _dptr(cen), _dptr(dep), _dptr(wid)))
-        opts = _Opts(int(block), int(bool(pp_overlap)), int(bool(y0_fp32)), 0)
+        opts = _Opts(int(block), int(bool(pp_overlap)), int(bool(y0_fp32)), int(bool(rr_mixed)))
         h = C.c_void_p()
         _check(self._lib.paw_fe_create(C.byref(mesh), int(degree), C.byref(atoms), C.byref(proj),
                                        _dptr(Dh), _dptr(dSh), vp, C.byref(opts), C.byref(h)))

@@ -481,6 +481,33 @@ __global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__res
 }
 
 // dD[a][al][be] = sum_v U[a][al][v] U[a][be][v]
+// Mixed-precision subspace rotation (Sec. 4.4): q32 = fl32(Q) with a zero
+// diagonal (column-major N x N), qd = diag(Q) in FP64.
+__global__ void k_split_q(int N, const double *__restrict__ Q, float *__restrict__ q32, double *__restrict__ qd) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)N * N) return;
+  const int r = (int)(i % N), col = (int)(i / N);
+  q32[i] = (r == col) ? 0.f : (float)Q[i];
+  if (r == col) qd[col] = Q[i];
+}
+
+// x32[r][j] = fl32(X[r][j]) for nr rows of N columns (X row pitch ld)
+__global__ void k_rows_to_f32(int nr, int N, const double *__restrict__ X, int ld, float *__restrict__ x32) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nr * N) return;
+  const size_t r = i / N, j = i % N;
+  x32[i] = (float)X[r * ld + j];
+}
+
+// X[r][j] = X[r][j] Q[j][j] + t32[r][j]   (FP64 combination)
+__global__ void k_rot_combine(int nr, int N, const double *__restrict__ qd, const float *__restrict__ t32,
+                              double *__restrict__ X, int ld) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nr * N) return;
+  const size_t r = i / N, j = i % N;
+  X[r * ld + j] = fma(X[r * ld + j], qd[j], (double)t32[i]);
+}
+
 template <typename T>
 // dD[a][ext(al)][ext(be)] = sum_v U[a][al][v] U[a][be][v]  (ext: internal -> caller's projector index)
 __global__ void k_grad_D(int npj, int npad, const T *__restrict__ U, int ldu, int ncols, const int *__restrict__ ext,
@@ -808,15 +835,16 @@ paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lam
   cublasSetStream(c->cublas, s);
   cusolverDnSetStream(c->cusolver, s);
   const double one = 1.0, zero = 0.0;
+  // lower triangle only (dsygvd reads the lower part): column block j0..j0+nb gets rows j0..N-1
   for (int j0 = 0; j0 < N; j0 += Bc) {
-    const int nb = std::min(Bc, N - j0);
+    const int nb = std::min(Bc, N - j0), nr = N - j0;
     op_H<double>(c, PAW_FP64, X + j0, ld, HX, nb, nb, s);
-    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, N, nb, M, &one, X, ld, HX, nb, &zero, Hp + (size_t)j0 * N,
-                    N) != CUBLAS_STATUS_SUCCESS)
+    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, nr, nb, M, &one, X + j0, ld, HX, nb, &zero,
+                    Hp + (size_t)j0 * N + j0, N) != CUBLAS_STATUS_SUCCESS)
       throw Error{PAW_ERR_LIBRARY, "cublasDgemm (H^p) failed"};
     op_S<double>(c, X + j0, ld, HX, nb, nb, s);
-    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, N, nb, M, &one, X, ld, HX, nb, &zero, Sp + (size_t)j0 * N,
-                    N) != CUBLAS_STATUS_SUCCESS)
+    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, nr, nb, M, &one, X + j0, ld, HX, nb, &zero,
+                    Sp + (size_t)j0 * N + j0, N) != CUBLAS_STATUS_SUCCESS)
       throw Error{PAW_ERR_LIBRARY, "cublasDgemm (S^p) failed"};
   }
   int lwork = 0;
@@ -837,15 +865,37 @@ paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lam
   PAW_REQUIRE(info == 0, PAW_ERR_LIBRARY, "dsygvd did not converge");
   // rotation X <- X Q in row chunks
   const int rows = std::min(M, std::max(1024, (1 << 27) / N));   // temp <= 1 GiB
-  c->ws_rot.ensure(sizeof(double) * (size_t)rows * N, &c->dev_bytes);
-  double *tmp = c->ws_rot.as<double>();
-  for (int r0 = 0; r0 < M; r0 += rows) {
-    const int nr = std::min(rows, M - r0);
-    if (cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, N, nr, N, &one, Hp, N, X + (size_t)r0 * ld, ld, &zero, tmp,
-                    N) != CUBLAS_STATUS_SUCCESS)
-      throw Error{PAW_ERR_LIBRARY, "cublasDgemm (rotation) failed"};
-    PAW_CUDA(cudaMemcpy2DAsync(X + (size_t)r0 * ld, sizeof(double) * ld, tmp, sizeof(double) * N, sizeof(double) * N,
-                               nr, cudaMemcpyDeviceToDevice, s));
+  if (c->opts.rr_mixed) {
+    // X <- X diag(Q) (FP64) + fl32(X) fl32(Q - diag(Q)) (FP32 GEMM, FP32 accumulation)
+    c->ws_rot.ensure(sizeof(float) * ((size_t)N * N + 2 * (size_t)rows * N) + sizeof(double) * N, &c->dev_bytes);
+    double *qd = c->ws_rot.as<double>();
+    float *q32 = reinterpret_cast<float *>(qd + N);
+    float *x32 = q32 + (size_t)N * N, *t32 = x32 + (size_t)rows * N;
+    k_split_q<<<(unsigned)(((size_t)N * N + 255) / 256), 256, 0, s>>>(N, Hp, q32, qd);
+    PAW_LAUNCH_CHECK("k_split_q");
+    const float onef = 1.f, zerof = 0.f;
+    for (int r0 = 0; r0 < M; r0 += rows) {
+      const int nr = std::min(rows, M - r0);
+      const size_t n = (size_t)nr * N;
+      k_rows_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nr, N, X + (size_t)r0 * ld, ld, x32);
+      PAW_LAUNCH_CHECK("k_rows_to_f32");
+      if (cublasSgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, N, nr, N, &onef, q32, N, x32, N, &zerof, t32, N) !=
+          CUBLAS_STATUS_SUCCESS)
+        throw Error{PAW_ERR_LIBRARY, "cublasSgemm (off-diagonal rotation) failed"};
+      k_rot_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nr, N, qd, t32, X + (size_t)r0 * ld, ld);
+      PAW_LAUNCH_CHECK("k_rot_combine");
+    }
+  } else {
+    c->ws_rot.ensure(sizeof(double) * (size_t)rows * N, &c->dev_bytes);
+    double *tmp = c->ws_rot.as<double>();
+    for (int r0 = 0; r0 < M; r0 += rows) {
+      const int nr = std::min(rows, M - r0);
+      if (cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, N, nr, N, &one, Hp, N, X + (size_t)r0 * ld, ld, &zero,
+                      tmp, N) != CUBLAS_STATUS_SUCCESS)
+        throw Error{PAW_ERR_LIBRARY, "cublasDgemm (rotation) failed"};
+      PAW_CUDA(cudaMemcpy2DAsync(X + (size_t)r0 * ld, sizeof(double) * ld, tmp, sizeof(double) * N,
+                                 sizeof(double) * N, nr, cudaMemcpyDeviceToDevice, s));
+    }
   }
   PAW_CUDA(cudaMemcpyAsync(lambda_out, c->ws_eig.ptr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   PAW_CUDA(cudaStreamSynchronize(s));

@@ -27,6 +27,23 @@ def test_rayleigh_ritz_and_residuals():
     assert np.abs(r - r_ref).max() < 1e-9 * r_ref.max()
 
 
+def test_rayleigh_ritz_mixed_rotation():
+    """rr_mixed: the projected problem is the same FP64 one (same Ritz values); the
+    rotation uses FP64 for diag(Q) and an FP32 GEMM for the rest, so the Ritz vectors
+    agree with the FP64 rotation to FP32 accuracy relative to their size."""
+    op = oracle_ops("tiny")
+    X = np.random.default_rng(8).standard_normal((op.mesh.ndof, 12))
+    Psi_ref, lam_ref = rr.rayleigh_ritz(op, X)
+    fe = gpu_fe("tiny", rr_mixed=True)
+    Xd = to_dev(X)
+    lam = fe.rayleigh_ritz(Xd)
+    assert np.abs(lam - lam_ref).max() < 1e-10 * max(1, np.abs(lam_ref).max())
+    Psi = Xd.cpu().numpy()
+    sgn = np.sign(np.sum(Psi * Psi_ref, 0))
+    err = rel_err(Psi * sgn, Psi_ref)
+    assert 1e-12 < err < 1e-5, err   # FP32-level, not FP64-level
+
+
 def test_lanczos_bounds_cover_spectrum():
     """The library's Lanczos runs on Shat^-1 H, the operator that Algorithm 1
     step 2 scales and shifts; its bound must cover that spectrum."""
@@ -56,16 +73,17 @@ def _rchfsi_gpu(fe, X0, m, iters, prec, nwanted):
     return X, lam, hist
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32-y32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32-y32", "tf32-rrmix"])
 def test_rchfsi_converges_to_dense(prec):
     """tiny workload: 10 iterations, degree 20; 8 lowest eigenvalues within 1e-6 Ha of
     the dense FP64 generalised eigensolve of the oracle's matrices ("-y32": the
-    residual block Y kept in FP32 only)."""
+    residual block Y kept in FP32 only; "-rrmix": mixed-precision subspace rotation)."""
     op = oracle_ops("tiny")
     lam_ex, V_ex = rr.dense_eigs(op, 8)
     y32 = prec.endswith("-y32")
+    rrmix = prec.endswith("-rrmix")
     prec = prec.split("-")[0]
-    fe = gpu_fe("tiny", block=16, y0_fp32=y32)
+    fe = gpu_fe("tiny", block=16, y0_fp32=y32, rr_mixed=rrmix)
     X0 = inputs.start_columns("tiny", range(16))
     X, lam, hist = _rchfsi_gpu(fe, X0, 20, 10, prec, 8)
     err = np.abs(lam[:8] - lam_ex).max()
