@@ -240,6 +240,28 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": units_per_step * ws / t_e2e / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * 8 + N * 8), "d2h_bytes_per_step": int(Oh.numel() * 8)}
 
+    # Rayleigh-Ritz on the filtered block: FP64 rotation vs the mixed-precision one (rr_mixed)
+    rrm = None
+    if args.rr:
+        def rr_time(h, Xs):
+            Xc = Xs.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam_r = h.rayleigh_ritz(Xc)             # synchronises (host eigenvalues)
+            return time.perf_counter() - t0, lam_r, Xc
+        rr_time(fe, out)                            # warm
+        t64, lam64, X64 = rr_time(fe, out)
+        fe_mx = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, rr_mixed=True)
+        rr_time(fe_mx, out)
+        tmx, lammx, Xmx = rr_time(fe_mx, out)
+        sgn = torch.sign((X64 * Xmx).sum(0))
+        rrm = {"vectors": N, "fp64_rotation_s": round(t64, 4), "mixed_rotation_s": round(tmx, 4),
+               "speedup": round(t64 / tmx, 3), "max_ritz_value_diff": float(np.abs(lam64 - lammx).max()),
+               "max_vector_diff_rel": float((X64 - Xmx * sgn).abs().max() / X64.abs().max()),
+               "projection": "lower triangle (column blocks)"}
+        fe_mx.close()
+        del X64, Xmx
+
     # roofline of the dominant phase
     peaks = _peaks()
     phases = {k: v for k, v in prof.items() if isinstance(v, dict)}
@@ -270,6 +292,8 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
         "bounds": [float(b) for b in bounds],
     }
+    if rrm is not None:
+        res["rayleigh_ritz"] = rrm
     fe.close()
     return res
 
@@ -511,6 +535,8 @@ def main():
     ap.add_argument("--y0-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rr", action="store_true",
+                    help="also time Rayleigh-Ritz on the filtered block, FP64 vs mixed-precision rotation")
     ap.add_argument("--start", default="ritz", choices=["ritz", "random"],
                     help="start block: Ritz vectors of a random block (default) or the random block itself")
     args = ap.parse_args()

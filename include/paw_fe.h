@@ -329,6 +329,19 @@ paw_status paw_energy(paw_handle h, paw_precision prec, const void *X, int ld, i
 paw_status paw_energy_grad(paw_handle h, paw_precision prec, const void *X, int ld,
                            int N, double *dE_dV, double *dE_dD, void *stream);
 
+/* Valence pseudo-density and PAW occupation matrices of a block of states
+ * (Eq. FE PAW governing equations at the Gamma point, one spin channel; the
+ * core density and the compensation charges are not included):
+ *   rho_q : device FP64 ncells x (p+2)^3, sum_i f_i u_i(x_q)^2 at the Gauss
+ *           points of every cell, u_i the FE function of column i
+ *   D_a   : device FP64 natoms x nproj x nproj (may be NULL),
+ *           sum_i f_i U_i U_i^T with U_i = P^a^T x_i (caller's projector order)
+ *   occ   : host FP64 N occupations f_i (NULL: all 1)
+ * X is FP64 (PAW_FP64) or FP32 (other precisions).  The same contractions as
+ * paw_energy_grad, without the quadrature weights.  Synchronises `stream`. */
+paw_status paw_density(paw_handle h, paw_precision prec, const void *X, int ld, int N,
+                       const double *occ, double *rho_q, double *D_a, void *stream);
+
 /* Phase timing of paw_cheb_filter (tracing, not part of the method).  When
  * enabled, every phase of Algorithm 2 is bracketed by CUDA events recorded on
  * the caller's stream; paw_profile_read synchronises and returns the summed

@@ -33,3 +33,25 @@ def energy_grad(ops, X):
         Ua = Pv.T @ X[dofs]
         dD[a] = Ua @ Ua.T
     return dV, dD
+
+
+def density(ops, X, occ=None):
+    """Valence pseudo-density at the Gauss points and PAW occupation matrices.
+
+    Eq. FE PAW governing equations at the Gamma point, one spin channel, without
+    the core density and the compensation charges:
+      rho(x_q) = sum_i f_i u_i(x_q)^2,          u_i = sum_I N_I(x_q) X_{e,I,i}
+      D^a      = sum_i f_i U^a_i (U^a_i)^T,     U^a = P^a^T X
+    Returns (rho as (ncells, nq), D as (natoms, npj, npj)).
+    """
+    X = np.asarray(X, float)
+    f = np.ones(X.shape[1]) if occ is None else np.asarray(occ, float)
+    Xe = X[ops.mesh.cell_dofs]                                # (ncells, nc, n)
+    U = np.einsum("qj,ejv->eqv", ops.Nq, Xe)
+    rho = np.einsum("eqv,v->eq", U * U, f)
+    D = np.empty((ops.natoms, ops.npj, ops.npj))
+    for a in range(ops.natoms):
+        dofs, Pv = ops.P[a]
+        Ua = Pv.T @ X[dofs]
+        D[a] = (Ua * f) @ Ua.T
+    return rho, D

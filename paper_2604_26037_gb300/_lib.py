@@ -115,6 +115,7 @@ SIGNATURES = {
     "paw_lanczos_bounds": [_VP, _I, C.c_uint64, _DP, _DP, _VP],
     "paw_energy": [_VP, _I, _VP, _I, _I, _DP, _VP],
     "paw_energy_grad": [_VP, _I, _VP, _I, _I, _VP, _VP, _VP],
+    "paw_density": [_VP, _I, _VP, _I, _I, _DP, _VP, _VP, _VP],
     "paw_profile_enable": [_VP, _I],
     "paw_profile_read": [_VP, C.c_void_p],
     "paw_sync_status": [_VP],
@@ -355,6 +356,20 @@ class PawFE:
         _check(self._lib.paw_energy_grad(self._h, prec, xp, ld, n, C.c_void_p(dV.data_ptr()),
                                          C.c_void_p(dD.data_ptr()), _stream(X)))
         return dV, dD[: self.natoms]
+
+    def density(self, X, occ=None, prec="fp64"):
+        """(rho at the Gauss points of every cell, occupation matrices D^a) of the block X."""
+        import torch
+        prec = Precision.of(prec)
+        xp, rows, n, ld = _mat(X, torch.float64 if prec == Precision.FP64 else torch.float32)
+        rho = torch.empty((self.ncells, self.quad_per_cell), dtype=torch.float64, device=X.device)
+        Dm = torch.zeros((max(self.natoms, 1), self.nproj, self.nproj), dtype=torch.float64, device=X.device)
+        f = None if occ is None else np.ascontiguousarray(np.asarray(occ, float).reshape(-1))
+        if f is not None and f.size != n:
+            raise ValueError("one occupation per column")
+        _check(self._lib.paw_density(self._h, prec, xp, ld, n, _dptr(f) if f is not None else None,
+                                     C.c_void_p(rho.data_ptr()), C.c_void_p(Dm.data_ptr()), _stream(X)))
+        return rho, Dm[: self.natoms]
 
 
 class PawBatch:

@@ -453,12 +453,13 @@ __global__ void k_random_vec(int64_t n, uint64_t seed, double *__restrict__ v) {
 }
 
 // ============================================================== gradient kernels
-// dV[e][q] = wq[q] * sum_v (sum_I Nq[q][I] X[dof_e(I)][v])^2, one block per cell
+// dV[e][q] = wq[q] * sum_v f[v] (sum_I Nq[q][I] X[dof_e(I)][v])^2, one block per cell
+// (wq NULL: 1, the values at the points; f NULL: 1)
 template <typename T>
 __global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__restrict__ cell_dofs,
                                                 const double *__restrict__ Nq, const double *__restrict__ wq,
                                                 const T *__restrict__ X, int ldx, int ncols,
-                                                double *__restrict__ dV) {
+                                                const double *__restrict__ f, double *__restrict__ dV) {
   extern __shared__ double xs[];   // [nc][32]
   const int e = blockIdx.x;
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -470,17 +471,17 @@ __global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__res
       xs[idx] = (v0 + v < ncols) ? (double)X[(size_t)cell_dofs[(size_t)e * nc + I] * ldx + v0 + v] : 0.0;
     }
     __syncthreads();
+    const double fv = (f && v0 + lane < ncols) ? f[v0 + lane] : 1.0;
     for (int q = grp; q < nq; q += 8) {
       double u = 0.0;
       for (int I = 0; I < nc; ++I) u += Nq[(size_t)q * nc + I] * xs[I * 32 + lane];
-      double s = u * u;
+      double s = fv * u * u;
       for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (lane == 0) dV[(size_t)e * nq + q] += wq[q] * s;
+      if (lane == 0) dV[(size_t)e * nq + q] += (wq ? wq[q] : 1.0) * s;
     }
   }
 }
 
-// dD[a][al][be] = sum_v U[a][al][v] U[a][be][v]
 // Mixed-precision subspace rotation (Sec. 4.4): q32 = fl32(Q) with a zero
 // diagonal (column-major N x N), qd = diag(Q) in FP64.
 __global__ void k_split_q(int N, const double *__restrict__ Q, float *__restrict__ q32, double *__restrict__ qd) {
@@ -508,16 +509,18 @@ __global__ void k_rot_combine(int nr, int N, const double *__restrict__ qd, cons
   X[r * ld + j] = fma(X[r * ld + j], qd[j], (double)t32[i]);
 }
 
+// dD[a][ext(al)][ext(be)] = sum_v f[v] U[a][al][v] U[a][be][v]  (ext: internal -> caller's
+// projector index; f NULL: 1)
 template <typename T>
-// dD[a][ext(al)][ext(be)] = sum_v U[a][al][v] U[a][be][v]  (ext: internal -> caller's projector index)
 __global__ void k_grad_D(int npj, int npad, const T *__restrict__ U, int ldu, int ncols, const int *__restrict__ ext,
-                         double *__restrict__ dD) {
+                         const double *__restrict__ f, double *__restrict__ dD) {
   const int a = blockIdx.x;
   for (int o = threadIdx.x; o < npj * npj; o += blockDim.x) {
     const int al = o / npj, be = o % npj;
     double s = 0.0;
     for (int v = 0; v < ncols; ++v)
-      s += (double)U[((size_t)a * npad + al) * ldu + v] * (double)U[((size_t)a * npad + be) * ldu + v];
+      s += (f ? f[v] : 1.0) * (double)U[((size_t)a * npad + al) * ldu + v] *
+           (double)U[((size_t)a * npad + be) * ldu + v];
     dD[(size_t)a * npj * npj + (size_t)ext[al] * npj + ext[be]] = s;
   }
 }
@@ -1003,6 +1006,37 @@ paw_status paw_energy(paw_handle c, paw_precision prec, const void *X, int ld, i
   PAW_TRY_END
 }
 
+// outV[e][q] = wq[q] sum_v f[v] u_v(x_q)^2 and outD[a] = sum_v f[v] U_v U_v^T (wq, f optional)
+static void density_like(paw_context *c, paw_precision prec, const void *X, int ld, int N, const double *wq,
+                         const double *f, double *outV, double *outD, cudaStream_t s) {
+  const size_t shm = sizeof(double) * c->nc * 32;
+  if (prec == PAW_FP64) {
+    PAW_CUDA(cudaFuncSetAttribute(k_grad_V<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_grad_V<double><<<c->ncells, 256, shm, s>>>(c->nc, c->nq, c->cell_dofs.as<int>(), c->Nq64.as<double>(), wq,
+                                                  (const double *)X, ld, N, f, outV);
+  } else {
+    PAW_CUDA(cudaFuncSetAttribute(k_grad_V<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_grad_V<float><<<c->ncells, 256, shm, s>>>(c->nc, c->nq, c->cell_dofs.as<int>(), c->Nq64.as<double>(), wq,
+                                                 (const float *)X, ld, N, f, outV);
+  }
+  PAW_LAUNCH_CHECK("k_grad_V");
+  if (c->nown_pairs > 0 && outD) {
+    if (prec == PAW_FP64) {
+      c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
+      nl_project<double>(c, PAW_FP64, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
+      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N,
+                                                 c->proj_ext_dev.as<int>(), f, outD);
+    } else {
+      c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
+      // projector coefficients stay in FP32 arithmetic
+      nl_project<float>(c, PAW_FP32, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
+      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N,
+                                                c->proj_ext_dev.as<int>(), f, outD);
+    }
+    PAW_LAUNCH_CHECK("k_grad_D");
+  }
+}
+
 paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int ld, int N, double *dE_dV,
                            double *dE_dD, void *stream) {
   PAW_TRY_BEGIN
@@ -1011,32 +1045,28 @@ paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int 
   PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
-  const size_t shm = sizeof(double) * c->nc * 32;
-  if (prec == PAW_FP64) {
-    PAW_CUDA(cudaFuncSetAttribute(k_grad_V<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_grad_V<double><<<c->ncells, 256, shm, s>>>(c->nc, c->nq, c->cell_dofs.as<int>(), c->Nq64.as<double>(),
-                                                  c->wq64.as<double>(), (const double *)X, ld, N, dE_dV);
-  } else {
-    PAW_CUDA(cudaFuncSetAttribute(k_grad_V<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_grad_V<float><<<c->ncells, 256, shm, s>>>(c->nc, c->nq, c->cell_dofs.as<int>(), c->Nq64.as<double>(),
-                                                 c->wq64.as<double>(), (const float *)X, ld, N, dE_dV);
+  density_like(c, prec, X, ld, N, c->wq64.as<double>(), nullptr, dE_dV, dE_dD, s);
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_density(paw_handle c, paw_precision prec, const void *X, int ld, int N, const double *occ,
+                       double *rho_q, double *D_a, void *stream) {
+  PAW_TRY_BEGIN
+  check_prec(prec);
+  PAW_REQUIRE(c && X && rho_q, PAW_ERR_INVALID_ARG, "NULL argument");
+  PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
+  auto s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const double *f = nullptr;
+  if (occ) {
+    for (int i = 0; i < N; ++i) PAW_REQUIRE(std::isfinite(occ[i]), PAW_ERR_NONFINITE, "occupation NaN/Inf");
+    c->ws_colscale.ensure(sizeof(double) * N, &c->dev_bytes);
+    PAW_CUDA(cudaMemcpyAsync(c->ws_colscale.ptr, occ, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    f = c->ws_colscale.as<double>();
   }
-  PAW_LAUNCH_CHECK("k_grad_V");
-  if (c->nown_pairs > 0 && dE_dD) {
-    if (prec == PAW_FP64) {
-      c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
-      nl_project<double>(c, PAW_FP64, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
-      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N,
-                                                 c->proj_ext_dev.as<int>(), dE_dD);
-    } else {
-      c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
-      // projector coefficients of the D_ij gradient stay in FP32 arithmetic
-      nl_project<float>(c, PAW_FP32, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
-      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N,
-                                                c->proj_ext_dev.as<int>(), dE_dD);
-    }
-    PAW_LAUNCH_CHECK("k_grad_D");
-  }
+  density_like(c, prec, X, ld, N, nullptr, f, rho_q, D_a, s);
+  PAW_CUDA(cudaStreamSynchronize(s));   // the occupations are read from host memory by the copy
   return PAW_OK;
   PAW_TRY_END
 }

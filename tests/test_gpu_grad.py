@@ -55,3 +55,24 @@ def test_autograd_function_matches_finite_differences():
     assert abs(fdD - gD) < 1e-5 * abs(gD)
     fe.set_veff(to_dev(op.Vq))
     fe.set_dij(op.D)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["tiny", "p6"])
+def test_density_vs_oracle(prec, name):
+    """paw_density: rho at the Gauss points and D^a with random occupations (p6: 13
+    projectors stored in the library's internal order, returned in the caller's)."""
+    import torch
+    op = oracle_ops(name)
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((op.mesh.ndof, 7))
+    f = rng.uniform(0.0, 2.0, 7)
+    fe = gpu_fe(name)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Xd = to_dev(X, dt)
+    Xr = Xd.double().cpu().numpy()
+    rho, D = fe.density(Xd, f, prec)
+    rr, rD = G.density(op, Xr, f)
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    assert rel_err(rho.cpu().numpy(), rr) < 1e-11   # accumulated in FP64 from the (exact) FP32 inputs
+    assert np.linalg.norm(D.cpu().numpy() - rD) < tol * np.linalg.norm(rD)

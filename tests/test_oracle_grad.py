@@ -24,3 +24,26 @@ def test_grad_V_and_D_by_finite_differences():
     Em = grad.energy(O.PawOperators(s, D=op.D - h * dirD), X)
     fd = (Ep - Em) / (2 * h)
     assert abs(fd - np.sum(dD * dirD)) < 1e-6 * abs(fd)
+
+
+def test_density_pins():
+    """rho and D^a of Eq. FE PAW governing equations (Gamma point, one spin):
+    the integral of rho equals sum_i f_i x_i^T M x_i with the separately assembled
+    consistent mass matrix (both quadratures are exact for products of degree-p
+    functions); with unit occupations rho w_q detJ and D^a are the energy gradient
+    (pinned above by finite differences); D^a is symmetric positive semidefinite."""
+    op = _tiny_ops()
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((op.mesh.ndof, 5))
+    f = rng.uniform(0.0, 2.0, 5)
+    rho, D = grad.density(op, X, f)
+    total = np.sum(op.Wq[None, :] * rho)
+    ref = np.sum(f * np.sum(X * op.apply_M(X), axis=0))
+    assert abs(total - ref) < 1e-12 * abs(ref)
+    rho1, D1 = grad.density(op, X)
+    dV, dD = grad.energy_grad(op, X)
+    assert np.abs(op.Wq[None, :] * rho1 - dV).max() < 1e-13 * np.abs(dV).max()
+    assert np.abs(D1 - dD).max() < 1e-13 * np.abs(dD).max()
+    for a in range(op.natoms):
+        assert np.abs(D[a] - D[a].T).max() < 1e-14 * np.abs(D[a]).max()
+        assert np.linalg.eigvalsh(D[a]).min() > -1e-12 * np.abs(D[a]).max()
