@@ -262,6 +262,45 @@ def run_ours(args, ws, rank, local):
         fe_mx.close()
         del X64, Xmx
 
+    # adjoint of E = tr(X^T H X) at the filtered block (the differentiation workload)
+    gradm = None
+    if args.grad:
+        Xf = out.clone()
+        X32 = Xf.float()
+        fe.energy_grad(X32, "fp32")
+        fe.energy_grad(Xf, "fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gV32, gD32 = fe.energy_grad(X32, "fp32")
+        torch.cuda.synchronize()
+        t32 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        gV, gD = fe.energy_grad(Xf, "fp64")
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        # E is linear in V and Delta_H: <dE/dV, d> = E(V = d) - E(V = 0) exactly (same for D)
+        rng = np.random.default_rng(99)
+        dV = torch.from_numpy(rng.standard_normal((fe.ncells, fe.quad_per_cell))).cuda()
+        dD = rng.standard_normal((fe.natoms, fe.nproj, fe.nproj))
+        dD = dD + dD.transpose(0, 2, 1)
+        fe.set_veff(dV)
+        e1 = fe.energy(Xf)
+        fe.set_veff(torch.zeros_like(dV))
+        e0 = fe.energy(Xf)
+        fdV = e1 - e0
+        fe.set_dij(dD)
+        e1 = fe.energy(Xf)
+        fe.set_dij(np.zeros_like(dD))
+        e0 = fe.energy(Xf)
+        fdD = e1 - e0
+        lin_V = float((gV * dV).sum())
+        lin_D = float((gD.cpu().numpy() * dD).sum())
+        gradm = {"vectors": N, "quad_points": fe.ncells * fe.quad_per_cell, "d_entries": fe.natoms * fe.nproj ** 2,
+                 "fp32_ms": round(t32 * 1e3, 3), "fp64_ms": round(t64 * 1e3, 3),
+                 "fp32_vs_fp64_rel_V": float((gV32 - gV).norm() / gV.norm()),
+                 "fp32_vs_fp64_rel_D": float((gD32 - gD).norm() / gD.norm()),
+                 "fd_rel_V": abs(fdV - lin_V) / abs(fdV), "fd_rel_D": abs(fdD - lin_D) / abs(fdD)}
+
     # roofline of the dominant phase
     peaks = _peaks()
     phases = {k: v for k, v in prof.items() if isinstance(v, dict)}
@@ -294,6 +333,8 @@ def run_ours(args, ws, rank, local):
     }
     if rrm is not None:
         res["rayleigh_ritz"] = rrm
+    if gradm is not None:
+        res["gradient"] = gradm
     fe.close()
     return res
 
@@ -535,6 +576,8 @@ def main():
     ap.add_argument("--y0-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grad", action="store_true",
+                    help="also time the adjoint (gradient of tr(X^T H X)) at the filtered block, with checks")
     ap.add_argument("--rr", action="store_true",
                     help="also time Rayleigh-Ritz on the filtered block, FP64 vs mixed-precision rotation")
     ap.add_argument("--start", default="ritz", choices=["ritz", "random"],
