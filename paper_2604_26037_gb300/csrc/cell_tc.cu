@@ -252,12 +252,14 @@ __global__ void k_tile_mats(const float *__restrict__ He, long long stride, int 
 
 // Persistent warp-specialised form (tc_stream.cuh) for 16-byte-aligned rows:
 // tile = (cell, 128 vectors), one accumulation round per N tile of H^e.
-template <bool BF>
+// SMALL: N tiles of at most 176 rows (degree <= 6), which leaves room for one
+// more pipeline stage.
+template <bool BF, bool SMALL>
 struct CellStream {
   static constexpr int NW = 1, NEPI = 8;
-  static constexpr int S = BF ? 2 : 3;
+  static constexpr int S = (BF ? 2 : 3) + (SMALL ? 1 : 0);
   static constexpr bool BF16 = BF;
-  static constexpr uint32_t B_MAX = 256u * 128u;
+  static constexpr uint32_t B_MAX = (SMALL ? 176u : 256u) * 128u;
   static constexpr int KR = BF ? 64 : 32;
   int ntiles, ncols, vtiles, nc, ntile, ntiles_n, kchunks, ldx, ldy;
   size_t cell_bytes;
@@ -350,10 +352,10 @@ size_t tc_smem_bytes(int ntile, int kchunks, bool bf16) {
   return b < 80 * 1024 ? 80 * 1024 : b;
 }
 
-template <bool BF>
+template <bool BF, bool SMALL>
 static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx, float *Y, int ldy, int ncols,
                         float alpha, cudaStream_t s) {
-  CellStream<BF> p;
+  CellStream<BF, SMALL> p;
   p.vtiles = (ncols + MT - 1) / MT;
   const int64_t nt = (int64_t)c->ncells * p.vtiles;
   PAW_REQUIRE(nt < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many cell tiles");
@@ -371,15 +373,15 @@ static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx
   p.X = X;
   p.Y = Y;
   p.alpha = alpha;
-  const size_t shm = tcs::Geo<CellStream<BF>>::SMEM;
-  PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<CellStream<BF>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)shm));
+  using P = CellStream<BF, SMALL>;
+  const size_t shm = tcs::Geo<P>::SMEM;
+  PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   int dev = 0, nsm = 0;
   PAW_CUDA(cudaGetDevice(&dev));
   PAW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int cap = c->grid_cap > 0 ? std::min(c->grid_cap, nsm) : nsm;
   const int grid = std::max(1, std::min(p.ntiles, cap));
-  tcs::k_tc_stream<CellStream<BF>><<<grid, tcs::threads_for(CellStream<BF>::NEPI), shm, s>>>(p, c->status_dev.as<int>());
+  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>());
   PAW_LAUNCH_CHECK("k_tc_stream<cell>");
 }
 
@@ -392,10 +394,18 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, 
   // rows of X copied with 16-byte cp.async: aligned base, pitch and vector range
   if (c->tc_variant == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 && ldx % 4 == 0 && ncols % 4 == 0 &&
       T.ntile <= 256) {
-    if (bf16)
-      cell_stream<true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
-    else
-      cell_stream<false>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+    const bool small = T.ntile <= 176;
+    if (bf16) {
+      if (small)
+        cell_stream<true, true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+      else
+        cell_stream<true, false>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+    } else {
+      if (small)
+        cell_stream<false, true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+      else
+        cell_stream<false, false>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+    }
     return;
   }
   TcArgs a;

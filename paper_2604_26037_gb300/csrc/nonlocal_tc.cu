@@ -490,9 +490,9 @@ __global__ void k_build_expB(const float *__restrict__ oP, const int *__restrict
 // ------------------------------------------------------------------ streaming forms
 // Persistent warp-specialised forms (tc_stream.cuh) for 16-byte-aligned rows.
 struct ProjStream {
-  static constexpr int NW = 1, S = 3, NEPI = 4;
+  static constexpr int NW = 1, S = 4, NEPI = 4;
   static constexpr bool BF16 = false;
-  static constexpr uint32_t B_MAX = 256u * 128u;
+  static constexpr uint32_t B_MAX = 192u * 128u;
   int ntiles, ncols, n, p, N1, own, npad, kc_own, ppt, vtiles, ldx;
   const int *own_off;
   const uint8_t *B;
@@ -544,17 +544,19 @@ struct ProjStream {
 // Persistent expansion.  The A operands (W rows, small and L2-resident) are
 // gathered by the transposer threads straight from global memory; the node
 // rows the output stage reads (R_Y, R_X, Y hi/lo, or X, or Y) are prefetched
-// 16 rows at a time into a three-deep staging ring with warp-wide 16-byte
+// 16 rows at a time into a four-deep staging ring with warp-wide 16-byte
 // cp.async, together with the rows' M_D^-1 and DoF indices (owner order), so
 // the epilogue warps only read shared memory and store.
 //   warp 0      B loader (one bulk copy per K-chunk)
 //   warp 1      MMA (lane 0), TMEM allocation
 //   warps 2..5  A gather (thread = vector row)
-//   warp 6      output-stage loader (lanes 0..15: one node row each)
-//   warps 7..14 epilogue: lane quarter warp % 4, half (warp - 7) / 4 of each 16-row group
+//   warps 6, 7  output-stage loaders (rows of even / odd index within a group;
+//               the 16 row addresses are formed once per group, then every
+//               copy is issued back to back)
+//   warps 8..15 epilogue: lane quarter warp % 4, half (warp - 8) / 4 of each 16-row group
 namespace xs {
-constexpr int SMAX = 3, NBUF = 3;   // A/B stages (at most), staged row groups
-constexpr int WARP_B = 0, WARP_MMA = 1, WARP_G0 = 2, WARP_SL = 6, WARP_E0 = 7, NEPI = 8;
+constexpr int SMAX = 3, NBUF = 4;   // A/B stages (at most), staged row groups
+constexpr int WARP_B = 0, WARP_MMA = 1, WARP_G0 = 2, WARP_SL = 6, NSL = 2, WARP_E0 = 8, NEPI = 8;
 constexpr int THREADS = 32 * (WARP_E0 + NEPI);
 constexpr uint32_t ROWB = 512;   // one staged node row: 128 vectors
 
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
       mbar_init(smem_u32(&sh->acce[b]), NEPI);
     }
     for (int b = 0; b < NBUF; ++b) {
-      mbar_init(smem_u32(&sh->sfull[b]), 32);   // one cp.async arrival per loader lane
+      mbar_init(smem_u32(&sh->sfull[b]), 32 * NSL);   // one cp.async arrival per loader lane
       mbar_init(smem_u32(&sh->sempty[b]), NEPI);
     }
     mbar_init(smem_u32(&sh->drain), 1);
@@ -772,8 +774,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
         mbar_arrive(smem_u32(&sh->afull[s]));
       }
     }
-  } else if (warp == WARP_SL) {
-    // ---------------------------------------------------------------- output-stage loader
+  } else if (warp < WARP_E0) {
+    // ---------------------------------------------------------------- output-stage loaders
+    const int sl = warp - WARP_SL;   // this warp stages the rows 2 i + sl of every group
     const void *src[4] = {nullptr, nullptr, nullptr, nullptr};
     int ld[4] = {0, 0, 0, 0};
     if (MODE == EXP_RECURRENCE) {
@@ -802,6 +805,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
         const int j = lane;
         const bool live = j < 16 && gi * 16 + j < T.nrows;
         const int d = live ? (int)(T.cb + owned_offset(T.o_beg + gi * 16 + j, a.A.p, a.A.N1)) : -1;
+        int dr[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dr[i] = __shfl_sync(0xffffffffu, d, 2 * i + sl);
         uint8_t *grp = stg + (size_t)gb * G::GROUP;
         const uint32_t dst0 = smem_u32(grp) + lane * 16u;
         const bool lok = (uint32_t)lane * 16u < rbytes;
@@ -809,16 +815,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
         for (int k = 0; k < G::NA; ++k) {
           if (!src[k]) continue;
           const uint8_t *sk = static_cast<const uint8_t *>(src[k]) + (size_t)T.vt * MT * 4 + lane * 16;
-          for (int r = 0; r < 16; ++r) {
-            const int dr = __shfl_sync(0xffffffffu, d, r);
-            if (dr >= 0 && lok) cp_async16(dst0 + (uint32_t)(k * 16 + r) * ROWB, sk + (size_t)dr * ld[k] * 4);
-          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (dr[i] >= 0 && lok)
+              cp_async16(dst0 + (uint32_t)(k * 16 + 2 * i + sl) * ROWB, sk + (size_t)dr[i] * ld[k] * 4);
         }
         // M_D^-1 (lanes 0..3) and DoF indices (lanes 4..7) of the 16 rows, owner order
         const size_t oo = ((size_t)T.e * a.nh + T.h) * a.ntile + gi * 16;
-        if (lane < 4)
+        if (sl == 1 && lane < 4)
           cp_async16(smem_u32(grp + G::MOFF) + lane * 16u, a.mdo + oo + lane * 4);
-        else if (lane < 8)
+        else if (sl == 1 && lane < 8)
           cp_async16(smem_u32(grp + G::DOFF) + (lane - 4) * 16u, a.odof + oo + (lane - 4) * 4);
         cp_async_arrive(smem_u32(&sh->sfull[gb]));
       }
@@ -940,7 +946,7 @@ void nltc_prepare(paw_context *c, cudaStream_t s) {
   if (N.valid) return;
   PAW_REQUIRE(nltc_supported(c), PAW_ERR_UNSUPPORTED, "tensor-core nonlocal kernels: unsupported projector layout");
   N.kc_own = (c->own + 31) / 32;
-  N.ppt = 256 / c->npad;
+  N.ppt = 192 / c->npad;   // N tile <= 192 columns: four 56 KB stages fit the persistent kernel
   N.ppc = 32 / c->npad;
   N.nh = (c->own + 127) / 128;
   N.ntile = (((c->own + N.nh - 1) / N.nh) + 15) / 16 * 16;

@@ -151,7 +151,8 @@ __device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane) {
 #pragma unroll
           for (int jj = 0; jj < KR / 32; ++jj) {
             const uint32_t dst0 = smem_u32(stage_raw<P>(base, s, w)) + (uint32_t)(jj * 32) * ROW_BYTES + lane * 16u;
-            for (int j = 0; j < 32; ++j) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {   // unrolled: the 32 shuffles are independent of the copies
               const float *rp = reinterpret_cast<const float *>(
                   __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(src[w][jj]), j));
               if (rp != nullptr && lok)
