@@ -170,7 +170,10 @@ paw_status paw_get_info(paw_handle h, paw_info *out);
 /* Y = H X (Eq. FE nonlocal contribution: cell-matrix local part by
  * extraction, cell products and assembly, Sec. 4.3, plus sum_a P^a D^a P^a^T).
  * X, Y device, ncols >= 0 (0 is a no-op), ldx, ldy >= ncols; X and Y must
- * not overlap. */
+ * not overlap.  FP64 and FP32 calls are asynchronous on `stream`; PAW_TF32
+ * and PAW_BF16 calls wait for the stream and return TIMEOUT when a
+ * tensor-core kernel gave up on one of its bounded waits (Y is then
+ * incomplete).  The same holds for paw_apply_Sinv_approx. */
 paw_status paw_apply_H(paw_handle h, paw_precision prec, const void *X, void *Y,
                        int ncols, int ldx, int ldy, void *stream);
 

@@ -745,6 +745,14 @@ static void check_block_args(paw_context *c, const void *X, const void *Y, int n
   PAW_REQUIRE(ldx >= ncols && ldy >= ncols, PAW_ERR_INVALID_ARG, "leading dimension smaller than ncols");
 }
 
+// Tensor-core precisions: wait for the stream and report a kernel that gave
+// up on a bounded wait (its output is incomplete).
+static void check_tc_status(paw_context *c, paw_precision prec) {
+  if (prec != PAW_TF32 && prec != PAW_BF16) return;
+  PAW_CUDA(cudaStreamSynchronize(c->last_stream));
+  PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+}
+
 static void check_prec(paw_precision prec) {
   PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16, PAW_ERR_INVALID_ARG,
               "unknown precision");
@@ -762,6 +770,7 @@ paw_status paw_apply_H(paw_handle c, paw_precision prec, const void *X, void *Y,
     op_H<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
   else
     op_H<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  check_tc_status(c, prec);
   return PAW_OK;
   PAW_TRY_END
 }
@@ -794,6 +803,7 @@ paw_status paw_apply_Sinv_approx(paw_handle c, paw_precision prec, const void *X
     op_Sinv<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
   else
     op_Sinv<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  check_tc_status(c, prec);
   return PAW_OK;
   PAW_TRY_END
 }

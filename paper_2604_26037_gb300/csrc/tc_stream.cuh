@@ -9,20 +9,29 @@
 //
 // The rows of A are contiguous 128-vector slices of a row-major block (a node
 // row of a DoF-major multivector, or a projector row of the atom-major
-// coefficients).  Roles:
-//   warp 0        loader: the K rows of a chunk with warp-wide cp.async (lane l
-//                 copies bytes 16 l .. 16 l + 15 of every row) into a raw
-//                 [K][128] FP32 stage, the pre-arranged B chunk with one
+// coefficients), so a chunk arrives vector-contiguous (MN-major); four
+// transposer warps turn it into the K-major operand.  (An MN-major TF32 A
+// descriptor, which would let the MMA read the copied rows directly, gave
+// all-zero products on GB300 in a self-checking test, so the pass stays.)
+// Roles:
+//   warps 0, 6    loaders: the K rows of a chunk with warp-wide cp.async (lane
+//                 l copies bytes 16 l .. 16 l + 15 of a row; warp 0 takes the
+//                 rows of even index, warp 6 the odd ones) into a raw [K][128]
+//                 FP32 stage (rows that do not exist copy a zero row); warp 0
+//                 also issues the pre-arranged B chunk as one
 //                 cp.async.bulk (small bulk copies issued by one warp cap the
-//                 bandwidth far below HBM; 16-byte cp.async from one warp does not)
+//                 bandwidth far below HBM; 16-byte cp.async does not).  The row
+//                 addresses of the next chunk are requested before the current
+//                 chunk is issued, so their lookup latency hides behind the wait
+//                 for a free stage
 //   warp 1        MMA: lane 0 issues tcgen05.mma (4 per 128-byte K-chunk);
 //                 the warp allocates and frees the tensor memory
 //   warps 2..5    transposers: thread = vector row; raw FP32 -> K-major
 //                 128-byte-swizzled A operand (TF32 or BF16)
-//   warps 6..     epilogue: warp w reads TMEM lane quarter w % 4
-// Barriers per stage s: full[s] (copies landed: 32 cp.async arrivals, one
-// arrival with the B byte count), afull[s] (A written by
-// the 128 transposer threads), empty[s] (MMAs done, tcgen05.commit); per
+//   warps 7..     epilogue: warp w reads TMEM lane quarter w % 4
+// Barriers per stage s: full[s] (copies landed: 64 cp.async arrivals, one
+// arrival with the B byte count), afull[s] (A written by the 128
+// transposer threads), empty[s] (MMAs done, tcgen05.commit); per
 // accumulator b: accf[b] (commit) and acce[b] (one arrival per epilogue warp).
 //
 // Every wait is bounded (2 s) and gives up early once another role has given
@@ -43,16 +52,21 @@ constexpr int MT = 128;                       // vectors per tile = MMA M
 constexpr uint32_t ROW_BYTES = MT * 4;        // one raw A row
 constexpr uint32_t A_BYTES = MT * 128;        // one swizzled A chunk
 constexpr uint32_t TMEM_COLS = 512;           // two accumulators of 256 columns
-constexpr int WARP_LOAD = 0, WARP_MMA = 1, WARP_XP0 = 2, NXP = 4, WARP_EPI0 = 6;
+constexpr int WARP_LOAD = 0, WARP_MMA = 1, WARP_XP0 = 2, NXP = 4, WARP_LOAD1 = 6, WARP_EPI0 = 7;
+constexpr int NLD = 2;                        // loader warps
 
 __host__ __device__ constexpr int threads_for(int nepi) { return 32 * (WARP_EPI0 + nepi); }
 
+constexpr int SMAX = 6;                       // stages at most
+
 struct Shared {
-  uint64_t full[4], afull[4], empty[4], accf[2], acce[2], drain;
-  uint64_t mask[4][2];   // live A rows of each stage and operand (bit j: row j copied)
+  uint64_t full[SMAX], afull[SMAX], empty[SMAX], accf[2], acce[2], drain;
   uint32_t taddr;
   int abort;
 };
+
+// source of the rows that do not exist (K padding, vectors past the block)
+static __device__ __align__(16) float zero_row[MT];
 
 template <class P>
 struct Geo {
@@ -63,7 +77,7 @@ struct Geo {
   static constexpr size_t SMEM0 = 1024 + (size_t)P::S * STAGE + sizeof(Shared);
   static constexpr size_t SMEM = SMEM0 < 120 * 1024 ? 120 * 1024 : SMEM0;
   static_assert(P::B_MAX % 1024 == 0, "B stage must keep 1024-byte alignment");
-  static_assert(P::S >= 2 && P::S <= 4 && P::NW >= 1 && P::NW <= 2, "stage / operand counts");
+  static_assert(P::S >= 2 && P::S <= SMAX && P::NW >= 1 && P::NW <= 2, "stage / operand counts");
   static_assert(P::NEPI % 4 == 0, "epilogue warps come in lane-quarter groups");
 };
 
@@ -108,64 +122,100 @@ __device__ __forceinline__ uint8_t *stage_B(uint8_t *base, int s) {
 }
 
 // ------------------------------------------------------------------ roles
+// The chunk sequence of one CTA: tiles t = blockIdx.x, t + gridDim.x, ...,
+// their accumulation rounds, and the K-chunks of each round, in the order
+// every role consumes them.
 template <class P>
-__device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane) {
+struct Walk {
+  typename P::Tile T;
+  int t, ns, sub, nk, kc;
+  __device__ bool start(const P &p) {
+    t = (int)blockIdx.x - (int)gridDim.x;
+    ns = nk = kc = sub = 0;
+    return settle(p);
+  }
+  __device__ bool next(const P &p) {
+    ++kc;
+    return settle(p);
+  }
+  // first chunk at or after the current position; false past the last tile
+  __device__ bool settle(const P &p) {
+    while (kc >= nk) {
+      kc = 0;
+      if (++sub >= ns) {
+        t += gridDim.x;
+        if (t >= p.ntiles) return false;
+        T = p.tile(t);
+        ns = p.nsub(T);
+        sub = 0;
+        if (ns == 0) {
+          nk = 0;
+          continue;
+        }
+      }
+      nk = p.nchunks(T, sub);
+    }
+    return true;
+  }
+};
+
+template <class P>
+__device__ __forceinline__ void chunk_rows(const P &p, const Walk<P> &w, int lane,
+                                           const float *(&src)[P::NW][Geo<P>::KR / 32]) {
+#pragma unroll
+  for (int o = 0; o < P::NW; ++o)
+#pragma unroll
+    for (int jj = 0; jj < Geo<P>::KR / 32; ++jj) src[o][jj] = p.row(w.T, w.sub, w.kc, jj * 32 + lane, o);
+}
+
+// ld: 0 or 1, the loader warp's share (rows 2 i + ld of every 32-row group)
+template <class P>
+__device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane, int ld) {
   constexpr int KR = Geo<P>::KR, S = P::S;
   volatile int *abort = &sh->abort;
   uint32_t g = 0;
   bool run = __shfl_sync(0xffffffffu, *abort, 0) == 0;   // warp-uniform
-  for (int t = blockIdx.x; run && t < p.ntiles; t += gridDim.x) {
-    const auto T = p.tile(t);
-    const int ns = p.nsub(T);
-    const uint32_t rbytes = p.row_bytes(T);
-    for (int sub = 0; run && sub < ns; ++sub) {
-      const int nk = p.nchunks(T, sub);
-      const uint32_t bbytes = (uint32_t)p.ncol(T, sub) * 128u;
-      for (int kc = 0; kc < nk; ++kc, ++g) {
-        const int s = (int)(g % S);
-        const uint32_t u = g / S;
-        if (g >= (uint32_t)S && !warp_wait(smem_u32(&sh->empty[s]), (u - 1) & 1u, abort, lane)) {
-          run = false;
-          break;
+  Walk<P> w;
+  bool have = w.start(p);
+  const float *src[P::NW][KR / 32];
+  if (have) chunk_rows<P>(p, w, lane, src);
+  for (; run && have; ++g) {
+    const int s = (int)(g % S);
+    const uint32_t u = g / S;
+    if (g >= (uint32_t)S && !warp_wait(smem_u32(&sh->empty[s]), (u - 1) & 1u, abort, lane)) {
+      run = false;
+      break;
+    }
+    const uint32_t full = smem_u32(&sh->full[s]);
+    if (ld == 0 && lane == 0) {
+      const uint32_t bbytes = (uint32_t)p.ncol(w.T, w.sub) * 128u;
+      mbar_arrive_tx(full, bbytes);
+      bulk_g2s(smem_u32(stage_B<P>(base, s)), p.bsrc(w.T, w.sub, w.kc), bbytes, full);
+    }
+    const bool lok = (uint32_t)lane * 16u < p.row_bytes(w.T);   // this lane's 16 bytes lie inside the vector range
+    const uint8_t *zsrc = reinterpret_cast<const uint8_t *>(zero_row) + lane * 16;
+#pragma unroll
+    for (int o = 0; o < P::NW; ++o) {
+      const uint32_t st = smem_u32(stage_raw<P>(base, s, o));
+#pragma unroll
+      for (int jj = 0; jj < KR / 32; ++jj) {
+#pragma unroll
+        for (int i = 0; i < 32 / NLD; ++i) {   // unrolled: the shuffles are independent of the copies
+          const int j = NLD * i + ld, k = jj * 32 + j;
+          const float *rp = reinterpret_cast<const float *>(
+              __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(src[o][jj]), j));
+          cp_async16(st + (uint32_t)k * ROW_BYTES + lane * 16u,
+                     (rp != nullptr && lok) ? reinterpret_cast<const uint8_t *>(rp) + lane * 16 : zsrc);
         }
-        const float *src[P::NW][KR / 32];
-#pragma unroll
-        for (int w = 0; w < P::NW; ++w) {
-          uint64_t m = 0;
-#pragma unroll
-          for (int jj = 0; jj < KR / 32; ++jj) {
-            src[w][jj] = p.row(T, sub, kc, jj * 32 + lane, w);
-            const uint32_t b = __ballot_sync(0xffffffffu, src[w][jj] != nullptr);
-            m |= (uint64_t)b << (32 * jj);
-          }
-          if (lane == 0) sh->mask[s][w] = m;
-        }
-        const uint32_t full = smem_u32(&sh->full[s]);
-        if (lane == 0) {
-          mbar_arrive_tx(full, bbytes);   // release: the masks above
-          bulk_g2s(smem_u32(stage_B<P>(base, s)), p.bsrc(T, sub, kc), bbytes, full);
-        }
-        const bool lok = (uint32_t)lane * 16u < rbytes;   // this lane's 16 bytes lie inside the vector range
-#pragma unroll
-        for (int w = 0; w < P::NW; ++w)
-#pragma unroll
-          for (int jj = 0; jj < KR / 32; ++jj) {
-            const uint32_t dst0 = smem_u32(stage_raw<P>(base, s, w)) + (uint32_t)(jj * 32) * ROW_BYTES + lane * 16u;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {   // unrolled: the 32 shuffles are independent of the copies
-              const float *rp = reinterpret_cast<const float *>(
-                  __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(src[w][jj]), j));
-              if (rp != nullptr && lok)
-                cp_async16(dst0 + (uint32_t)j * ROW_BYTES, reinterpret_cast<const uint8_t *>(rp) + lane * 16);
-            }
-          }
-        cp_async_arrive(full);
       }
     }
+    cp_async_arrive(full);
+    have = w.next(p);
+    if (have) chunk_rows<P>(p, w, lane, src);   // consumed after the next stage wait
   }
   // let every copy in flight land before the CTA can exit
   cp_async_wait_all();
-  if (lane == 0) {
+  if (ld == 0 && lane == 0) {
     const uint32_t issued = g;
     for (int s = 0; s < S; ++s) {
       if ((uint32_t)s >= issued) break;
@@ -185,7 +235,6 @@ __device__ void role_transpose(const P &p, uint8_t *base, Shared *sh, int r) {
   for (int t = blockIdx.x; run && t < p.ntiles; t += gridDim.x) {
     const auto T = p.tile(t);
     const int ns = p.nsub(T);
-    const bool vok = p.vt(T) * MT + r < p.ncols;
     for (int sub = 0; run && sub < ns; ++sub) {
       const int nk = p.nchunks(T, sub);
       for (int kc = 0; kc < nk; ++kc, ++g) {
@@ -197,7 +246,6 @@ __device__ void role_transpose(const P &p, uint8_t *base, Shared *sh, int r) {
         }
 #pragma unroll
         for (int w = 0; w < P::NW; ++w) {
-          const uint64_t m = vok ? sh->mask[s][w] : 0ull;
           const float *raw = reinterpret_cast<const float *>(stage_raw<P>(base, s, w));
           uint8_t *A = stage_A<P>(base, s, w);
 #pragma unroll
@@ -208,9 +256,7 @@ __device__ void role_transpose(const P &p, uint8_t *base, Shared *sh, int r) {
 #pragma unroll
               for (int i = 0; i < 4; ++i) {
                 const int j = c * 8 + 2 * i;
-                const float x0 = ((m >> j) & 1ull) ? raw[j * MT + r] : 0.f;
-                const float x1 = ((m >> (j + 1)) & 1ull) ? raw[(j + 1) * MT + r] : 0.f;
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(raw[j * MT + r], raw[(j + 1) * MT + r]);
                 h[i] = *reinterpret_cast<uint32_t *>(&b2);
               }
               q = make_uint4(h[0], h[1], h[2], h[3]);
@@ -219,7 +265,7 @@ __device__ void role_transpose(const P &p, uint8_t *base, Shared *sh, int r) {
 #pragma unroll
               for (int i = 0; i < 4; ++i) {
                 const int j = c * 4 + i;
-                h[i] = to_tf32(((m >> j) & 1ull) ? raw[j * MT + r] : 0.f);
+                h[i] = to_tf32(raw[j * MT + r]);
               }
               q = make_uint4(h[0], h[1], h[2], h[3]);
             }
@@ -265,7 +311,7 @@ __device__ void role_mma(const P &p, uint8_t *base, Shared *sh, uint32_t tmem) {
         for (int w = 0; w < P::NW; ++w) {
           const uint64_t ad = sw128_desc(smem_u32(stage_A<P>(base, s, w)));
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
+          for (int j = 0; j < 4; ++j)   // K-step j: 32 bytes of every K-major row
             mma<P::BF16>(tmem + (uint32_t)(b * 256) + p.dcol(w), ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j),
                          idesc, (kc | j) != 0);
         }
@@ -314,7 +360,7 @@ __global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const P p
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P::S; ++s) {
-      mbar_init(smem_u32(&sh->full[s]), 33);   // 32 cp.async arrivals + the B byte count
+      mbar_init(smem_u32(&sh->full[s]), 32 * NLD + 1);   // cp.async arrivals + the B byte count
       mbar_init(smem_u32(&sh->afull[s]), NXP * 32);
       mbar_init(smem_u32(&sh->empty[s]), 1);
     }
@@ -337,12 +383,12 @@ __global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const P p
   tc_fence_after();
   const uint32_t tmem = sh->taddr;
 
-  if (warp == WARP_LOAD) {
-    role_loader<P>(p, base, sh, lane);
+  if (warp == WARP_LOAD || warp == WARP_LOAD1) {
+    role_loader<P>(p, base, sh, lane, warp == WARP_LOAD ? 0 : 1);
   } else if (warp == WARP_MMA) {
     if (lane == 0) role_mma<P>(p, base, sh, tmem);
     __syncwarp();
-  } else if (warp < WARP_EPI0) {
+  } else if (warp < WARP_XP0 + NXP) {
     role_transpose<P>(p, base, sh, threadIdx.x - 32 * WARP_XP0);
   } else {
     role_epilogue<P>(p, sh, tmem, warp, lane);

@@ -24,9 +24,11 @@ def _x(op, ncols, seed):
     return np.random.default_rng(seed).standard_normal((op.mesh.ndof, ncols))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
-@pytest.mark.parametrize("ncols", [1, 37, 130])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("ncols", [1, 37, 130, 132, 256])
 def test_apply_H(pair, prec, ncols):
+    """ncols 132 and 256 take the tensor-core cell and projector kernels
+    (column count a multiple of 4); 132 leaves a 4-vector tail tile."""
     import torch
     name, op, fe = pair
     X = _x(op, ncols, 1)
