@@ -689,6 +689,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
                     &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
                     &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
+                    &c->own_lg, &c->own_sidx, &c->own_cnt,
                     &c->nltc.eoff};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);

@@ -156,6 +156,13 @@ struct paw_context {
   pawfe::DevBuf own_atom;                     // int32 nown_pairs
   pawfe::DevBuf ownP64, ownP32;               // nown_pairs * own * npad
   pawfe::DevBuf own_ngrp;                     // int32 per pair: projector groups of 4 with a nonzero value
+  // per pair and owned node o: index of the last projector group of 4 with a
+  // nonzero value at o (-1: none); the owned nodes sorted by that index
+  // (descending) and, per group g, the number of nodes whose index is >= g.
+  // The FP64 kernels multiply only groups that can be nonzero on a node.
+  pawfe::DevBuf own_lg;                       // int8  nown_pairs * own
+  pawfe::DevBuf own_sidx;                     // int16 nown_pairs * own
+  pawfe::DevBuf own_cnt;                      // int32 nown_pairs * npad/4
   int64_t proj_nnz = 0;                       // nonzero (owned node, projector) entries over all pairs
   pawfe::DevBuf apair_off, apair;             // atom-major list of the pairs (int32)
   // atom-pair Gram blocks G_ab = P^a^T M_D^-1 P^b for atoms with common support

@@ -32,19 +32,11 @@ template <>
 struct ProjCfg<float> {
   static constexpr int VT = 64;
 };
-template <>
-struct ProjCfg<double> {
-  static constexpr int VT = 32;
-};
 template <typename T>
 struct ExpCfg;
 template <>
 struct ExpCfg<float> {
   static constexpr int VT = 32;
-};
-template <>
-struct ExpCfg<double> {
-  static constexpr int VT = 16;
 };
 
 constexpr int OWN_MAX = 512;   // p <= 8
@@ -80,6 +72,7 @@ __device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
 }
 
 // ------------------------------------------------------------------ projection
+// FP32 SIMT form (the FP64 form is k_own_project64 below).
 // Thread tile 4 projectors x 4 vectors; the owned nodes are split over OG
 // thread groups whose partial sums are reduced through shared memory.
 template <typename T, int NPAD>
@@ -165,24 +158,31 @@ __global__ void __launch_bounds__(256) k_own_project(int n, int p, int N1, const
 }
 
 // U[a][al][v] = sum over the pairs k of atom a (fixed order) of partial[k][al][v]
-// One warp per (atom, projector, 32 vectors); four interleaved partial sums keep
-// several loads in flight, combined in a fixed order.
+// One warp per (atom, projector, 32 vectors); eight interleaved partial sums keep
+// eight loads in flight, combined in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(32) k_pair_reduce(const int *__restrict__ aoff, const int *__restrict__ apair,
                                                     const T *__restrict__ partial, int npad, int ncols,
                                                     T *__restrict__ U) {
+  constexpr int R = 8;
   const int v = blockIdx.x * 32 + threadIdx.x;
   const int al = blockIdx.y, a = blockIdx.z;
   if (v >= ncols) return;
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  T acc[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) acc[u] = T(0);
   const int s0 = aoff[a], s1 = aoff[a + 1];
   int s = s0;
-  for (; s + 3 < s1; s += 4) {
+  for (; s + R - 1 < s1; s += R) {
+    T x[R];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] += partial[((size_t)apair[s + u] * npad + al) * ncols + v];
+    for (int u = 0; u < R; ++u) x[u] = partial[((size_t)apair[s + u] * npad + al) * ncols + v];
+#pragma unroll
+    for (int u = 0; u < R; ++u) acc[u] += x[u];
   }
   for (; s < s1; ++s) acc[0] += partial[((size_t)apair[s] * npad + al) * ncols + v];
-  U[((size_t)a * npad + al) * ncols + v] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  U[((size_t)a * npad + al) * ncols + v] =
+      ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 // ------------------------------------------------------------------ coupling
@@ -219,44 +219,44 @@ __global__ void k_own_couple(int npj, const T *__restrict__ U, const double *__r
 }
 
 // W_H[a] = scale * D_H[a] (U[a] - sum_b G_ab W_S[b])  (= scale D_H P^a^T Shat^-1 R)
-// accumulated in the arithmetic of T (FP32 for the FP32 / TF32 / BF16 filter)
+// accumulated in the arithmetic of T (FP32 for the FP32 / TF32 / BF16 filter).
+// Block = (atom a, 32 vectors), warp be = projector be: t[be][v] over the atoms
+// b that share support nodes with a (G rows read as warp broadcasts), then
+// W_H = D_H t through shared memory.
 template <typename T, int NPAD>
-__global__ void k_own_couple_h(int npj, const int *__restrict__ goff, const int *__restrict__ gatom,
-                               const T *__restrict__ G, const T *__restrict__ U, const T *__restrict__ WS,
-                               const double *__restrict__ DH, double scale, T *__restrict__ WH, int ncols) {
-  const int a = blockIdx.x;
-  const int v = blockIdx.y * blockDim.x + threadIdx.x;
-  if (v >= ncols) return;
-  T u[NPAD];
-#pragma unroll
-  for (int be = 0; be < NPAD; ++be) u[be] = (be < npj) ? U[((size_t)a * NPAD + be) * ncols + v] : T(0);
-  for (int s = goff[a]; s < goff[a + 1]; ++s) {
-    const int b = gatom[s];
-    const T *Gs = G + (size_t)s * NPAD * NPAD;
-    T w[NPAD];
-#pragma unroll
-    for (int ga = 0; ga < NPAD; ++ga) w[ga] = (ga < npj) ? WS[((size_t)b * NPAD + ga) * ncols + v] : T(0);
-#pragma unroll
-    for (int be = 0; be < NPAD; ++be) {
-      T t = T(0);
-#pragma unroll
-      for (int ga = 0; ga < NPAD; ++ga) t = fma(Gs[be * NPAD + ga], w[ga], t);
-      u[be] -= t;
+__global__ void __launch_bounds__(NPAD * 32) k_own_couple_h(int npj, const int *__restrict__ goff,
+                                                            const int *__restrict__ gatom, const T *__restrict__ G,
+                                                            const T *__restrict__ U, const T *__restrict__ WS,
+                                                            const double *__restrict__ DH, double scale,
+                                                            T *__restrict__ WH, int ncols) {
+  __shared__ T ts[NPAD][32];
+  const int a = blockIdx.x, lane = threadIdx.x & 31, be = threadIdx.x >> 5;
+  const int v = blockIdx.y * 32 + lane;
+  const int vc = v < ncols ? v : ncols - 1;   // in-range column for the loads of idle lanes
+  T t = T(0);
+  if (be < npj) {
+    t = U[((size_t)a * NPAD + be) * ncols + vc];
+    for (int s = goff[a]; s < goff[a + 1]; ++s) {
+      const T *Gr = G + ((size_t)s * NPAD + be) * NPAD;
+      const T *w = WS + (size_t)gatom[s] * NPAD * ncols + vc;
+      T acc = T(0);
+      for (int ga = 0; ga < npj; ++ga) acc = fma(Gr[ga], w[(size_t)ga * ncols], acc);
+      t -= acc;
     }
   }
-  const double *Da = DH + (size_t)a * npj * npj;
-  for (int al = 0; al < NPAD; ++al) {
-    T w = T(0);
-    if (al < npj) {
-#pragma unroll
-      for (int be = 0; be < NPAD; ++be)
-        if (be < npj) w = fma(T(Da[al * npj + be]), u[be], w);
-    }
-    WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * (double)w);
+  ts[be][lane] = t;
+  __syncthreads();
+  const int al = be;
+  T w = T(0);
+  if (al < npj) {
+    const double *Da = DH + ((size_t)a * npj + al) * npj;
+    for (int b2 = 0; b2 < npj; ++b2) w = fma(T(Da[b2]), ts[b2][lane], w);
   }
+  if (v < ncols) WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * (double)w);
 }
 
 // ------------------------------------------------------------------ expansion
+// FP32 SIMT form (the FP64 form is k_own_expand64 below).
 // Expansion with a fused output stage.  W of every pair of the cell is staged
 // in shared memory (at most 48 pairs); a thread owns 4 vectors of one node row
 // at a time.
@@ -356,16 +356,11 @@ __global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__res
         t[j] = m * (ry[j] - s1[j]);
         const T bracket = -T(A.beta) * ry[j] - T(A.gamma) * rx[j] + s2[j];
         const int vj = min(v + j, ncols - 1);
-        if constexpr (sizeof(T) == 4) {
-          const float *yh = static_cast<const float *>(A.Y0);
-          const float *yl = static_cast<const float *>(A.Y0lo);
-          const float yhv = yh[d * A.ldy0 + vj];
-          const float ylv = yl ? yl[d * A.ldy0 + vj] : 0.f;
-          out[j] = add_product_df(bracket, A.chi[vj], A.clo[vj], yhv, ylv);
-        } else {
-          const double *y0 = static_cast<const double *>(A.Y0);
-          out[j] = fma(A.c64[vj], y0[d * A.ldy0 + vj], bracket);
-        }
+        const float *yh = static_cast<const float *>(A.Y0);
+        const float *yl = static_cast<const float *>(A.Y0lo);
+        const float yhv = yh[d * A.ldy0 + vj];
+        const float ylv = yl ? yl[d * A.ldy0 + vj] : 0.f;
+        out[j] = add_product_df(bracket, A.chi[vj], A.clo[vj], yhv, ylv);
       }
       if (vec) {
         st4(tp, t);
@@ -430,6 +425,167 @@ __global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__res
   }
 }
 
+// ------------------------------------------------------------------ FP64 forms
+// GB300 retires about one warp-wide FP64 FMA per 16 SM clocks, so the FP64
+// kernels spend FP64 instructions only where a projector can be nonzero: lane
+// = vector (32 per CTA), and every FP64 instruction of a warp belongs to one
+// owned node and one group of 4 projectors (warp-uniform control flow), taken
+// only up to the last group with a nonzero value on that node (own_lg).
+
+// Projection: warp w takes positions w, w + 8, ... of each pair's node list
+// sorted by descending last nonzero group, so the eight warps share every pair
+// evenly; their partial sums are added in a fixed order through shared memory.
+template <int NPAD>
+__global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, const int *__restrict__ own_off,
+                                                       const int *__restrict__ own_cnt,
+                                                       const int16_t *__restrict__ own_sidx,
+                                                       const double *__restrict__ oP, const double *__restrict__ X,
+                                                       int ldx, int ncols, const double *__restrict__ rowscale,
+                                                       double *__restrict__ U) {
+  constexpr int NG = NPAD / 4, NWARP = 8;
+  __shared__ int ooff[OWN_MAX];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int e = blockIdx.y, v0 = blockIdx.x * 32;   // vector tiles of one cell are adjacent: P reused from L2
+  const int k0 = own_off[e], k1 = own_off[e + 1];
+  if (k0 == k1) return;
+  const int own = p * p * p;
+  double *Xs = reinterpret_cast<double *>(sm_raw);   // [own][32]
+  double *red = Xs + (size_t)own * 32;               // [NWARP][NPAD][32]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t base = owned_table(e, n, p, N1, ooff, own);
+  __syncthreads();
+  const int v = v0 + lane;
+  for (int o = warp; o < own; o += NWARP) {
+    const int64_t d = base + ooff[o];
+    double x = (v < ncols) ? X[d * ldx + v] : 0.0;
+    if (rowscale) x *= rowscale[d];
+    Xs[o * 32 + lane] = x;
+  }
+  __syncthreads();
+  for (int k = k0; k < k1; ++k) {
+    int cg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) cg[g] = own_cnt[(size_t)k * NG + g];
+    const int16_t *sidx = own_sidx + (size_t)k * own;
+    const double *Pk = oP + (size_t)k * own * NPAD;
+    double acc[NPAD];
+#pragma unroll
+    for (int al = 0; al < NPAD; ++al) acc[al] = 0.0;
+    int o = (warp < cg[0]) ? sidx[warp] : 0;
+    for (int i = warp; i < cg[0]; i += NWARP) {
+      const int onext = (i + NWARP < cg[0]) ? sidx[i + NWARP] : 0;   // index of the next node in flight
+      const double x = Xs[o * 32 + lane];
+      const double2 *Pr = reinterpret_cast<const double2 *>(Pk + (size_t)o * NPAD);
+      // a real branch (not predication): FP64 instructions of groups that are
+      // zero on the node would still occupy the FP64 pipe
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (i >= cg[g]) break;   // this and the later groups are zero on the node
+        const double2 a = __ldg(Pr + 2 * g), b = __ldg(Pr + 2 * g + 1);
+        acc[4 * g + 0] = fma(a.x, x, acc[4 * g + 0]);
+        acc[4 * g + 1] = fma(a.y, x, acc[4 * g + 1]);
+        acc[4 * g + 2] = fma(b.x, x, acc[4 * g + 2]);
+        acc[4 * g + 3] = fma(b.y, x, acc[4 * g + 3]);
+      }
+      o = onext;
+    }
+    // only the warps that met a node and the groups that are nonzero somewhere
+    // on the pair take part in the reduction; the other rows are zero
+    const int nwk = min(NWARP, cg[0]);
+    int nact = 0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) nact += (cg[g] > 0) ? 4 : 0;
+    if (warp < nwk) {
+#pragma unroll
+      for (int al = 0; al < NPAD; ++al)
+        if (al < nact) red[((size_t)warp * NPAD + al) * 32 + lane] = acc[al];
+    }
+    __syncthreads();
+    // per-pair partial sums: plain coalesced stores, reduced per atom by k_pair_reduce
+    for (int idx = tid; idx < NPAD * 32; idx += 256) {
+      const int al = idx >> 5, l = idx & 31;
+      if (v0 + l < ncols) {
+        double sum = 0.0;
+        if (al < nact) {
+          sum = red[idx];
+          for (int w = 1; w < nwk; ++w) sum += red[(size_t)w * NPAD * 32 + idx];
+        }
+        U[((size_t)k * NPAD + al) * ncols + v0 + l] = sum;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Expansion: warp w takes the owned nodes w, w + 8, ...; for each pair of the
+// cell the groups up to the node's last nonzero one are multiplied (four
+// accumulators, one per projector of a group, added in a fixed order), then the
+// output stage of k_own_expand (MODE) is applied to the node row.
+template <int NPAD, int MODE>
+__global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const double *__restrict__ oP,
+                                                      const int8_t *__restrict__ own_lg,
+                                                      const double *__restrict__ W1, const double *__restrict__ W2) {
+  constexpr int NG = NPAD / 4, NWARP = 8;
+  constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
+  __shared__ int ooff[OWN_MAX];
+  __shared__ int patom[64];
+  const int e = blockIdx.y, v0 = blockIdx.x * 32;
+  const int k0 = A.own_off[e], k1 = A.own_off[e + 1];
+  if (MODE == EXP_ADD && k0 == k1) return;
+  const int own = A.p * A.p * A.p;
+  const int np = k1 - k0;
+  const int ncols = A.ncols;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t base = owned_table(e, A.n, A.p, A.N1, ooff, own);
+  for (int i = tid; i < np; i += 256) patom[i] = A.own_atom[k0 + i];
+  __syncthreads();
+  const int v = v0 + lane;
+  const bool vok = v < ncols;
+  const int vc = vok ? v : ncols - 1;   // in-range column for the loads of idle lanes
+  const int8_t *lgc = own_lg + (size_t)k0 * own;
+  for (int o = warp; o < own; o += NWARP) {
+    double s1[4] = {0.0, 0.0, 0.0, 0.0}, s2[4] = {0.0, 0.0, 0.0, 0.0};   // four independent FMA chains per sum
+    for (int kk = 0; kk < np; ++kk) {
+      const int lg = lgc[(size_t)kk * own + o];   // warp-uniform
+      if (lg < 0) continue;
+      const double2 *Pr = reinterpret_cast<const double2 *>(oP + ((size_t)(k0 + kk) * own + o) * NPAD);
+      const double *w1 = W1 + (size_t)patom[kk] * NPAD * ncols + vc;
+      const double *w2 = (NW == 2) ? W2 + (size_t)patom[kk] * NPAD * ncols + vc : nullptr;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (g > lg) break;
+        const double2 a = __ldg(Pr + 2 * g), b = __ldg(Pr + 2 * g + 1);
+        const double pv[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s1[j] = fma(pv[j], __ldg(w1 + (size_t)(4 * g + j) * ncols), s1[j]);
+        if constexpr (NW == 2) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) s2[j] = fma(pv[j], __ldg(w2 + (size_t)(4 * g + j) * ncols), s2[j]);
+        }
+      }
+    }
+    const double S1 = (s1[0] + s1[1]) + (s1[2] + s1[3]);
+    const double S2 = (NW == 2) ? (s2[0] + s2[1]) + (s2[2] + s2[3]) : 0.0;
+    if (!vok) continue;
+    const int64_t d = base + ooff[o];
+    const double *Xin = static_cast<const double *>(A.Xin);
+    double *Y = static_cast<double *>(A.Y);
+    if (MODE == EXP_ADD) {
+      Y[d * A.ldy + v] += (A.cs ? A.cs[v] : 1.0) * S1;
+    } else if (MODE == EXP_SINV) {
+      const double m = static_cast<const double *>(A.mdinv)[d];
+      Y[d * A.ldy + v] = m * (Xin[d * A.ldx + v] - S1);
+    } else {
+      const double m = static_cast<const double *>(A.mdinv)[d];
+      double *RX = static_cast<double *>(A.RX);
+      const double ry = Xin[d * A.ldx + v], rx = RX[d * A.ldx + v];
+      Y[d * A.ldy + v] = m * (ry - S1);
+      const double bracket = -A.beta * ry - A.gamma * rx + S2;
+      RX[d * A.ldx + v] = fma(A.c64[v], static_cast<const double *>(A.Y0)[d * A.ldy0 + v], bracket);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host side
 // true when p (may be NULL) and the row pitch allow 16-byte vector access
 static bool aligned16(const void *p, size_t pitch_bytes) {
@@ -439,24 +595,34 @@ static bool aligned16(const void *p, size_t pitch_bytes) {
 template <typename T>
 static const T *ownP(paw_context *c);
 template <>
-const double *ownP<double>(paw_context *c) { return c->ownP64.as<double>(); }
-template <>
 const float *ownP<float>(paw_context *c) { return c->ownP32.as<float>(); }
 
 template <typename T, int NPAD>
 static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T *rowscale, T *U, cudaStream_t s) {
-  constexpr int VT = ProjCfg<T>::VT;
-  constexpr int TPG = (NPAD / 4) * (VT / 4);
-  constexpr int OG = 256 / TPG;
-  const size_t shm = sizeof(T) * ((size_t)c->own * VT + (size_t)OG * NPAD * VT);
-  PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
-              "projection tile exceeds shared memory (degree too high)");
-  PAW_CUDA(cudaFuncSetAttribute(k_own_project<T, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  dim3 g1((ncols + VT - 1) / VT, c->ncells);
-  const int xa = aligned16(X, ldx * sizeof(T)) ? 1 : 0;
-  k_own_project<T, NPAD><<<g1, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_ngrp.as<int>(),
-                                              ownP<T>(c), X, ldx, ncols, rowscale, c->npj, U, xa);
-  PAW_LAUNCH_CHECK("k_own_project");
+  if constexpr (sizeof(T) == 8) {
+    const size_t shm = sizeof(double) * ((size_t)c->own * 32 + (size_t)8 * NPAD * 32);
+    PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+                "projection tile exceeds shared memory (degree too high)");
+    PAW_CUDA(cudaFuncSetAttribute(k_own_project64<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    dim3 g((ncols + 31) / 32, c->ncells);
+    k_own_project64<NPAD><<<g, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_cnt.as<int>(),
+                                             c->own_sidx.as<int16_t>(), c->ownP64.as<double>(), X, ldx, ncols,
+                                             rowscale, U);
+    PAW_LAUNCH_CHECK("k_own_project64");
+  } else {
+    constexpr int VT = ProjCfg<T>::VT;
+    constexpr int TPG = (NPAD / 4) * (VT / 4);
+    constexpr int OG = 256 / TPG;
+    const size_t shm = sizeof(T) * ((size_t)c->own * VT + (size_t)OG * NPAD * VT);
+    PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+                "projection tile exceeds shared memory (degree too high)");
+    PAW_CUDA(cudaFuncSetAttribute(k_own_project<T, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    dim3 g1((ncols + VT - 1) / VT, c->ncells);
+    const int xa = aligned16(X, ldx * sizeof(T)) ? 1 : 0;
+    k_own_project<T, NPAD><<<g1, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_ngrp.as<int>(),
+                                                ownP<T>(c), X, ldx, ncols, rowscale, c->npj, U, xa);
+    PAW_LAUNCH_CHECK("k_own_project");
+  }
 }
 
 // U = P^T (rowscale .* X) into c->ws_partial (natoms x npad x ncols): per-pair
@@ -533,14 +699,14 @@ void nl_project_filter(paw_context *c, paw_precision prec, const T *RY, int ldr,
   if (c->nown_pairs == 0 || ncols <= 0) return;
   const T *U = project_U<T>(c, prec, RY, ldr, ncols, mdinv, s);
   couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, WS, ncols, s);
-  dim3 g2(c->natoms, (ncols + 63) / 64);
+  dim3 g2(c->natoms, (ncols + 31) / 32);
   const T *G = gram<T>(c);
   if (c->npad == 16)
-    k_own_couple_h<T, 16><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), G, U, WS,
-                                             c->DH64.as<double>(), alpha, WH, ncols);
+    k_own_couple_h<T, 16><<<g2, 16 * 32, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), G, U, WS,
+                                                  c->DH64.as<double>(), alpha, WH, ncols);
   else
-    k_own_couple_h<T, 32><<<g2, 64, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), G, U, WS,
-                                             c->DH64.as<double>(), alpha, WH, ncols);
+    k_own_couple_h<T, 32><<<g2, 32 * 32, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), G, U, WS,
+                                                  c->DH64.as<double>(), alpha, WH, ncols);
   PAW_LAUNCH_CHECK("k_own_couple_h");
 }
 
@@ -552,26 +718,36 @@ static void own_expand(paw_context *c, paw_precision prec, ExpArgs A, const T *W
       return;
     }
   }
-  constexpr int VT = ExpCfg<T>::VT;
-  const size_t y0e = (sizeof(T) == 4) ? sizeof(float) : sizeof(double);
-  A.vec_ok = aligned16(A.Y, A.ldy * sizeof(T)) && aligned16(A.Xin, A.ldx * sizeof(T)) &&
-             aligned16(A.RX, A.ldx * sizeof(T)) && aligned16(A.Y0, A.ldy0 * y0e) &&
-             aligned16(A.Y0lo, A.ldy0 * sizeof(float));
-  constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
-  const size_t shm = sizeof(T) * (size_t)NW * std::max(1, c->max_own_pairs) * c->npad * VT;
-  PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
-              "too many atoms on one cell for the expansion kernel");
-  dim3 g((A.ncols + VT - 1) / VT, c->ncells);
-  if (c->npad == 16) {
-    auto kern = k_own_expand<T, 16, MODE>;
-    PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
+  if constexpr (sizeof(T) == 8) {
+    PAW_REQUIRE(c->max_own_pairs <= 64 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+                "too many atoms on one cell for the expansion kernel");
+    dim3 g((A.ncols + 31) / 32, c->ncells);
+    if (c->npad == 16)
+      k_own_expand64<16, MODE><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
+    else
+      k_own_expand64<32, MODE><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
+    PAW_LAUNCH_CHECK("k_own_expand64");
   } else {
-    auto kern = k_own_expand<T, 32, MODE>;
-    PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
+    constexpr int VT = ExpCfg<T>::VT;
+    A.vec_ok = aligned16(A.Y, A.ldy * sizeof(T)) && aligned16(A.Xin, A.ldx * sizeof(T)) &&
+               aligned16(A.RX, A.ldx * sizeof(T)) && aligned16(A.Y0, A.ldy0 * sizeof(float)) &&
+               aligned16(A.Y0lo, A.ldy0 * sizeof(float));
+    constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
+    const size_t shm = sizeof(T) * (size_t)NW * std::max(1, c->max_own_pairs) * c->npad * VT;
+    PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+                "too many atoms on one cell for the expansion kernel");
+    dim3 g((A.ncols + VT - 1) / VT, c->ncells);
+    if (c->npad == 16) {
+      auto kern = k_own_expand<T, 16, MODE>;
+      PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
+    } else {
+      auto kern = k_own_expand<T, 32, MODE>;
+      PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
+    }
+    PAW_LAUNCH_CHECK("k_own_expand");
   }
-  PAW_LAUNCH_CHECK("k_own_expand");
 }
 
 static ExpArgs exp_args(paw_context *c, int ncols) {

@@ -565,6 +565,36 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
     }
     c->own_ngrp.ensure(sizeof(int) * ngrp.size(), &c->dev_bytes);
     PAW_CUDA(cudaMemcpy(c->own_ngrp.ptr, ngrp.data(), sizeof(int) * ngrp.size(), cudaMemcpyHostToDevice));
+    // last nonzero group per (pair, owned node), nodes sorted by it, prefix counts per group
+    {
+      const int ng4 = c->npad / 4, own = c->own;
+      std::vector<int8_t> lg(std::max<size_t>(1, keys.size() * own), -1);
+      std::vector<int16_t> sidx(std::max<size_t>(1, keys.size() * own), 0);
+      std::vector<int> cnt(std::max<size_t>(1, keys.size() * ng4), 0);
+      for (size_t k = 0; k < keys.size(); ++k) {
+        int8_t *L = lg.data() + k * own;
+        for (int o = 0; o < own; ++o) {
+          const double *row = oP.data() + k * blk + (size_t)o * c->npad;
+          int last = -1;
+          for (int al = c->npad - 1; al >= 0; --al)
+            if (row[al] != 0.0) {
+              last = al;
+              break;
+            }
+          L[o] = (int8_t)(last >= 0 ? last / 4 : -1);
+          for (int g = 0; g <= L[o]; ++g) cnt[k * ng4 + g]++;
+        }
+        int16_t *S = sidx.data() + k * own;
+        for (int o = 0; o < own; ++o) S[o] = (int16_t)o;
+        std::stable_sort(S, S + own, [L](int16_t x, int16_t y) { return L[x] > L[y]; });
+      }
+      c->own_lg.ensure(lg.size(), &c->dev_bytes);
+      c->own_sidx.ensure(sizeof(int16_t) * sidx.size(), &c->dev_bytes);
+      c->own_cnt.ensure(sizeof(int) * cnt.size(), &c->dev_bytes);
+      PAW_CUDA(cudaMemcpy(c->own_lg.ptr, lg.data(), lg.size(), cudaMemcpyHostToDevice));
+      PAW_CUDA(cudaMemcpy(c->own_sidx.ptr, sidx.data(), sizeof(int16_t) * sidx.size(), cudaMemcpyHostToDevice));
+      PAW_CUDA(cudaMemcpy(c->own_cnt.ptr, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice));
+    }
     c->own_off.ensure(sizeof(int) * off.size(), &c->dev_bytes);
     c->own_atom.ensure(sizeof(int) * std::max<size_t>(1, oatom.size()), &c->dev_bytes);
     c->ownP64.ensure(sizeof(double) * std::max<size_t>(1, oP.size()), &c->dev_bytes);

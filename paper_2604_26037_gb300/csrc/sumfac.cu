@@ -15,7 +15,7 @@
 // GB300 has little FP64 throughput, so the FP64 paths (Y = H X - S X Lambda,
 // the FP64 filter form, Rayleigh-Ritz products, residuals) use this form.
 //
-// Block: one cell, VT vectors, 256 threads; each 1D contraction handles one
+// Block: one cell, VT vectors, SF_THREADS threads; each 1D contraction handles one
 // line (all points along the contracted direction) per thread, in the even/odd
 // split of the centro-symmetric 1D matrices (about 25.7k FP64 operations per
 // cell and vector at p = 6 instead of 35.7k).  Shared-memory tensors are
@@ -30,6 +30,10 @@ namespace {
 
 template <int NP>
 constexpr int sf_vt() { return NP >= 9 ? 4 : 8; }
+// 512 threads at <= 128 registers: one block of 16 warps per SM (shared memory
+// allows one), so that every line of a contraction stage runs in one pass and
+// the FP64 pipe sees twice the warps of a 256-thread block
+constexpr int SF_THREADS = 512;
 
 // Even/odd halves of a centro-symmetric 1D matrix A (m x n, A[m-1-i][n-1-j] = A[i][j]):
 //   Ae[i][j] = (A[i][j] + A[i][n-1-j]) / 2   (j < n/2),  Ae[i][n/2] = A[i][n/2] for odd n,
@@ -101,7 +105,7 @@ struct Half {
 };
 
 template <int NP>
-__global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, const int *__restrict__ cell_dofs,
+__global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int ncells, const int *__restrict__ cell_dofs,
                                                   const double *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
                                                   const double *__restrict__ X, int ldx, double *__restrict__ Y,
                                                   int ldy, int ncols, double alpha, double cK, double cV,
@@ -125,21 +129,21 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
   {
     const double *src = reinterpret_cast<const double *>(&tab);
     double *dst = reinterpret_cast<double *>(&st);
-    for (int i = tid; i < (int)(sizeof(SfTables) / sizeof(double)); i += 256) dst[i] = src[i];
+    for (int i = tid; i < (int)(sizeof(SfTables) / sizeof(double)); i += SF_THREADS) dst[i] = src[i];
   }
-  for (int i = tid; i < N3; i += 256) dofs[i] = cell_dofs[(size_t)e * N3 + i];
+  for (int i = tid; i < N3; i += SF_THREADS) dofs[i] = cell_dofs[(size_t)e * N3 + i];
   const bool doV = cV != 0.0;
   if (doV)
-    for (int i = tid; i < NQ * NQ * NQ; i += 256) sw[i] = cV * wV[(size_t)e * NQ * NQ * NQ + i];
+    for (int i = tid; i < NQ * NQ * NQ; i += SF_THREADS) sw[i] = cV * wV[(size_t)e * NQ * NQ * NQ + i];
   __syncthreads();
-  for (int idx = tid; idx < N3 * VT; idx += 256) {
+  for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
     const int r = idx / VT, v = idx - r * VT;
     A0[idx] = (v0 + v < ncols) ? X[(size_t)dofs[r] * ldx + v0 + v] : 0.0;
   }
   __syncthreads();
   const double kf = cK * st.kfac, mf = st.mfac;
   // c-contractions, one (a, b) line per thread: P = M_c x, Q = D_c x
-  for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int ab = idx / VT, v = idx - ab * VT;
     const Split<NP> x = split_line<NP>(A0 + ab * VT + v, NP * NP * VT);
     Half<NP> P, Q;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
   }
   __syncthreads();
   // b-contractions, one (a, c) line per thread: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S
-  for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int ac = idx / VT, v = idx - ac * VT;
     const int a = ac % NP, c = ac / NP;
     const int base = (c * NP * NP + a) * VT + v;
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
   }
   __syncthreads();
   // a-contractions, one (b, c) line per thread: y = kf D_a S + M_a R
-  for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int bc = idx / VT, v = idx - bc * VT;
     const int base = bc * NP * VT + v;
     const Split<NP> sl = split_line<NP>(A3 + base, VT);
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
   if (doV) {
     __syncthreads();
     // U1[c][b][i] = sum_a phi[i][a] x[c][b][a]            (line (b, c), NP -> NQ)
-    for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+    for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
       const int bc = idx / VT, v = idx - bc * VT;
       const Split<NP> x = split_line<NP>(A0 + bc * NP * VT + v, VT);
       Half<NQ> U;
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     }
     __syncthreads();
     // U2[c][j][i] = sum_b phi[j][b] U1[c][b][i]           (line (i, c))
-    for (int idx = tid; idx < NQ * NP * VT; idx += 256) {
+    for (int idx = tid; idx < NQ * NP * VT; idx += SF_THREADS) {
       const int ic = idx / VT, v = idx - ic * VT;
       const int i = ic % NQ, c = ic / NQ;
       const Split<NP> x = split_line<NP>(A2 + (c * NP * NQ + i) * VT + v, NQ * VT);
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     }
     __syncthreads();
     // U3[k][j][i] = w_q V_q sum_c phi[k][c] U2[c][j][i]    (line (i, j))
-    for (int idx = tid; idx < NQ * NQ * VT; idx += 256) {
+    for (int idx = tid; idx < NQ * NQ * VT; idx += SF_THREADS) {
       const int ji = idx / VT, v = idx - ji * VT;
       const Split<NP> x = split_line<NP>(A3 + ji * VT + v, NQ * NQ * VT);
       Half<NQ> U;
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     }
     __syncthreads();
     // B2[c][j][i] = sum_k phi[k][c] U3[k][j][i]            (line (i, j), NQ -> NP)
-    for (int idx = tid; idx < NQ * NQ * VT; idx += 256) {
+    for (int idx = tid; idx < NQ * NQ * VT; idx += SF_THREADS) {
       const int ji = idx / VT, v = idx - ji * VT;
       const Split<NQ> x = split_line<NQ>(A4 + ji * VT + v, NQ * NQ * VT);
       Half<NP> B;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     }
     __syncthreads();
     // B1[c][b][i] = sum_j phi[j][b] B2[c][j][i]            (line (i, c))
-    for (int idx = tid; idx < NQ * NP * VT; idx += 256) {
+    for (int idx = tid; idx < NQ * NP * VT; idx += SF_THREADS) {
       const int ic = idx / VT, v = idx - ic * VT;
       const int i = ic % NQ, c = ic / NQ;
       const Split<NQ> x = split_line<NQ>(A3 + (c * NQ * NQ + i) * VT + v, NQ * VT);
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     }
     __syncthreads();
     // y[c][b][a] += sum_i phi[i][a] B1[c][b][i]            (line (b, c))
-    for (int idx = tid; idx < NP * NP * VT; idx += 256) {
+    for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
       const int bc = idx / VT, v = idx - bc * VT;
       const Split<NQ> x = split_line<NQ>(A2 + bc * NQ * VT + v, VT);
       Half<NP> B;
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(256) k_local_sf(SfTables tab, int ncells, cons
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < N3 * VT; idx += 256) {
+  for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
     const int r = idx / VT, v = idx - r * VT;
     if (v0 + v < ncols) atomicAdd(&Y[(size_t)dofs[r] * ldy + v0 + v], alpha * A1[idx]);
   }
@@ -283,7 +287,7 @@ void launch_sf(paw_context *c, const SfTables &t, const double *wV, const double
   const size_t shm = sf_smem<NP>();
   PAW_CUDA(cudaFuncSetAttribute(k_local_sf<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 g(c->ncells, (ncols + sf_vt<NP>() - 1) / sf_vt<NP>());
-  k_local_sf<NP><<<g, 256, shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy, ncols, alpha, cK, cV,
+  k_local_sf<NP><<<g, SF_THREADS, shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy, ncols, alpha, cK, cV,
                                      cM, cMcol);
   PAW_LAUNCH_CHECK("k_local_sf");
 }
