@@ -5,6 +5,8 @@
 #include <cstring>
 #include <numeric>
 
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace pawfe {
@@ -55,6 +57,27 @@ int read_status(paw_context *c) {
     return -1;
   if (v != 0 && cudaMemsetAsync(c->status_dev.ptr, 0, sizeof(int), c->last_stream) != cudaSuccess) return -1;
   return v;
+}
+
+void encode_row_map(CUtensorMap *map, const float *base, int64_t rows, int cols, int ld) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                                                                 : nullptr;
+  }();
+  PAW_REQUIRE(encode != nullptr, PAW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  PAW_REQUIRE(reinterpret_cast<uintptr_t>(base) % 16 == 0 && ld % 4 == 0 && cols >= 1 && cols <= ld && rows >= 1,
+              PAW_ERR_INVALID_ARG, "row map: base must be 16-byte aligned, ld a multiple of 4");
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {128, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  PAW_REQUIRE(r == CUDA_SUCCESS, PAW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
 void DevBuf::ensure(size_t nbytes, int64_t *counter) {

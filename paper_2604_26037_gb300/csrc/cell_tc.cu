@@ -261,6 +261,7 @@ struct CellStream {
   static constexpr bool BF16 = BF;
   static constexpr uint32_t B_MAX = (SMALL ? 176u : 256u) * 128u;
   static constexpr int KR = BF ? 64 : 32;
+  CUtensorMap tm[NW];   // rows of X (gathered with TMA)
   int ntiles, ncols, vtiles, nc, ntile, ntiles_n, kchunks, ldx, ldy;
   size_t cell_bytes;
   const uint8_t *Ht;
@@ -281,10 +282,10 @@ struct CellStream {
   __device__ int nsub(const Tile &) const { return ntiles_n; }
   __device__ int nchunks(const Tile &, int) const { return kchunks; }
   __device__ int ncol(const Tile &, int) const { return ntile; }
-  __device__ uint32_t row_bytes(const Tile &T) const { return (uint32_t)min(MT, ncols - T.vt * MT) * 4u; }
-  __device__ const float *row(const Tile &T, int, int kc, int j, int) const {
+  __device__ int xcol(const Tile &T) const { return T.vt * MT; }
+  __device__ int row_id(const Tile &T, int, int kc, int j, int) const {
     const int k = kc * KR + j;
-    return k < nc ? X + (size_t)cell_dofs[(size_t)T.e * nc + k] * ldx + T.vt * MT : nullptr;
+    return k < nc ? cell_dofs[(size_t)T.e * nc + k] : -1;
   }
   __device__ const uint8_t *bsrc(const Tile &T, int sub, int kc) const {
     return Ht + (size_t)T.e * cell_bytes + ((size_t)sub * kchunks + kc) * ntile * 128;
@@ -373,6 +374,7 @@ static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx
   p.X = X;
   p.Y = Y;
   p.alpha = alpha;
+  encode_row_map(&p.tm[0], X, c->ndof, ncols, ldx);
   using P = CellStream<BF, SMALL>;
   const size_t shm = tcs::Geo<P>::SMEM;
   PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));

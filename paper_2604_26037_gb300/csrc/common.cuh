@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libpawfe.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cublas_v2.h>
 #include <cusolverDn.h>
@@ -49,6 +50,13 @@ extern int64_t g_launch_count;
   do {                                                                        \
     if (!(cond)) throw ::pawfe::Error{(code), (msg)};                         \
   } while (0)
+
+// ---------------------------------------------------------------- TMA
+// Tensor map of a row-major FP32 block (rows x cols, row pitch ld elements,
+// 16-byte aligned base, ld a multiple of 4) read by the row-gather copies of
+// the persistent tcgen05 kernels: box = 128 columns x 1 row (tile::gather4
+// fetches four such rows per instruction); columns past cols read as zero.
+void encode_row_map(CUtensorMap *map, const float *base, int64_t rows, int cols, int ld);
 
 // ---------------------------------------------------------------- memory
 // Device buffer owned by a context.  Grows, never shrinks.

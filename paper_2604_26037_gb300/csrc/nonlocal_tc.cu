@@ -493,6 +493,7 @@ struct ProjStream {
   static constexpr int NW = 1, S = 4, NEPI = 4;
   static constexpr bool BF16 = false;
   static constexpr uint32_t B_MAX = 192u * 128u;
+  CUtensorMap tm[NW];   // rows of X (gathered with TMA)
   int ntiles, ncols, n, p, N1, own, npad, kc_own, ppt, vtiles, ldx;
   const int *own_off;
   const uint8_t *B;
@@ -515,10 +516,10 @@ struct ProjStream {
   __device__ int nsub(const Tile &T) const { return (T.np + ppt - 1) / ppt; }
   __device__ int nchunks(const Tile &, int) const { return kc_own; }
   __device__ int ncol(const Tile &T, int sub) const { return min(ppt, T.np - sub * ppt) * npad; }
-  __device__ uint32_t row_bytes(const Tile &T) const { return (uint32_t)min(MT, ncols - T.vt * MT) * 4u; }
-  __device__ const float *row(const Tile &T, int, int kc, int j, int) const {
+  __device__ int xcol(const Tile &T) const { return T.vt * MT; }
+  __device__ int row_id(const Tile &T, int, int kc, int j, int) const {
     const int o = kc * 32 + j;
-    return o < own ? X + (T.cb + owned_offset(o, p, N1)) * ldx + T.vt * MT : nullptr;
+    return o < own ? (int)(T.cb + owned_offset(o, p, N1)) : -1;
   }
   __device__ const uint8_t *bsrc(const Tile &T, int sub, int kc) const {
     return B + (size_t)(T.k0 + sub * ppt) * npad * 128 * kc_own + (size_t)kc * ncol(T, sub) * 128;
@@ -544,15 +545,16 @@ struct ProjStream {
 // Persistent expansion.  The A operands (W rows, small and L2-resident) are
 // gathered by the transposer threads straight from global memory; the node
 // rows the output stage reads (R_Y, R_X, Y hi/lo, or X, or Y) are prefetched
-// 16 rows at a time into a four-deep staging ring with warp-wide 16-byte
-// cp.async, together with the rows' M_D^-1 and DoF indices (owner order), so
-// the epilogue warps only read shared memory and store.
+// 16 rows at a time into a four-deep staging ring with TMA row gathers
+// (tile::gather4 from one tensor map per array), together with the rows'
+// M_D^-1 and DoF indices (owner order, bulk copies), so the epilogue warps
+// only read shared memory and store.
 //   warp 0      B loader (one bulk copy per K-chunk)
 //   warp 1      MMA (lane 0), TMEM allocation
 //   warps 2..5  A gather (thread = vector row)
-//   warps 6, 7  output-stage loaders (rows of even / odd index within a group;
-//               the 16 row addresses are formed once per group, then every
-//               copy is issued back to back)
+//   warp 6      output-stage loader: lane 4 k + q gathers rows 4 q .. 4 q + 3
+//               of array k; lanes 16, 17 copy M_D^-1 and the DoF indices
+//   warp 7      idle
 //   warps 8..15 epilogue: lane quarter warp % 4, half (warp - 8) / 4 of each 16-row group
 namespace xs {
 constexpr int SMAX = 3, NBUF = 4;   // A/B stages (at most), staged row groups
@@ -586,6 +588,8 @@ constexpr size_t smem_bytes() {
 }
 
 struct Args {
+  CUtensorMap tm[4];   // staged arrays (R_Y, R_X, Y hi, Y lo; or X; or Y), rows gathered with TMA
+  int amask;           // bit k: array k is staged
   ExpArgs A;
   int ntiles, npad, ppc, ntile, nh, vtiles, own;
   const uint8_t *B;
@@ -622,7 +626,7 @@ __device__ __forceinline__ bool skip_tile(const Tile &T) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *status) {
+__global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const __grid_constant__ Args a, int *status) {
   using G = Geo<MODE>;
   constexpr int S = G::S;
   extern __shared__ uint8_t smem_raw[];
@@ -642,7 +646,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
       mbar_init(smem_u32(&sh->acce[b]), NEPI);
     }
     for (int b = 0; b < NBUF; ++b) {
-      mbar_init(smem_u32(&sh->sfull[b]), 32 * NSL);   // one cp.async arrival per loader lane
+      mbar_init(smem_u32(&sh->sfull[b]), 1);   // one arrival carrying the byte count
       mbar_init(smem_u32(&sh->sempty[b]), NEPI);
     }
     mbar_init(smem_u32(&sh->drain), 1);
@@ -774,27 +778,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
         mbar_arrive(smem_u32(&sh->afull[s]));
       }
     }
-  } else if (warp < WARP_E0) {
-    // ---------------------------------------------------------------- output-stage loaders
-    const int sl = warp - WARP_SL;   // this warp stages the rows 2 i + sl of every group
-    const void *src[4] = {nullptr, nullptr, nullptr, nullptr};
-    int ld[4] = {0, 0, 0, 0};
-    if (MODE == EXP_RECURRENCE) {
-      src[0] = a.A.Xin;  ld[0] = a.A.ldx;    // R_Y
-      src[1] = a.A.RX;   ld[1] = a.A.ldx;    // R_X
-      src[2] = a.A.Y0;   ld[2] = a.A.ldy0;   // Y hi
-      src[3] = a.A.Y0lo; ld[3] = a.A.ldy0;   // Y lo (may be NULL)
-    } else if (MODE == EXP_SINV) {
-      src[0] = a.A.Xin;  ld[0] = a.A.ldx;
-    } else {
-      src[0] = a.A.Y;    ld[0] = a.A.ldy;
-    }
+  } else if (warp == WARP_SL) {
+    // ---------------------------------------------------------------- output-stage loader
+    int na = 0;
+#pragma unroll
+    for (int k = 0; k < G::NA; ++k) na += (a.amask >> k) & 1;
+    const uint32_t gbytes = (uint32_t)na * 16u * ROWB + 128u;   // row gathers + M_D^-1 + DoF indices
+    const int k = lane >> 2, q = lane & 3;
+    const bool mine = k < G::NA && ((a.amask >> k) & 1);
     uint32_t gc = 0;
     bool run = __shfl_sync(0xffffffffu, *abort, 0) == 0;
     for (int t = blockIdx.x; run && t < a.ntiles; t += gridDim.x) {
       const Tile T = tile_of(a, t);
       if (skip_tile<MODE>(T)) continue;
-      const uint32_t rbytes = (uint32_t)min(MT, ncols - T.vt * MT) * 4u;
+      const int x = T.vt * MT;
       for (int gi = 0; gi < T.ngroups; ++gi, ++gc) {
         const int gb = (int)(gc % NBUF);
         const uint32_t ug = gc / NBUF;
@@ -802,40 +799,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const Args a, int *st
           run = false;
           break;
         }
-        const int j = lane;
-        const bool live = j < 16 && gi * 16 + j < T.nrows;
-        const int d = live ? (int)(T.cb + owned_offset(T.o_beg + gi * 16 + j, a.A.p, a.A.N1)) : -1;
-        int dr[8];
+        // row j of the group (lanes 0..15); rows past the tile repeat its first row (never read back)
+        const int nrow = min(16, T.nrows - gi * 16);
+        const int jr = (lane & 15) < nrow ? (lane & 15) : 0;
+        const int d = (int)(T.cb + owned_offset(T.o_beg + gi * 16 + jr, a.A.p, a.A.N1));
+        int r4[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) dr[i] = __shfl_sync(0xffffffffu, d, 2 * i + sl);
+        for (int i = 0; i < 4; ++i) r4[i] = __shfl_sync(0xffffffffu, d, 4 * q + i);
         uint8_t *grp = stg + (size_t)gb * G::GROUP;
-        const uint32_t dst0 = smem_u32(grp) + lane * 16u;
-        const bool lok = (uint32_t)lane * 16u < rbytes;
-#pragma unroll
-        for (int k = 0; k < G::NA; ++k) {
-          if (!src[k]) continue;
-          const uint8_t *sk = static_cast<const uint8_t *>(src[k]) + (size_t)T.vt * MT * 4 + lane * 16;
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (dr[i] >= 0 && lok)
-              cp_async16(dst0 + (uint32_t)(k * 16 + 2 * i + sl) * ROWB, sk + (size_t)dr[i] * ld[k] * 4);
-        }
-        // M_D^-1 (lanes 0..3) and DoF indices (lanes 4..7) of the 16 rows, owner order
+        const uint32_t full = smem_u32(&sh->sfull[gb]);
+        if (lane == 0) mbar_arrive_tx(full, gbytes);
+        __syncwarp();
+        if (mine)
+          tma_gather4(smem_u32(grp) + (uint32_t)(k * 16 + 4 * q) * ROWB, &a.tm[k], x, r4[0], r4[1], r4[2], r4[3],
+                      full);
         const size_t oo = ((size_t)T.e * a.nh + T.h) * a.ntile + gi * 16;
-        if (sl == 1 && lane < 4)
-          cp_async16(smem_u32(grp + G::MOFF) + lane * 16u, a.mdo + oo + lane * 4);
-        else if (sl == 1 && lane < 8)
-          cp_async16(smem_u32(grp + G::DOFF) + (lane - 4) * 16u, a.odof + oo + (lane - 4) * 4);
-        cp_async_arrive(smem_u32(&sh->sfull[gb]));
+        if (lane == 16) bulk_g2s(smem_u32(grp + G::MOFF), a.mdo + oo, 64u, full);
+        if (lane == 17) bulk_g2s(smem_u32(grp + G::DOFF), a.odof + oo, 64u, full);
       }
     }
-    cp_async_wait_all();
     if (lane == 0)
       for (int gb = 0; gb < NBUF && (uint32_t)gb < gc; ++gb) {   // let the copies in flight land
         const uint32_t last = ((gc - 1 - (uint32_t)gb) / NBUF) * NBUF + (uint32_t)gb;
         mbar_wait(smem_u32(&sh->sfull[gb]), (last / NBUF) & 1u);
       }
     __syncwarp();
+  } else if (warp < WARP_E0) {
+    // idle
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3, part = (warp - WARP_E0) >> 2;
@@ -1059,6 +1049,7 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
     p.B = scaled ? N.projBs.as<uint8_t>() : N.projB.as<uint8_t>();
     p.X = X;
     p.PP = PP;
+    encode_row_map(&p.tm[0], X, c->ndof, ncols, ldx);
     launch_stream(c, p, s, "k_tc_stream<projection>");
     return;
   }
@@ -1107,6 +1098,25 @@ static void expand_stream(paw_context *c, const ExpArgs &A, const float *W1, con
   p.W2 = W2;
   p.mdo = N.mdo.as<float>();
   p.odof = N.odof.as<int>();
+  // staged arrays: R_Y, R_X, Y hi, Y lo (recurrence); X (Shat^-1); Y (add)
+  const void *arr[4] = {nullptr, nullptr, nullptr, nullptr};
+  int ld[4] = {0, 0, 0, 0};
+  if (MODE == EXP_RECURRENCE) {
+    arr[0] = A.Xin, ld[0] = A.ldx;
+    arr[1] = A.RX, ld[1] = A.ldx;
+    arr[2] = A.Y0, ld[2] = A.ldy0;
+    arr[3] = A.Y0lo, ld[3] = A.ldy0;
+  } else if (MODE == EXP_SINV) {
+    arr[0] = A.Xin, ld[0] = A.ldx;
+  } else {
+    arr[0] = A.Y, ld[0] = A.ldy;
+  }
+  p.amask = 0;
+  for (int k = 0; k < 4; ++k)
+    if (arr[k]) {
+      encode_row_map(&p.tm[k], static_cast<const float *>(arr[k]), c->ndof, A.ncols, ld[k]);
+      p.amask |= 1 << k;
+    }
   const size_t shm = xs::smem_bytes<MODE>();
   PAW_CUDA(cudaFuncSetAttribute(xs::k_exp_stream<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const int grid = std::max(1, std::min(p.ntiles, persistent_grid(c)));

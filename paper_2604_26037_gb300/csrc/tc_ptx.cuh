@@ -62,6 +62,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       : "memory");
 }
 
+// Four rows (row0..row3) of a 2D tensor, columns x .. x + box - 1, into four
+// consecutive box-sized rows of shared memory at dst (TMA tile::gather4; the
+// map's box is one row high); completes on mbarrier bar.  x * element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void *map, int x, int row0, int row1, int row2,
+                                            int row3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(row0), "r"(row1), "r"(row2), "r"(row3), "r"(bar)
+      : "memory");
+}
+
 // 16 bytes global -> shared through L1 (cp.async, cache at L2 only)
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");

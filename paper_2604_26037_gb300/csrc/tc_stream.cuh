@@ -14,23 +14,24 @@
 // descriptor, which would let the MMA read the copied rows directly, gave
 // all-zero products on GB300 in a self-checking test, so the pass stays.)
 // Roles:
-//   warps 0, 6    loaders: the K rows of a chunk with warp-wide cp.async (lane
-//                 l copies bytes 16 l .. 16 l + 15 of a row; warp 0 takes the
-//                 rows of even index, warp 6 the odd ones) into a raw [K][128]
-//                 FP32 stage (rows that do not exist copy a zero row); warp 0
-//                 also issues the pre-arranged B chunk as one
-//                 cp.async.bulk (small bulk copies issued by one warp cap the
-//                 bandwidth far below HBM; 16-byte cp.async does not).  The row
-//                 addresses of the next chunk are requested before the current
-//                 chunk is issued, so their lookup latency hides behind the wait
-//                 for a free stage
+//   warp 0        loader: the K rows of a chunk with TMA row gathers
+//                 (tile::gather4, four 512-byte rows per instruction, issued by
+//                 lanes 0 .. K/4 - 1 from the operand's tensor map) into a raw
+//                 [K][128] FP32 stage, and the pre-arranged B chunk as one
+//                 cp.async.bulk; rows that do not exist repeat the chunk's
+//                 first row (the B operand is zero there).  The TMA unit keeps
+//                 far more bytes in flight per SM than warp-wide 16-byte
+//                 cp.async, whose issue stalled the loaders.  The row indices
+//                 of the next chunk are looked up before the wait for a free
+//                 stage
+//   warp 6        idle
 //   warp 1        MMA: lane 0 issues tcgen05.mma (4 per 128-byte K-chunk);
 //                 the warp allocates and frees the tensor memory
 //   warps 2..5    transposers: thread = vector row; raw FP32 -> K-major
 //                 128-byte-swizzled A operand (TF32 or BF16)
 //   warps 7..     epilogue: warp w reads TMEM lane quarter w % 4
-// Barriers per stage s: full[s] (copies landed: 64 cp.async arrivals, one
-// arrival with the B byte count), afull[s] (A written by the 128
+// Barriers per stage s: full[s] (copies landed: one arrival with the byte
+// count of the row gathers and the B chunk), afull[s] (A written by the 128
 // transposer threads), empty[s] (MMAs done, tcgen05.commit); per
 // accumulator b: accf[b] (commit) and acce[b] (one arrival per epilogue warp).
 //
@@ -52,8 +53,7 @@ constexpr int MT = 128;                       // vectors per tile = MMA M
 constexpr uint32_t ROW_BYTES = MT * 4;        // one raw A row
 constexpr uint32_t A_BYTES = MT * 128;        // one swizzled A chunk
 constexpr uint32_t TMEM_COLS = 512;           // two accumulators of 256 columns
-constexpr int WARP_LOAD = 0, WARP_MMA = 1, WARP_XP0 = 2, NXP = 4, WARP_LOAD1 = 6, WARP_EPI0 = 7;
-constexpr int NLD = 2;                        // loader warps
+constexpr int WARP_LOAD = 0, WARP_MMA = 1, WARP_XP0 = 2, NXP = 4, WARP_IDLE = 6, WARP_EPI0 = 7;
 
 __host__ __device__ constexpr int threads_for(int nepi) { return 32 * (WARP_EPI0 + nepi); }
 
@@ -64,9 +64,6 @@ struct Shared {
   uint32_t taddr;
   int abort;
 };
-
-// source of the rows that do not exist (K padding, vectors past the block)
-static __device__ __align__(16) float zero_row[MT];
 
 template <class P>
 struct Geo {
@@ -159,26 +156,25 @@ struct Walk {
   }
 };
 
+// row indices of the current chunk: lane l holds rows l, 32 + l, ... (-1: no row)
 template <class P>
-__device__ __forceinline__ void chunk_rows(const P &p, const Walk<P> &w, int lane,
-                                           const float *(&src)[P::NW][Geo<P>::KR / 32]) {
+__device__ __forceinline__ void chunk_ids(const P &p, const Walk<P> &w, int lane, int (&rid)[P::NW][Geo<P>::KR / 32]) {
 #pragma unroll
   for (int o = 0; o < P::NW; ++o)
 #pragma unroll
-    for (int jj = 0; jj < Geo<P>::KR / 32; ++jj) src[o][jj] = p.row(w.T, w.sub, w.kc, jj * 32 + lane, o);
+    for (int jj = 0; jj < Geo<P>::KR / 32; ++jj) rid[o][jj] = p.row_id(w.T, w.sub, w.kc, jj * 32 + lane, o);
 }
 
-// ld: 0 or 1, the loader warp's share (rows 2 i + ld of every 32-row group)
 template <class P>
-__device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane, int ld) {
-  constexpr int KR = Geo<P>::KR, S = P::S;
+__device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane) {
+  constexpr int KR = Geo<P>::KR, S = P::S, RPL = KR / 32;
   volatile int *abort = &sh->abort;
   uint32_t g = 0;
   bool run = __shfl_sync(0xffffffffu, *abort, 0) == 0;   // warp-uniform
   Walk<P> w;
   bool have = w.start(p);
-  const float *src[P::NW][KR / 32];
-  if (have) chunk_rows<P>(p, w, lane, src);
+  int rid[P::NW][RPL];
+  if (have) chunk_ids<P>(p, w, lane, rid);
   for (; run && have; ++g) {
     const int s = (int)(g % S);
     const uint32_t u = g / S;
@@ -187,35 +183,37 @@ __device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane, int
       break;
     }
     const uint32_t full = smem_u32(&sh->full[s]);
-    if (ld == 0 && lane == 0) {
-      const uint32_t bbytes = (uint32_t)p.ncol(w.T, w.sub) * 128u;
-      mbar_arrive_tx(full, bbytes);
-      bulk_g2s(smem_u32(stage_B<P>(base, s)), p.bsrc(w.T, w.sub, w.kc), bbytes, full);
-    }
-    const bool lok = (uint32_t)lane * 16u < p.row_bytes(w.T);   // this lane's 16 bytes lie inside the vector range
-    const uint8_t *zsrc = reinterpret_cast<const uint8_t *>(zero_row) + lane * 16;
+    const uint32_t bbytes = (uint32_t)p.ncol(w.T, w.sub) * 128u;
+    if (lane == 0) mbar_arrive_tx(full, bbytes + (uint32_t)(P::NW * KR) * ROW_BYTES);
+    __syncwarp();
+    if (lane == 0) bulk_g2s(smem_u32(stage_B<P>(base, s)), p.bsrc(w.T, w.sub, w.kc), bbytes, full);
+    const int x = p.xcol(w.T);
 #pragma unroll
     for (int o = 0; o < P::NW; ++o) {
-      const uint32_t st = smem_u32(stage_raw<P>(base, s, o));
+      // rows that do not exist repeat the chunk's first row (always present)
+      const int first = __shfl_sync(0xffffffffu, rid[o][0], 0);
+      // lane l < KR / 4 gathers rows 4 l .. 4 l + 3, held by lanes (4 l + i) % 32, slot (4 l + i) / 32
+      int r4[4];
 #pragma unroll
-      for (int jj = 0; jj < KR / 32; ++jj) {
+      for (int i = 0; i < 4; ++i) {
+        const int row = 4 * lane + i;
+        int val = 0;
 #pragma unroll
-        for (int i = 0; i < 32 / NLD; ++i) {   // unrolled: the shuffles are independent of the copies
-          const int j = NLD * i + ld, k = jj * 32 + j;
-          const float *rp = reinterpret_cast<const float *>(
-              __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(src[o][jj]), j));
-          cp_async16(st + (uint32_t)k * ROW_BYTES + lane * 16u,
-                     (rp != nullptr && lok) ? reinterpret_cast<const uint8_t *>(rp) + lane * 16 : zsrc);
+        for (int jj = 0; jj < RPL; ++jj) {
+          const int t = __shfl_sync(0xffffffffu, rid[o][jj], row & 31);
+          if ((row >> 5) == jj) val = t;
         }
+        r4[i] = val >= 0 ? val : first;
       }
+      if (lane < KR / 4)
+        tma_gather4(smem_u32(stage_raw<P>(base, s, o)) + (uint32_t)lane * 4u * ROW_BYTES, &p.tm[o], x, r4[0], r4[1],
+                    r4[2], r4[3], full);
     }
-    cp_async_arrive(full);
     have = w.next(p);
-    if (have) chunk_rows<P>(p, w, lane, src);   // consumed after the next stage wait
+    if (have) chunk_ids<P>(p, w, lane, rid);   // consumed after the next stage wait
   }
   // let every copy in flight land before the CTA can exit
-  cp_async_wait_all();
-  if (ld == 0 && lane == 0) {
+  if (lane == 0) {
     const uint32_t issued = g;
     for (int s = 0; s < S; ++s) {
       if ((uint32_t)s >= issued) break;
@@ -353,14 +351,14 @@ __device__ void role_epilogue(const P &p, Shared *sh, uint32_t tmem, int warp, i
 }
 
 template <class P>
-__global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const P p, int *status) {
+__global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const __grid_constant__ P p, int *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = align1024(smem_raw);
   Shared *sh = reinterpret_cast<Shared *>(base + (size_t)P::S * Geo<P>::STAGE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P::S; ++s) {
-      mbar_init(smem_u32(&sh->full[s]), 32 * NLD + 1);   // cp.async arrivals + the B byte count
+      mbar_init(smem_u32(&sh->full[s]), 1);   // one arrival carrying the byte count
       mbar_init(smem_u32(&sh->afull[s]), NXP * 32);
       mbar_init(smem_u32(&sh->empty[s]), 1);
     }
@@ -383,8 +381,9 @@ __global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const P p
   tc_fence_after();
   const uint32_t tmem = sh->taddr;
 
-  if (warp == WARP_LOAD || warp == WARP_LOAD1) {
-    role_loader<P>(p, base, sh, lane, warp == WARP_LOAD ? 0 : 1);
+  if (warp == WARP_LOAD) {
+    role_loader<P>(p, base, sh, lane);
+  } else if (warp == WARP_IDLE) {
   } else if (warp == WARP_MMA) {
     if (lane == 0) role_mma<P>(p, base, sh, tmem);
     __syncwarp();
