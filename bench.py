@@ -305,8 +305,8 @@ def run_ours(args, ws, rank, local):
     peaks = _peaks()
     phases = {k: v for k, v in prof.items() if isinstance(v, dict)}
     dom = max(phases, key=lambda k: phases[k]["ms"])
-    roof = roofline(dom, phases[dom], fe, sysd, cfg, args.prec, peaks, clocks)
-    all_roof = {k: roofline(k, v, fe, sysd, cfg, args.prec, peaks, clocks) for k, v in phases.items()}
+    roof = roofline(dom, phases[dom], fe, sysd, cfg, args.prec, peaks, clocks, args.workload)
+    all_roof = {k: roofline(k, v, fe, sysd, cfg, args.prec, peaks, clocks, args.workload) for k, v in phases.items()}
     launches = prof["total_launches"] // args.steps
 
     res = {
@@ -324,7 +324,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
         "roofline": roof,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in phases.items()},
-        "phase_roofline": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "ms_per_launch")
+        "phase_roofline": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "ms_per_launch", "traffic")
                                if kk in v} for k, v in all_roof.items()},
         "fp64_form": fp64,
         "speedup_vs_fp64": (round(value / fp64["value"], 3) if fp64 else None),
@@ -346,12 +346,36 @@ def fe_np1(nc):
 # kernels that make up each profiled phase of the filter (library phase brackets)
 PHASE_KERNELS = {
     "residual_local": "k_local_sf (FP64 even/odd sum-factorised 1/2 K + V - lambda M)",
-    "residual_nonlocal": "k_own_project + k_pair_reduce + k_own_couple + k_own_expand (FP64)",
-    "recurrence": "k_own_expand (fused Shat^-1 expansion + nonlocal H + recurrence update)",
-    "projection": "k_own_project + k_pair_reduce + k_own_couple + k_own_couple_h",
-    "cell_products": "k_cell_tc (tcgen05) or k_cell_simt",
+    "residual_nonlocal": "k_own_project64 + k_pair_reduce + k_own_couple + k_own_expand64 (FP64)",
+    "recurrence": "k_exp_stream (tcgen05: fused Shat^-1 expansion + nonlocal H + recurrence update)",
+    "projection": "k_tc_stream<ProjStream> + k_pair_reduce + k_own_couple + k_own_couple_h",
+    "cell_products": "k_tc_stream<CellStream> (tcgen05 TF32/BF16) or k_cell_simt",
     "recovery": "Shat^-1 of R_m + FP64 combination",
 }
+
+# DRAM bytes per DoF.vector moved by the main kernel of a phase, read off one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, single pass) of a full 256-vector launch on the
+# 884,736-DoF workload with the kernels of this version; a launch of another size is scaled by its
+# DoF.vectors.  Keyed by (phase, precision); None = the same kernel in every precision.
+MEASURED_TRAFFIC = {
+    ("residual_local", None): (39.38, "k_local_sf"),
+    ("residual_nonlocal", None): (13.09 + 17.37, "k_own_project64 + k_own_expand64"),
+    ("cell_products", "tf32"): (23.17, "k_tc_stream<CellStream>"),
+    ("projection", "tf32"): (7.24, "k_tc_stream<ProjStream>"),
+    ("recurrence", "tf32"): (25.60, "k_exp_stream<2>"),
+}
+TRAFFIC_WORKLOAD = "mid"
+
+
+def measured_traffic(phase, prec, units, workload):
+    """(bytes per launch, note) from MEASURED_TRAFFIC, or (None, None)."""
+    hit = MEASURED_TRAFFIC.get((phase, None)) or MEASURED_TRAFFIC.get((phase, prec))
+    if not hit:
+        return None, None
+    note = f"ncu capture of {hit[1]} on the {TRAFFIC_WORKLOAD} workload"
+    if workload != TRAFFIC_WORKLOAD:
+        note += ", scaled by DoF.vectors"
+    return round(hit[0] * units), note
 
 
 def sf_flops_per_cell_vec(n1):
@@ -424,7 +448,7 @@ def compute_peak(kind, peaks, sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "alu"          # FP32 FFMA: 152 SMs x 128 lanes x 2
 
 
-def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
+def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks, workload=None):
     """Roofline of one phase of the filter, per launch, from algorithmic bytes/flops."""
     per_launch_ms = pinfo["ms"] / max(pinfo["intervals"], 1)
     flops, byts, kind = phase_model(phase, fe, cfg, prec)
@@ -433,12 +457,13 @@ def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks):
                 "traffic": None, "kernel": phase}
     sec = per_launch_ms / 1e3
     gbs = byts / sec / 1e9
+    traffic, tnote = measured_traffic(phase, prec, float(fe.ndof) * cfg["block"], workload)
     tfs = flops / sec / 1e12
     hbm_frac = gbs / peaks["hbm"]
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     cpk, cbound = compute_peak(kind, peaks, sm_mhz)
     c_frac = tfs / cpk
-    common = {"traffic": None, "kernel": phase, "kernels": PHASE_KERNELS.get(phase),
+    common = {"traffic": traffic, "traffic_source": tnote, "kernel": phase, "kernels": PHASE_KERNELS.get(phase),
               "ms_per_launch": round(per_launch_ms, 4), "algorithmic_bytes_per_launch": byts,
               "algorithmic_flops_per_launch": flops, "peak_source": peaks["src"]}
     if c_frac >= hbm_frac:
