@@ -20,6 +20,9 @@ rr      Algorithm 1 steps 4-6 (Rayleigh-Ritz), residual norms (Sec. 4),
         generalised Lanczos bounds, dense brute-force eigensolve.
 grad    derivative of tr(X^T H X) with respect to V at quadrature points and
         to the PAW coupling matrices Delta_H.
+kpoint  the same operators at a Bloch wavevector k (Eq. hij with the 1/2 |k|^2
+        and -i k . grad terms, Bloch phases of Eqs. FE nonlocal contribution /
+        FEM Cmatrix): complex H(k), S(k), exact and approximate S(k)^-1.
 
 Parity status of each function is stated in its docstring ("pinned by ..."
 naming the test in ``tests/test_oracle_*.py``); functions without a pin say

@@ -64,11 +64,13 @@ def rchfsi_filter(apply_H, apply_S, apply_Sinv, X, lam, m: int,
                   a0: float, bW: float, bU: float, trace=None):
     """Algorithm 2, steps 1-5, in the paper's order and notation.
 
-    X: (ndof, B) block Psi_in; lam: (B,) eigenvalue estimates Lambda.
-    Returns Psi_f = S^-1 R_Y + X Lambda_Y.  ``trace`` (a list) receives the
-    per-iteration (zeta, Lambda_Y) after each loop step.
+    X: (ndof, B) block Psi_in (real, or complex for the problem at a Bloch
+    wavevector k); lam: (B,) eigenvalue estimates Lambda (real: H, S are
+    Hermitian).  Returns Psi_f = S^-1 R_Y + X Lambda_Y.  ``trace`` (a list)
+    receives the per-iteration (zeta, Lambda_Y) after each loop step.
     """
-    X = np.asarray(X, float)
+    X = np.asarray(X)
+    X = X if np.iscomplexobj(X) else X.astype(float)
     lam = np.asarray(lam, float)
     # step 1
     e = (bU - bW) / 2.0

@@ -16,13 +16,18 @@ from . import cheb
 
 
 def rayleigh_ritz(ops, Xf):
-    """Steps 4-6 of Algorithm 1 in FP64. Returns (Psi, lambda) ascending."""
+    """Steps 4-6 of Algorithm 1 in FP64. Returns (Psi, lambda) ascending.
+
+    H^p = Psi_f^dagger H Psi_f (the transpose for real blocks, the conjugate
+    transpose for complex ones at a Bloch wavevector k).
+    """
     HX = ops.apply_H(Xf)
     SX = ops.apply_S(Xf)
-    Hp = Xf.T @ HX
-    Sp = Xf.T @ SX
-    Hp = 0.5 * (Hp + Hp.T)
-    Sp = 0.5 * (Sp + Sp.T)
+    Xh = Xf.conj().T
+    Hp = Xh @ HX
+    Sp = Xh @ SX
+    Hp = 0.5 * (Hp + Hp.conj().T)
+    Sp = 0.5 * (Sp + Sp.conj().T)
     lam, Q = sla.eigh(Hp, Sp)
     return Xf @ Q, lam
 
@@ -42,16 +47,16 @@ def lanczos_bounds(apply_SinvH, apply_S, ndof: int, k: int = 20, seed: int = 7):
     """
     rng = np.random.default_rng(seed)
     v = rng.standard_normal(ndof)
-    v /= np.sqrt(v @ apply_S(v[:, None])[:, 0])
+    v = v / np.sqrt(np.vdot(v, apply_S(v[:, None])[:, 0]).real)
     vprev = np.zeros(ndof)
     alphas, betas = [], []
     beta = 0.0
     for _j in range(k):
         w = apply_SinvH(v[:, None])[:, 0]
-        a = v @ apply_S(w[:, None])[:, 0]
+        a = np.vdot(v, apply_S(w[:, None])[:, 0]).real      # S inner product (Hermitian: real)
         w = w - a * v - beta * vprev
         Sw = apply_S(w[:, None])[:, 0]
-        beta = float(np.sqrt(max(w @ Sw, 0.0)))
+        beta = float(np.sqrt(max(np.vdot(w, Sw).real, 0.0)))
         alphas.append(a)
         betas.append(beta)
         vprev, v = v, w / beta
