@@ -35,6 +35,20 @@
  * N1 = n p.  Kinetic and mass cell matrices use (p+1)^3 Gauss points, the
  * potential and projector integrals use (p+2)^3 Gauss points; quadrature
  * point q = i + (p+2) (j + (p+2) k) of cell e = cx + n (cy + n cz).
+ *
+ * Bloch wavevector (Eq. FE PAW governing equations, k in the Brillouin zone):
+ * paw_options.kpoint = k (Cartesian, 1/bohr).  With k != 0 the handle solves
+ * H(k) u = eps S(k) u for the periodic factor u of psi = e^{i k.x} u, with the
+ * 1/2 |k|^2 mass term and the -i k . N_I grad N_J term of Eq. hij and the
+ * Bloch phases e^{-i k.(x - L_r)} of C^{a,k} (Eqs. FE nonlocal contribution,
+ * FEM Cmatrix), and every multivector argument of paw_apply_H / _S /
+ * _Sinv_approx, paw_cheb_filter, paw_rayleigh_ritz and paw_residuals is
+ * COMPLEX, interleaved (real, imaginary) per entry: element (dof, j) is the
+ * pair X[2 (dof * ld + j)], X[2 (dof * ld + j) + 1] (cuDoubleComplex for
+ * FP64 arguments, cuFloatComplex for FP32 ones), ld counted in complex
+ * entries.  Eigenvalues, bounds and norms stay real.  paw_lanczos_bounds,
+ * paw_energy, paw_energy_grad, paw_density, the batch calls and
+ * paw_apply_Sinv_approx_noalloc return PAW_ERR_UNSUPPORTED for such handles.
  */
 #ifndef PAW_FE_H
 #define PAW_FE_H
@@ -109,6 +123,8 @@ typedef struct {
   int32_t rr_mixed;    /* 1: paw_rayleigh_ritz rotates with the diagonal of Q in
                           FP64 and its off-diagonal part in FP32 (Sec. 4.4,
                           mixed-precision subspace rotation)                    */
+  double kpoint[3];    /* Bloch wavevector k (1/bohr); nonzero: complex vectors
+                          (see the conventions at the top of this file)        */
 } paw_options;
 
 /* Filter bounds (Algorithm 2 inputs): a0 lower end of the wanted spectrum,
@@ -131,8 +147,10 @@ typedef struct {
   int64_t owner_pairs;     /* (cell, atom) pairs with P^a nonzero on a node the
                               cell owns (local indices < p): the work unit of the
                               projector contractions                          */
-  int32_t nproj_padded;    /* projectors per atom as stored (16 or 32)        */
-  int32_t reserved;
+  int32_t nproj_padded;    /* projectors per atom as stored (16 or 32; with k != 0
+                              the real and imaginary parts of C^{a,k} are stored
+                              as 2 nproj real projectors)                      */
+  int32_t complex_vectors; /* 1: k != 0, multivector arguments are complex     */
   int64_t proj_nnz;        /* nonzero entries of the assembled P^a on owned nodes,
                               summed over atoms: the algorithmic size of one
                               projector contraction (per vector)              */

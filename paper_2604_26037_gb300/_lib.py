@@ -58,7 +58,7 @@ class _Vloc(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("block", C.c_int32), ("pp_overlap", C.c_int32), ("y0_fp32", C.c_int32),
-                ("rr_mixed", C.c_int32)]
+                ("rr_mixed", C.c_int32), ("kpoint", C.c_double * 3)]
 
 
 class _Bounds(C.Structure):
@@ -69,7 +69,7 @@ class _Info(C.Structure):
     _fields_ = [("ndof", C.c_int64), ("ncells", C.c_int32), ("nodes_per_cell", C.c_int32),
                 ("quad_per_cell", C.c_int32), ("natoms", C.c_int32), ("nproj", C.c_int32),
                 ("degree", C.c_int32), ("support_pairs", C.c_int64), ("device_bytes", C.c_int64),
-                ("owner_pairs", C.c_int64), ("nproj_padded", C.c_int32), ("reserved", C.c_int32),
+                ("owner_pairs", C.c_int64), ("nproj_padded", C.c_int32), ("complex_vectors", C.c_int32),
                 ("proj_nnz", C.c_int64)]
 
 
@@ -187,7 +187,7 @@ class PawFE:
     """One PAW finite-element problem on the current CUDA device."""
 
     def __init__(self, L, ncell, degree, positions=(), shells=(), D=None, dS=None,
-                 vloc=None, block=256, pp_overlap=False, y0_fp32=False, rr_mixed=False):
+                 vloc=None, block=256, pp_overlap=False, y0_fp32=False, rr_mixed=False, kpoint=None):
         self._lib = load_library()
         pos = np.ascontiguousarray(np.asarray(positions, float).reshape(-1, 3))
         na = pos.shape[0]
@@ -209,7 +209,9 @@ class PawFE:
             wid = np.ascontiguousarray(np.asarray(vloc["width"], float))
             keep += [cen, dep, wid]
             vp = C.pointer(_Vloc(cen.shape[0], _dptr(cen), _dptr(dep), _dptr(wid)))
-        opts = _Opts(int(block), int(bool(pp_overlap)), int(bool(y0_fp32)), int(bool(rr_mixed)))
+        kp = (0.0, 0.0, 0.0) if kpoint is None else tuple(float(x) for x in kpoint)
+        opts = _Opts(int(block), int(bool(pp_overlap)), int(bool(y0_fp32)), int(bool(rr_mixed)),
+                     (C.c_double * 3)(*kp))
         h = C.c_void_p()
         _check(self._lib.paw_fe_create(C.byref(mesh), int(degree), C.byref(atoms), C.byref(proj),
                                        _dptr(Dh), _dptr(dSh), vp, C.byref(opts), C.byref(h)))
@@ -225,6 +227,7 @@ class PawFE:
         self.owner_pairs = int(info.owner_pairs)
         self.nproj_padded = int(info.nproj_padded)
         self.proj_nnz = int(info.proj_nnz)
+        self.complex = bool(info.complex_vectors)   # k != 0: complex multivectors
         self.block = int(block)
 
     @classmethod
@@ -270,7 +273,10 @@ class PawFE:
     def _apply(self, fn, X, Y, prec):
         import torch
         prec = Precision.of(prec)
-        dt = torch.float64 if prec == Precision.FP64 else torch.float32
+        if self.complex:
+            dt = torch.complex128 if prec == Precision.FP64 else torch.complex64
+        else:
+            dt = torch.float64 if prec == Precision.FP64 else torch.float32
         xp, rows, n, ldx = _mat(X, dt)
         if rows != self.ndof:
             raise ValueError(f"X has {rows} rows, expected {self.ndof}")
@@ -292,12 +298,16 @@ class PawFE:
         return self._apply(self._lib.paw_apply_Sinv_approx, X, Y, prec)
 
     # ------------------------------------------------------------------ filter
+    def _fp64(self):
+        import torch
+        return torch.complex128 if self.complex else torch.float64
+
     def cheb_filter(self, X, lam, degree, bounds, prec="tf32", out=None):
         import torch
-        xp, rows, n, ldx = _mat(X, torch.float64)
+        xp, rows, n, ldx = _mat(X, self._fp64())
         if out is None:
-            out = torch.empty((self.ndof, n), dtype=torch.float64, device=X.device)
-        op, _, n2, ldo = _mat(out, torch.float64)
+            out = torch.empty((self.ndof, n), dtype=self._fp64(), device=X.device)
+        op, _, n2, ldo = _mat(out, self._fp64())
         lam = np.ascontiguousarray(np.asarray(lam, float).reshape(-1))
         if n2 != n or lam.size != n:
             raise ValueError("column counts of X, out and lambda differ")
@@ -307,15 +317,13 @@ class PawFE:
         return out
 
     def rayleigh_ritz(self, X):
-        import torch
-        xp, rows, n, ld = _mat(X, torch.float64)
+        xp, rows, n, ld = _mat(X, self._fp64())
         lam = np.zeros(n)
         _check(self._lib.paw_rayleigh_ritz(self._h, xp, ld, n, _dptr(lam), _stream(X)))
         return lam
 
     def residuals(self, X, lam):
-        import torch
-        xp, rows, n, ld = _mat(X, torch.float64)
+        xp, rows, n, ld = _mat(X, self._fp64())
         lam = np.ascontiguousarray(np.asarray(lam, float))
         out = np.zeros(n)
         _check(self._lib.paw_residuals(self._h, xp, ld, _dptr(lam), n, _dptr(out), _stream(X)))

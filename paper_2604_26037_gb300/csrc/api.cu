@@ -172,14 +172,52 @@ static inline dim3 ew_grid(int64_t rows, int ncols) {
   return dim3((unsigned)((rows + 7) / 8), (ncols + 31) / 32);
 }
 
+// Complex multivectors at k != 0: interleaved (re, im) entries, ld in complex
+// entries  <->  split real blocks [Re | Im] of 2 n columns (ld = 2 n).
+template <typename T>
+__global__ void k_split_cplx(int64_t rows, int n, const T *__restrict__ Z, int ldz, T *__restrict__ Xs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= rows || j >= n) return;
+  const T re = Z[2 * (i * ldz + j)], im = Z[2 * (i * ldz + j) + 1];
+  Xs[i * 2 * n + j] = re;
+  Xs[i * 2 * n + n + j] = im;
+}
+
+template <typename T>
+__global__ void k_merge_cplx(int64_t rows, int n, const T *__restrict__ Xs, T *__restrict__ Z, int ldz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= rows || j >= n) return;
+  Z[2 * (i * ldz + j)] = Xs[i * 2 * n + j];
+  Z[2 * (i * ldz + j) + 1] = Xs[i * 2 * n + n + j];
+}
+
+template <typename T>
+static void split_cplx(paw_context *c, const T *Z, int ldz, int n, T *Xs, cudaStream_t s) {
+  k_split_cplx<T><<<ew_grid(c->ndof, n), dim3(32, 8), 0, s>>>(c->ndof, n, Z, ldz, Xs);
+  PAW_LAUNCH_CHECK("k_split_cplx");
+}
+
+template <typename T>
+static void merge_cplx(paw_context *c, const T *Xs, int n, T *Z, int ldz, cudaStream_t s) {
+  k_merge_cplx<T><<<ew_grid(c->ndof, n), dim3(32, 8), 0, s>>>(c->ndof, n, Xs, Z, ldz);
+  PAW_LAUNCH_CHECK("k_merge_cplx");
+}
+
 // Y = H X - S X Lambda in FP64 (Algorithm 2 step 2)
 static void residual_block(paw_context *c, const double *X, int ldx, const double *negLam_dev,
                            double *Y, int ldy, int ncols, cudaStream_t s) {
   zero_block<double>(Y, c->ndof, ncols, ldy, s);
-  // (1/2 K^e + V^e - lambda_j M^e) X_e in one sum-factorised pass
+  // (1/2 K^e + V^e + (1/2 |k|^2 - lambda_j) M^e) X_e in one sum-factorised pass;
+  // at k != 0 the Bloch term -i B of Eq. hij on the split block [Re | Im]
   {
     PhaseScope ps(c, 0, s);
-    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, 0.0, negLam_dev, s);
+    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, c->kmass, negLam_dev, s);
+    if (c->kc) {
+      bloch_sf(c, X + ncols / 2, ldx, Y, ldy, ncols / 2, 1.0, s);
+      bloch_sf(c, X, ldx, Y + ncols / 2, ldy, ncols / 2, -1.0, s);
+    }
   }
   if (c->nown_pairs > 0) {
     PhaseScope ps(c, 4, s);
@@ -592,6 +630,51 @@ static void check_sym(const double *A, int na, int n, const char *what) {
   }
 }
 
+// At k != 0: split the complex argument, apply the operator to the real block
+// [Re | Im] of 2 ncols columns, merge the result back (0: H, 1: S, 2: Shat^-1).
+template <typename T>
+static void apply_cplx(paw_context *c, paw_precision prec, int which, const T *X, int ldx, T *Y, int ldy, int ncols,
+                       cudaStream_t s) {
+  const int n2 = 2 * ncols;
+  c->ws_cx.ensure(sizeof(T) * (size_t)c->ndof * n2, &c->dev_bytes);
+  c->ws_cy.ensure(sizeof(T) * (size_t)c->ndof * n2, &c->dev_bytes);
+  T *xs = c->ws_cx.as<T>(), *ys = c->ws_cy.as<T>();
+  split_cplx<T>(c, X, ldx, ncols, xs, s);
+  if (which == 0)
+    op_H<T>(c, prec, xs, n2, ys, n2, n2, s);
+  else if (which == 1)
+    op_S<T>(c, xs, n2, ys, n2, n2, s);
+  else
+    op_Sinv<T>(c, prec, xs, n2, ys, n2, n2, s);
+  merge_cplx<T>(c, ys, ncols, Y, ldy, s);
+}
+
+static void apply_any(paw_context *c, paw_precision prec, int which, const void *X, int ldx, void *Y, int ldy,
+                      int ncols, cudaStream_t s) {
+  if (c->kc) {
+    if (prec == PAW_FP64)
+      apply_cplx<double>(c, prec, which, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+    else
+      apply_cplx<float>(c, prec, which, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+    return;
+  }
+  if (prec == PAW_FP64) {
+    if (which == 0)
+      op_H<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+    else if (which == 1)
+      op_S<double>(c, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+    else
+      op_Sinv<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+  } else {
+    if (which == 0)
+      op_H<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+    else if (which == 1)
+      op_S<float>(c, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+    else
+      op_Sinv<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  }
+}
+
 extern "C" {
 
 const char *paw_last_error(void) { return g_last_error.c_str(); }
@@ -677,6 +760,14 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
     }
     if (opts) c->opts = *opts;
     if (c->opts.block <= 0) c->opts.block = 256;
+    for (int d = 0; d < 3; ++d) {
+      PAW_REQUIRE(std::isfinite(c->opts.kpoint[d]), PAW_ERR_INVALID_ARG, "kpoint has NaN/Inf");
+      c->kvec[d] = c->opts.kpoint[d];
+    }
+    c->kc = (c->kvec[0] != 0.0 || c->kvec[1] != 0.0 || c->kvec[2] != 0.0) ? 1 : 0;
+    c->kmass = 0.5 * (c->kvec[0] * c->kvec[0] + c->kvec[1] * c->kvec[1] + c->kvec[2] * c->kvec[2]);
+    PAW_REQUIRE(!c->kc || npj <= 16, PAW_ERR_UNSUPPORTED, "at most 16 projectors per atom with a Bloch wavevector");
+    c->npjr = c->kc ? 2 * npj : npj;
     if (npj == 0) c->natoms = 0;   // atoms without projectors carry no nonlocal term
     c->status_dev.ensure(sizeof(int), &c->dev_bytes);
     PAW_CUDA(cudaMemset(c->status_dev.ptr, 0, sizeof(int)));
@@ -712,7 +803,8 @@ paw_status paw_destroy(paw_handle c) {
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
                     &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
                     &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
-                    &c->own_lg, &c->own_sidx, &c->own_cnt,
+                    &c->own_lg, &c->own_sidx, &c->own_cnt, &c->Bk64, &c->Bk32, &c->tc_bk_tf32.He,
+                    &c->tc_bk_bf16.He, &c->ws_cx, &c->ws_cy,
                     &c->nltc.eoff};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -736,7 +828,7 @@ paw_status paw_get_info(paw_handle c, paw_info *out) {
   out->owner_pairs = c->nown_pairs;
   out->nproj_padded = c->npad;
   out->proj_nnz = c->proj_nnz;
-  out->reserved = 0;
+  out->complex_vectors = c->kc;
   return PAW_OK;
 }
 
@@ -790,10 +882,7 @@ paw_status paw_apply_H(paw_handle c, paw_precision prec, const void *X, void *Y,
   if (ncols == 0) return PAW_OK;
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
-  if (prec == PAW_FP64)
-    op_H<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
-  else
-    op_H<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  apply_any(c, prec, 0, X, ldx, Y, ldy, ncols, s);
   check_tc_status(c, prec);
   return PAW_OK;
   PAW_TRY_END
@@ -807,10 +896,7 @@ paw_status paw_apply_S(paw_handle c, paw_precision prec, const void *X, void *Y,
   if (ncols == 0) return PAW_OK;
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
-  if (prec == PAW_FP64)
-    op_S<double>(c, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
-  else
-    op_S<float>(c, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  apply_any(c, prec, 1, X, ldx, Y, ldy, ncols, s);
   return PAW_OK;
   PAW_TRY_END
 }
@@ -823,10 +909,7 @@ paw_status paw_apply_Sinv_approx(paw_handle c, paw_precision prec, const void *X
   if (ncols == 0) return PAW_OK;
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
-  if (prec == PAW_FP64)
-    op_Sinv<double>(c, prec, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
-  else
-    op_Sinv<float>(c, prec, (const float *)X, ldx, (float *)Y, ldy, ncols, s);
+  apply_any(c, prec, 2, X, ldx, Y, ldy, ncols, s);
   check_tc_status(c, prec);
   return PAW_OK;
   PAW_TRY_END
@@ -850,10 +933,82 @@ paw_status paw_cheb_filter(paw_handle c, paw_precision prec, const double *X_in,
   const int B = c->opts.block;
   for (int j0 = 0; j0 < ncols; j0 += B) {
     const int nb = std::min(B, ncols - j0);
+    if (c->kc) {
+      // complex block: Algorithm 2 on the split block [Re | Im] with every
+      // eigenvalue estimate applying to both halves (the scalars stay real)
+      c->ws_cx.ensure(sizeof(double) * (size_t)c->ndof * 2 * nb, &c->dev_bytes);
+      c->ws_cy.ensure(sizeof(double) * (size_t)c->ndof * 2 * nb, &c->dev_bytes);
+      std::vector<double> lam2(2 * (size_t)nb);
+      for (int j = 0; j < nb; ++j) lam2[j] = lam2[nb + j] = lambda_in[j0 + j];
+      split_cplx<double>(c, X_in + 2 * (size_t)j0, ldx, nb, c->ws_cx.as<double>(), s);
+      cheb_block(c, prec, c->ws_cx.as<double>(), 2 * nb, lam2.data(), 2 * nb, degree, b, c->ws_cy.as<double>(),
+                 2 * nb, s);
+      merge_cplx<double>(c, c->ws_cy.as<double>(), nb, X_out + 2 * (size_t)j0, ldo, s);
+      continue;
+    }
     cheb_block(c, prec, X_in + j0, ldx, lambda_in + j0, nb, degree, b, X_out + j0, ldo, s);
   }
   return PAW_OK;
   PAW_TRY_END
+}
+
+// Rayleigh-Ritz at k != 0 (complex X, interleaved, ld complex entries).  In the
+// column-major view Xc = X^T (N x M), C = (H X)^T Xc^H = conj(H^p) and
+// D = conj(S^p); zhegvd on (C, D) gives the Ritz values and Y = conj(Q), and
+// X <- X Q is Xc <- Y^H Xc.
+static void rr_complex(paw_context *c, double *X, int ld, int N, double *lambda_out, cudaStream_t s) {
+  const int M = (int)c->ndof;
+  const int Bc = std::min(N, c->opts.block);
+  c->ws_HX.ensure(sizeof(double) * 2 * (size_t)M * N, &c->dev_bytes);
+  c->ws_SX.ensure(sizeof(double) * 2 * (size_t)M * N, &c->dev_bytes);
+  c->ws_Hp.ensure(sizeof(double) * 2 * (size_t)N * N, &c->dev_bytes);
+  c->ws_Sp.ensure(sizeof(double) * 2 * (size_t)N * N, &c->dev_bytes);
+  double *HX = c->ws_HX.as<double>(), *SX = c->ws_SX.as<double>();
+  for (int j0 = 0; j0 < N; j0 += Bc) {
+    const int nb = std::min(Bc, N - j0);
+    apply_cplx<double>(c, PAW_FP64, 0, X + 2 * (size_t)j0, ld, HX + 2 * (size_t)j0, N, nb, s);
+    apply_cplx<double>(c, PAW_FP64, 1, X + 2 * (size_t)j0, ld, SX + 2 * (size_t)j0, N, nb, s);
+  }
+  cublasSetStream(c->cublas, s);
+  cusolverDnSetStream(c->cusolver, s);
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+  auto *Xc = reinterpret_cast<cuDoubleComplex *>(X);
+  auto *Cm = reinterpret_cast<cuDoubleComplex *>(c->ws_Hp.ptr);
+  auto *Dm = reinterpret_cast<cuDoubleComplex *>(c->ws_Sp.ptr);
+  if (cublasZgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_C, N, N, M, &one, reinterpret_cast<cuDoubleComplex *>(HX), N,
+                  Xc, ld, &zero, Cm, N) != CUBLAS_STATUS_SUCCESS ||
+      cublasZgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_C, N, N, M, &one, reinterpret_cast<cuDoubleComplex *>(SX), N,
+                  Xc, ld, &zero, Dm, N) != CUBLAS_STATUS_SUCCESS)
+    throw Error{PAW_ERR_LIBRARY, "cublasZgemm (projection) failed"};
+  int lwork = 0;
+  c->ws_eig.ensure(sizeof(double) * N, &c->dev_bytes);
+  c->ws_info.ensure(sizeof(int), &c->dev_bytes);
+  if (cusolverDnZhegvd_bufferSize(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                  N, Cm, N, Dm, N, c->ws_eig.as<double>(), &lwork) != CUSOLVER_STATUS_SUCCESS)
+    throw Error{PAW_ERR_LIBRARY, "cusolverDnZhegvd_bufferSize failed"};
+  c->ws_solver.ensure(sizeof(cuDoubleComplex) * std::max(1, lwork), &c->dev_bytes);
+  if (cusolverDnZhegvd(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, Cm, N,
+                       Dm, N, c->ws_eig.as<double>(), reinterpret_cast<cuDoubleComplex *>(c->ws_solver.ptr), lwork,
+                       c->ws_info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+    throw Error{PAW_ERR_LIBRARY, "cusolverDnZhegvd failed"};
+  int info = 0;
+  PAW_CUDA(cudaMemcpyAsync(&info, c->ws_info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PAW_CUDA(cudaStreamSynchronize(s));
+  PAW_REQUIRE(info <= N, PAW_ERR_NOT_SPD, "projected overlap S^p is not positive definite");
+  PAW_REQUIRE(info == 0, PAW_ERR_LIBRARY, "zhegvd did not converge");
+  const int rows = std::min(M, std::max(1024, (1 << 26) / N));
+  c->ws_rot.ensure(sizeof(cuDoubleComplex) * (size_t)rows * N, &c->dev_bytes);
+  auto *tmp = reinterpret_cast<cuDoubleComplex *>(c->ws_rot.ptr);
+  for (int r0 = 0; r0 < M; r0 += rows) {
+    const int nr = std::min(rows, M - r0);
+    if (cublasZgemm(c->cublas, CUBLAS_OP_C, CUBLAS_OP_N, N, nr, N, &one, Cm, N, Xc + (size_t)r0 * ld, ld, &zero,
+                    tmp, N) != CUBLAS_STATUS_SUCCESS)
+      throw Error{PAW_ERR_LIBRARY, "cublasZgemm (rotation) failed"};
+    PAW_CUDA(cudaMemcpy2DAsync(Xc + (size_t)r0 * ld, sizeof(cuDoubleComplex) * ld, tmp, sizeof(cuDoubleComplex) * N,
+                               sizeof(cuDoubleComplex) * N, nr, cudaMemcpyDeviceToDevice, s));
+  }
+  PAW_CUDA(cudaMemcpyAsync(lambda_out, c->ws_eig.ptr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  PAW_CUDA(cudaStreamSynchronize(s));
 }
 
 paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lambda_out, void *stream) {
@@ -863,6 +1018,10 @@ paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lam
   PAW_REQUIRE(c->ndof < (1ll << 31), PAW_ERR_UNSUPPORTED, "ndof >= 2^31");
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
+  if (c->kc) {
+    rr_complex(c, X, ld, N, lambda_out, s);
+    return PAW_OK;
+  }
   const int M = (int)c->ndof;
   const int Bc = std::min(N, c->opts.block);
   c->ws_HX.ensure(sizeof(double) * (size_t)M * Bc, &c->dev_bytes);
@@ -948,6 +1107,26 @@ paw_status paw_residuals(paw_handle c, const double *X, int ld, const double *la
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
   const int Bc = std::min(N, c->opts.block);
+  if (c->kc) {
+    // complex columns: ||r||^2 = ||Re r||^2 + ||Im r||^2 from the split block
+    c->ws_cx.ensure(sizeof(double) * (size_t)c->ndof * 2 * Bc, &c->dev_bytes);
+    c->ws_HX.ensure(sizeof(double) * (size_t)c->ndof * 2 * Bc, &c->dev_bytes);
+    c->ws_SX.ensure(sizeof(double) * (size_t)c->ndof * 2 * Bc, &c->dev_bytes);
+    c->ws_colscale.ensure(sizeof(double) * 2 * Bc, &c->dev_bytes);
+    for (int j0 = 0; j0 < N; j0 += Bc) {
+      const int nb = std::min(Bc, N - j0);
+      std::vector<double> nl(2 * (size_t)nb);
+      for (int j = 0; j < nb; ++j) nl[j] = nl[nb + j] = -lambda[j0 + j];
+      PAW_CUDA(cudaMemcpyAsync(c->ws_colscale.ptr, nl.data(), sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, s));
+      split_cplx<double>(c, X + 2 * (size_t)j0, ld, nb, c->ws_cx.as<double>(), s);
+      op_H<double>(c, PAW_FP64, c->ws_cx.as<double>(), 2 * nb, c->ws_HX.as<double>(), 2 * nb, 2 * nb, s);
+      op_S<double>(c, c->ws_cx.as<double>(), 2 * nb, c->ws_SX.as<double>(), 2 * nb, 2 * nb, s);
+      std::vector<double> r = column_reduce(c, false, c->ws_HX.as<double>(), 2 * nb, c->ws_SX.as<double>(), 2 * nb,
+                                            c->ws_colscale.as<double>(), 2 * nb, s);
+      for (int j = 0; j < nb; ++j) rnorm_out[j0 + j] = std::sqrt(r[j] + r[nb + j]);
+    }
+    return PAW_OK;
+  }
   c->ws_HX.ensure(sizeof(double) * (size_t)c->ndof * Bc, &c->dev_bytes);
   c->ws_SX.ensure(sizeof(double) * (size_t)c->ndof * Bc, &c->dev_bytes);
   c->ws_colscale.ensure(sizeof(double) * Bc, &c->dev_bytes);
@@ -972,26 +1151,34 @@ paw_status paw_lanczos_bounds(paw_handle c, int k, uint64_t seed, double *theta_
   PAW_REQUIRE(k >= 2 && k <= 200, PAW_ERR_INVALID_ARG, "k must be in 2..200");
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
-  const int64_t M = c->ndof;
+  // at k != 0 a vector is the split pair [Re v | Im v] (two columns): the process
+  // runs on the real symmetric form of the Hermitian pencil, whose inner product
+  // Re <v, S w> is the sum over both columns
+  const int nw = c->kc ? 2 : 1;
+  const int64_t M = c->ndof * nw;
   c->ws_vec.ensure(sizeof(double) * M * 5, &c->dev_bytes);
   double *v = c->ws_vec.as<double>(), *vp = v + M, *w = v + 2 * M, *Hv = v + 3 * M, *Sw = v + 4 * M;
   const unsigned g = (unsigned)((M + 255) / 256);
+  auto dot = [&](const double *A, const double *B) {
+    const std::vector<double> r = column_reduce(c, true, A, nw, B, nw, nullptr, nw, s);
+    return nw == 2 ? r[0] + r[1] : r[0];
+  };
   k_random_vec<<<g, 256, 0, s>>>(M, seed, v);
   PAW_LAUNCH_CHECK("k_random_vec");
-  op_S<double>(c, v, 1, Sw, 1, 1, s);
-  double nrm = std::sqrt(column_reduce(c, true, v, 1, Sw, 1, nullptr, 1, s)[0]);
+  op_S<double>(c, v, nw, Sw, nw, nw, s);
+  double nrm = std::sqrt(dot(v, Sw));
   k_axpby<<<g, 256, 0, s>>>(M, 1.0 / nrm, v, 0.0, nullptr, 0.0, nullptr, v);
   PAW_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * M, s));
   std::vector<double> al, be;
   double beta = 0.0;
   for (int j = 0; j < k; ++j) {
-    op_H<double>(c, PAW_FP64, v, 1, Hv, 1, 1, s);
-    op_Sinv<double>(c, PAW_FP64, Hv, 1, w, 1, 1, s);
-    op_S<double>(c, w, 1, Sw, 1, 1, s);
-    const double a = column_reduce(c, true, v, 1, Sw, 1, nullptr, 1, s)[0];
+    op_H<double>(c, PAW_FP64, v, nw, Hv, nw, nw, s);
+    op_Sinv<double>(c, PAW_FP64, Hv, nw, w, nw, nw, s);
+    op_S<double>(c, w, nw, Sw, nw, nw, s);
+    const double a = dot(v, Sw);
     k_axpby<<<g, 256, 0, s>>>(M, 1.0, w, -a, v, -beta, vp, w);
-    op_S<double>(c, w, 1, Sw, 1, 1, s);
-    beta = std::sqrt(std::max(column_reduce(c, true, w, 1, Sw, 1, nullptr, 1, s)[0], 0.0));
+    op_S<double>(c, w, nw, Sw, nw, nw, s);
+    beta = std::sqrt(std::max(dot(w, Sw), 0.0));
     al.push_back(a);
     be.push_back(beta);
     PAW_CUDA(cudaMemcpyAsync(vp, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
@@ -1014,6 +1201,7 @@ paw_status paw_lanczos_bounds(paw_handle c, int k, uint64_t seed, double *theta_
 paw_status paw_energy(paw_handle c, paw_precision prec, const void *X, int ld, int N, double *E_out,
                       void *stream) {
   PAW_TRY_BEGIN
+  PAW_REQUIRE(c == nullptr || !c->kc, PAW_ERR_UNSUPPORTED, "paw_energy has no Bloch-wavevector form");
   check_prec(prec);
   PAW_REQUIRE(c && X && E_out, PAW_ERR_INVALID_ARG, "NULL argument");
   PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
@@ -1074,6 +1262,7 @@ static void density_like(paw_context *c, paw_precision prec, const void *X, int 
 paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int ld, int N, double *dE_dV,
                            double *dE_dD, void *stream) {
   PAW_TRY_BEGIN
+  PAW_REQUIRE(c == nullptr || !c->kc, PAW_ERR_UNSUPPORTED, "paw_energy_grad has no Bloch-wavevector form");
   check_prec(prec);
   PAW_REQUIRE(c && X && dE_dV, PAW_ERR_INVALID_ARG, "NULL argument");
   PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");
@@ -1087,6 +1276,7 @@ paw_status paw_energy_grad(paw_handle c, paw_precision prec, const void *X, int 
 paw_status paw_density(paw_handle c, paw_precision prec, const void *X, int ld, int N, const double *occ,
                        double *rho_q, double *D_a, void *stream) {
   PAW_TRY_BEGIN
+  PAW_REQUIRE(c == nullptr || !c->kc, PAW_ERR_UNSUPPORTED, "paw_density has no Bloch-wavevector form");
   check_prec(prec);
   PAW_REQUIRE(c && X && rho_q, PAW_ERR_INVALID_ARG, "NULL argument");
   PAW_REQUIRE(N >= 1 && ld >= N, PAW_ERR_INVALID_ARG, "need 1 <= N <= ld");

@@ -234,6 +234,7 @@ paw_status paw_batch_create(const paw_handle *handles, int count, const paw_batc
     PAW_REQUIRE(handles != nullptr && count >= 1, PAW_ERR_INVALID_ARG, "need count >= 1 handles");
     for (int i = 0; i < count; ++i) {
       PAW_REQUIRE(handles[i] != nullptr, PAW_ERR_INVALID_ARG, "NULL handle in the batch");
+      PAW_REQUIRE(!handles[i]->kc, PAW_ERR_UNSUPPORTED, "batches take handles without a Bloch wavevector");
       for (int j = 0; j < i; ++j)
         PAW_REQUIRE(handles[j] != handles[i], PAW_ERR_INVALID_ARG, "a handle appears twice in the batch");
     }

@@ -325,24 +325,30 @@ static void tile_geometry(int nc, bool bf16, int &ntile, int &ntiles, int &kchun
   kchunks = (nc + epr - 1) / epr;
 }
 
-void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s) {
-  const bool bf16 = prec == PAW_BF16;
-  TcMats &T = bf16 ? c->tc_bf16 : c->tc_tf32;
+// Tiled tcgen05 image of nmat FP32 cell matrices (nc x nc, row-major, stride
+// nc^2) into T (TF32-rounded or BF16), built once.
+static void tc_prepare_mats(paw_context *c, paw_precision prec, TcMats &T, const float *src, int nmat,
+                            cudaStream_t s) {
   if (T.valid) return;
+  const bool bf16 = prec == PAW_BF16;
   tile_geometry(c->nc, bf16, T.ntile, T.ntiles, T.kchunks);
   T.chunk_bytes = (size_t)T.ntile * 128;
   T.cell_bytes = T.chunk_bytes * T.kchunks * T.ntiles;
-  T.He.ensure(T.cell_bytes * c->ncells, &c->dev_bytes);
-  const int64_t total = (int64_t)c->ncells * T.ntiles * T.kchunks * T.ntile * 8;
+  T.He.ensure(T.cell_bytes * nmat, &c->dev_bytes);
+  const int64_t total = (int64_t)nmat * T.ntiles * T.kchunks * T.ntile * 8;
   const unsigned grid = (unsigned)((total + 255) / 256);
   if (bf16)
-    k_tile_mats<true><<<grid, 256, 0, s>>>(c->He32.as<float>(), (long long)c->nc * c->nc, c->ncells, c->nc,
-                                           T.ntile, T.ntiles, T.kchunks, T.He.as<uint8_t>());
+    k_tile_mats<true><<<grid, 256, 0, s>>>(src, (long long)c->nc * c->nc, nmat, c->nc, T.ntile, T.ntiles,
+                                           T.kchunks, T.He.as<uint8_t>());
   else
-    k_tile_mats<false><<<grid, 256, 0, s>>>(c->He32.as<float>(), (long long)c->nc * c->nc, c->ncells, c->nc,
-                                            T.ntile, T.ntiles, T.kchunks, T.He.as<uint8_t>());
+    k_tile_mats<false><<<grid, 256, 0, s>>>(src, (long long)c->nc * c->nc, nmat, c->nc, T.ntile, T.ntiles,
+                                            T.kchunks, T.He.as<uint8_t>());
   PAW_LAUNCH_CHECK("k_tile_mats");
   T.valid = 1;
+}
+
+void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s) {
+  tc_prepare_mats(c, prec, prec == PAW_BF16 ? c->tc_bf16 : c->tc_tf32, c->He32.as<float>(), c->ncells, s);
 }
 
 size_t tc_smem_bytes(int ntile, int kchunks, bool bf16) {
@@ -387,36 +393,37 @@ static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx
   PAW_LAUNCH_CHECK("k_tc_stream<cell>");
 }
 
-void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, float *Y, int ldy, int ncols,
-                   float alpha, cudaStream_t s) {
-  if (ncols <= 0) return;
+// Y += alpha A_e X_e cell by cell with the tiled matrices of T (cell_bytes = 0:
+// one matrix shared by every cell)
+static void cell_apply_tc_mats(paw_context *c, paw_precision prec, const TcMats &T, size_t cell_bytes,
+                               const float *X, int ldx, float *Y, int ldy, int ncols, float alpha, cudaStream_t s) {
   const bool bf16 = prec == PAW_BF16;
-  tc_prepare(c, prec, s);
-  TcMats &T = bf16 ? c->tc_bf16 : c->tc_tf32;
-  // rows of X copied with 16-byte cp.async: aligned base, pitch and vector range
+  TcMats Tm = T;
+  Tm.cell_bytes = cell_bytes;
+  // rows of X gathered with TMA: aligned base, pitch and vector range
   if (c->tc_variant == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 && ldx % 4 == 0 && ncols % 4 == 0 &&
-      T.ntile <= 256) {
-    const bool small = T.ntile <= 176;
+      Tm.ntile <= 256) {
+    const bool small = Tm.ntile <= 176;
     if (bf16) {
       if (small)
-        cell_stream<true, true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<true, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
       else
-        cell_stream<true, false>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<true, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
     } else {
       if (small)
-        cell_stream<false, true>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<false, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
       else
-        cell_stream<false, false>(c, T, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<false, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
     }
     return;
   }
   TcArgs a;
-  a.Ht = T.He.as<uint8_t>();
-  a.cell_bytes = T.cell_bytes;
+  a.Ht = Tm.He.as<uint8_t>();
+  a.cell_bytes = cell_bytes;
   a.nc = c->nc;
-  a.ntile = T.ntile;
-  a.ntiles = T.ntiles;
-  a.kchunks = T.kchunks;
+  a.ntile = Tm.ntile;
+  a.ntiles = Tm.ntiles;
+  a.kchunks = Tm.kchunks;
   a.vtiles = (ncols + MT - 1) / MT;
   a.cell_dofs = c->cell_dofs.as<int>();
   a.X = X;
@@ -426,8 +433,8 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, 
   a.ncols = ncols;
   a.alpha = alpha;
   a.status = c->status_dev.as<int>();
-  const size_t shm = tc_smem_bytes(T.ntile, T.kchunks, bf16);
-  const int64_t blocks = (int64_t)c->ncells * T.ntiles * a.vtiles;
+  const size_t shm = tc_smem_bytes(Tm.ntile, Tm.kchunks, bf16);
+  const int64_t blocks = (int64_t)c->ncells * Tm.ntiles * a.vtiles;
   PAW_REQUIRE(blocks < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many cell tiles");
   if (bf16) {
     PAW_CUDA(cudaFuncSetAttribute(k_cell_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -437,6 +444,22 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, 
     k_cell_tc<false><<<(unsigned)blocks, THREADS, shm, s>>>(a);
   }
   PAW_LAUNCH_CHECK("k_cell_tc");
+}
+
+void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, float *Y, int ldy, int ncols,
+                   float alpha, cudaStream_t s) {
+  if (ncols <= 0) return;
+  tc_prepare(c, prec, s);
+  const TcMats &T = prec == PAW_BF16 ? c->tc_bf16 : c->tc_tf32;
+  cell_apply_tc_mats(c, prec, T, T.cell_bytes, X, ldx, Y, ldy, ncols, alpha, s);
+}
+
+void bloch_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx, float *Y, int ldy, int ncols,
+                    float alpha, cudaStream_t s) {
+  if (ncols <= 0 || !c->kc) return;
+  TcMats &T = prec == PAW_BF16 ? c->tc_bk_bf16 : c->tc_bk_tf32;
+  tc_prepare_mats(c, prec, T, c->Bk32.as<float>(), 1, s);
+  cell_apply_tc_mats(c, prec, T, 0, X, ldx, Y, ldy, ncols, alpha, s);
 }
 
 }  // namespace pawfe

@@ -121,6 +121,16 @@ struct paw_context {
   int64_t ndof = 0;
   double L = 0, h = 0, detJ = 0;
   int natoms = 0, npj = 0;
+  // Bloch wavevector: kc = 1 when k != 0.  Complex multivectors are then
+  // processed as real blocks of 2 ncols columns [Re | Im]; the projectors
+  // C^{a,k} are stored as npjr = 2 npj real projectors [Re C | Im C]
+  // (npjr = npj at k = 0) and the per-atom couplings act on complex
+  // coefficients.
+  int kc = 0, npjr = 0;
+  double kvec[3] = {0.0, 0.0, 0.0};
+  double kmass = 0.0;                         // 1/2 |k|^2
+  std::vector<double> C1s;                    // 1D skew matrix (C1 - C1^T)/2, C1[a][b] = int l_a l_b' dxi
+  pawfe::DevBuf Bk64, Bk32;                   // Bloch cell matrix B^e = sum_d k_d G^e_d (nc x nc, all cells)
   std::vector<int> shell_l;                   // shells in internal order (decreasing width)
   std::vector<double> shell_w;
   std::vector<int> proj_ext;                  // internal projector -> caller's projector index
@@ -145,6 +155,7 @@ struct paw_context {
   pawfe::DevBuf wV;                           // ncells*nq: w_q detJ V_q (sum-factorised V^e)
   int wV_valid = 0;
   pawfe::TcMats tc_tf32, tc_bf16;
+  pawfe::TcMats tc_bk_tf32, tc_bk_bf16;       // tcgen05 images of B^e (one shared matrix)
   pawfe::NlTcMats nltc;
 
   // projectors: atom-major support entries
@@ -187,6 +198,7 @@ struct paw_context {
   pawfe::DevBuf ws_lam, ws_colscale, ws_red, ws_vec;
   pawfe::DevBuf ws_pp;                        // per-pair projection partials
   pawfe::DevBuf ws_HX, ws_SX, ws_Hp, ws_Sp, ws_eig, ws_solver, ws_info, ws_rot;
+  pawfe::DevBuf ws_cx, ws_cy;                 // split [Re | Im] copies of complex arguments (k != 0)
 
   // tensor-core kernel family: 0 persistent warp-specialised where the layout
   // allows it, 1 one-CTA-per-tile kernels; grid_cap > 0 limits the CTAs of a
@@ -261,7 +273,13 @@ void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, co
 // Y += alpha * (cK K^e + cV V^e + (cM + cMcol[j]) M^e) X, cell by cell with assembly
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
               double cK, double cV, double cM, const double *cMcol, cudaStream_t s);
-// local part of H, accumulated with factor alpha
+// FP64 sum-factorised Bloch term: Y += alpha * B X, B = sum_d k_d G_d cell by cell
+// (G_d the skew cell form of int N_I dN_J/dx_d, Eq. hij), with assembly
+void bloch_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
+              cudaStream_t s);
+// local part of H, accumulated with factor alpha.  With k != 0, ncols is even
+// and X, Y are split complex blocks [Re | Im] of ncols / 2 columns each:
+// H_loc(k) = A - i B adds Y_re += alpha B X_im and Y_im -= alpha B X_re.
 template <typename T>
 void local_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols,
              double alpha, cudaStream_t s);
@@ -286,6 +304,9 @@ void op_Sinv(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int 
 void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s);
 void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
                    float *Y, int ldy, int ncols, float alpha, cudaStream_t s);
+// the same with the one Bloch cell matrix B^e shared by every cell (k != 0)
+void bloch_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
+                    float *Y, int ldy, int ncols, float alpha, cudaStream_t s);
 // device status word of the instance: 0 when no bounded wait of a tensor-core
 // kernel expired since the last read, 1 when one did (read on the last stream,
 // then cleared); -1 when it cannot be read

@@ -255,6 +255,134 @@ __global__ void __launch_bounds__(NPAD * 32) k_own_couple_h(int npj, const int *
   if (v < ncols) WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * (double)w);
 }
 
+// ------------------------------------------------------------------ Bloch wavevector (k != 0)
+// Complex multivectors are split blocks [Re X | Im X] (nb = ncols / 2 columns
+// each) and the projectors C^{a,k} are stored as 2 np real projectors
+// [Re C | Im C].  A projection of the split block then holds, per atom and
+// complex column v, a = Re C^T Re x, b = Im C^T Re x (column v) and
+// c = Re C^T Im x, d = Im C^T Im x (column v + nb), so that
+// U = C^dagger x = (a + d) + i (c - b).  An expansion of coefficients W'
+// gives C W = (Re C Re W - Im C Im W) + i (Re C Im W + Im C Re W) when
+// W'[al] = Re W, W'[np + al] = -Im W (column v) and W'[al] = Im W,
+// W'[np + al] = Re W (column v + nb).
+template <typename T>
+__device__ __forceinline__ void cplx_u(const T *U, int npad, int ncols, int a, int np, int al, int v, int nb,
+                                       double &ur, double &ui) {
+  const size_t r0 = ((size_t)a * npad + al) * ncols, r1 = ((size_t)a * npad + np + al) * ncols;
+  ur = (double)U[r0 + v] + (double)U[r1 + v + nb];
+  ui = (double)U[r0 + v + nb] - (double)U[r1 + v];
+}
+
+template <typename T>
+__device__ __forceinline__ void cplx_w_store(T *W, int npad, int ncols, int a, int np, int al, int v, int nb,
+                                             double wr, double wi) {
+  const size_t r0 = ((size_t)a * npad + al) * ncols, r1 = ((size_t)a * npad + np + al) * ncols;
+  W[r0 + v] = (T)wr;
+  W[r1 + v] = (T)(-wi);
+  W[r0 + v + nb] = (T)wi;
+  W[r1 + v + nb] = (T)wr;
+}
+
+// W = coup_scale (C + cs[v] C2) U per atom and complex column: C complex
+// (interleaved re, im; cplxC = 1) or real, C2 real (may be NULL), C NULL:
+// identity.  Rows 2 np .. npad - 1 of W are zero.
+template <typename T, int NPAD>
+__global__ void k_couple_c(int np, const T *__restrict__ U, const double *__restrict__ C, int cplxC,
+                           const double *__restrict__ C2, const double *__restrict__ cs, double coup_scale,
+                           T *__restrict__ W, int ncols) {
+  const int a = blockIdx.x, nb = ncols / 2;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (v >= nb) return;
+  double ur[NPAD / 2], ui[NPAD / 2];
+#pragma unroll
+  for (int be = 0; be < NPAD / 2; ++be) {
+    ur[be] = ui[be] = 0.0;
+    if (be < np) cplx_u(U, NPAD, ncols, a, np, be, v, nb, ur[be], ui[be]);
+  }
+  const double sv = cs ? cs[v] : 0.0;
+  for (int al = 0; al < np; ++al) {
+    double wr = 0.0, wi = 0.0;
+    if (C) {
+#pragma unroll
+      for (int be = 0; be < NPAD / 2; ++be) {
+        if (be >= np) break;
+        double kr, ki;
+        if (cplxC) {
+          kr = C[2 * (((size_t)a * np + al) * np + be)];
+          ki = C[2 * (((size_t)a * np + al) * np + be) + 1];
+        } else {
+          kr = C[((size_t)a * np + al) * np + be] + (C2 ? sv * C2[((size_t)a * np + al) * np + be] : 0.0);
+          ki = 0.0;
+        }
+        wr += kr * ur[be] - ki * ui[be];
+        wi += kr * ui[be] + ki * ur[be];
+      }
+    } else {
+#pragma unroll
+      for (int be = 0; be < NPAD / 2; ++be)
+        if (be == al) {
+          wr = ur[be];
+          wi = ui[be];
+        }
+    }
+    cplx_w_store(W, NPAD, ncols, a, np, al, v, nb, coup_scale * wr, coup_scale * wi);
+  }
+  for (int j = 2 * np; j < NPAD; ++j) {
+    W[((size_t)a * NPAD + j) * ncols + v] = T(0);
+    W[((size_t)a * NPAD + j) * ncols + v + nb] = T(0);
+  }
+}
+
+// W_H = scale D_H (U - sum_b G_ab W_S[b]) with complex U, W_S and G_ab =
+// C^a^dagger M_D^-1 C^b (from the Gram block of the stored projectors:
+// (G_rr + G_ii) + i (G_ri - G_ir)); W_S in expansion form, W_H written in it.
+// Block = (atom, 32 complex columns), warp al = projector al.
+template <typename T, int NPAD>
+__global__ void __launch_bounds__(NPAD / 2 * 32) k_couple_h_c(int np, const int *__restrict__ goff,
+                                                              const int *__restrict__ gatom,
+                                                              const T *__restrict__ G, const T *__restrict__ U,
+                                                              const T *__restrict__ WS,
+                                                              const double *__restrict__ DH, double scale,
+                                                              T *__restrict__ WH, int ncols) {
+  __shared__ double tr_s[NPAD / 2][32], ti_s[NPAD / 2][32];
+  const int a = blockIdx.x, lane = threadIdx.x & 31, al = threadIdx.x >> 5, nb = ncols / 2;
+  const int v = blockIdx.y * 32 + lane;
+  const int vc = v < nb ? v : nb - 1;
+  double tr = 0.0, ti = 0.0;
+  if (al < np) {
+    cplx_u(U, NPAD, ncols, a, np, al, vc, nb, tr, ti);
+    for (int s = goff[a]; s < goff[a + 1]; ++s) {
+      const int b = gatom[s];
+      const T *Gs = G + (size_t)s * NPAD * NPAD;
+      for (int be = 0; be < np; ++be) {
+        const double gr = (double)Gs[al * NPAD + be] + (double)Gs[(np + al) * NPAD + np + be];
+        const double gi = (double)Gs[al * NPAD + np + be] - (double)Gs[(np + al) * NPAD + be];
+        const double wr = (double)WS[((size_t)b * NPAD + be) * ncols + vc];
+        const double wi = (double)WS[((size_t)b * NPAD + be) * ncols + vc + nb];
+        tr -= gr * wr - gi * wi;
+        ti -= gr * wi + gi * wr;
+      }
+    }
+    tr_s[al][lane] = tr;
+    ti_s[al][lane] = ti;
+  }
+  __syncthreads();
+  if (al < np && v < nb) {
+    double wr = 0.0, wi = 0.0;
+    const double *Da = DH + ((size_t)a * np + al) * np;
+    for (int be = 0; be < np; ++be) {
+      wr += Da[be] * tr_s[be][lane];
+      wi += Da[be] * ti_s[be][lane];
+    }
+    cplx_w_store(WH, NPAD, ncols, a, np, al, v, nb, scale * wr, scale * wi);
+  }
+  if (v < nb)
+    for (int j = 2 * np + al; j < NPAD; j += NPAD / 2) {
+      WH[((size_t)a * NPAD + j) * ncols + v] = T(0);
+      WH[((size_t)a * NPAD + j) * ncols + v + nb] = T(0);
+    }
+}
+
 // ------------------------------------------------------------------ expansion
 // FP32 SIMT form (the FP64 form is k_own_expand64 below).
 // Expansion with a fused output stage.  W of every pair of the cell is staged
@@ -620,7 +748,7 @@ static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T
     dim3 g1((ncols + VT - 1) / VT, c->ncells);
     const int xa = aligned16(X, ldx * sizeof(T)) ? 1 : 0;
     k_own_project<T, NPAD><<<g1, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_ngrp.as<int>(),
-                                                ownP<T>(c), X, ldx, ncols, rowscale, c->npj, U, xa);
+                                                ownP<T>(c), X, ldx, ncols, rowscale, c->npjr, U, xa);
     PAW_LAUNCH_CHECK("k_own_project");
   }
 }
@@ -662,6 +790,17 @@ static T *project_U(paw_context *c, paw_precision prec, const T *X, int ldx, int
 template <typename T>
 static void couple(paw_context *c, const T *U, const double *C, const double *C2, const double *cs,
                    double scale, T *W, int ncols, cudaStream_t s) {
+  if (c->kc) {   // complex coefficients: Delta_Sinv is complex, D_H and dS are real
+    PAW_REQUIRE(ncols % 2 == 0 && 2 * c->npj <= c->npad, PAW_ERR_UNSUPPORTED, "complex coupling layout");
+    const int cplxC = (C != nullptr && C == c->DSinv64.as<double>()) ? 1 : 0;
+    dim3 gc(c->natoms, (ncols / 2 + 63) / 64);
+    if (c->npad == 16)
+      k_couple_c<T, 16><<<gc, 64, 0, s>>>(c->npj, U, C, cplxC, C2, cs, scale, W, ncols);
+    else
+      k_couple_c<T, 32><<<gc, 64, 0, s>>>(c->npj, U, C, cplxC, C2, cs, scale, W, ncols);
+    PAW_LAUNCH_CHECK("k_couple_c");
+    return;
+  }
   dim3 g2(c->natoms, (ncols + 63) / 64);
   if (c->npad == 16)
     k_own_couple<T, 16><<<g2, 64, 0, s>>>(c->npj, U, C, C2, cs, scale, W, ncols);
@@ -699,6 +838,17 @@ void nl_project_filter(paw_context *c, paw_precision prec, const T *RY, int ldr,
   if (c->nown_pairs == 0 || ncols <= 0) return;
   const T *U = project_U<T>(c, prec, RY, ldr, ncols, mdinv, s);
   couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, WS, ncols, s);
+  if (c->kc) {
+    dim3 gc(c->natoms, (ncols / 2 + 31) / 32);
+    if (c->npad == 16)
+      k_couple_h_c<T, 16><<<gc, 8 * 32, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), gram<T>(c), U,
+                                                WS, c->DH64.as<double>(), alpha, WH, ncols);
+    else
+      k_couple_h_c<T, 32><<<gc, 16 * 32, 0, s>>>(c->npj, c->gnb_off.as<int>(), c->gnb_atom.as<int>(), gram<T>(c), U,
+                                                 WS, c->DH64.as<double>(), alpha, WH, ncols);
+    PAW_LAUNCH_CHECK("k_couple_h_c");
+    return;
+  }
   dim3 g2(c->natoms, (ncols + 31) / 32);
   const T *G = gram<T>(c);
   if (c->npad == 16)
@@ -912,6 +1062,7 @@ extern "C" paw_status paw_apply_Sinv_approx_noalloc(paw_handle c, paw_precision 
   using namespace pawfe;
   try {
     PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+    PAW_REQUIRE(!c->kc, PAW_ERR_UNSUPPORTED, "the allocation-free entry point has no Bloch-wavevector form");
     PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16, PAW_ERR_INVALID_ARG,
                 "unknown precision");
     PAW_REQUIRE(ncols >= 0, PAW_ERR_INVALID_ARG, "ncols < 0");

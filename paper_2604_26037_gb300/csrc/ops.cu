@@ -181,13 +181,30 @@ const float *MdInv<float>(paw_context *c) { return c->md_inv32.as<float>(); }
 template <typename T>
 void local_H(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols, double alpha,
              cudaStream_t s) {
+  // A = 1/2 K + V + 1/2 |k|^2 M on every column (the |k|^2 term is in H^e and in cM)
   if constexpr (sizeof(T) == 8) {
-    local_sf(c, X, ldx, Y, ldy, ncols, alpha, 1.0, 1.0, 0.0, nullptr, s);
+    local_sf(c, X, ldx, Y, ldy, ncols, alpha, 1.0, 1.0, c->kmass, nullptr, s);
   } else {
     if (prec == PAW_TF32 || prec == PAW_BF16)
       cell_apply_tc(c, prec, X, ldx, Y, ldy, ncols, (float)alpha, s);
     else
       cell_apply_simt<T>(c, HeMats<T>(c), (long long)c->nc * c->nc, X, ldx, Y, ldy, ncols, alpha, nullptr, s);
+  }
+  if (!c->kc) return;
+  // Bloch term of H_loc(k) = A - i B on the split block [Re | Im]:
+  // Y_re += alpha B X_im, Y_im -= alpha B X_re
+  const int nb = ncols / 2;
+  if constexpr (sizeof(T) == 8) {
+    bloch_sf(c, X + nb, ldx, Y, ldy, nb, alpha, s);
+    bloch_sf(c, X, ldx, Y + nb, ldy, nb, -alpha, s);
+  } else {
+    if (prec == PAW_TF32 || prec == PAW_BF16) {
+      bloch_apply_tc(c, prec, X + nb, ldx, Y, ldy, nb, (float)alpha, s);
+      bloch_apply_tc(c, prec, X, ldx, Y + nb, ldy, nb, -(float)alpha, s);
+    } else {
+      cell_apply_simt<T>(c, c->Bk32.as<T>(), 0, X + nb, ldx, Y, ldy, nb, alpha, nullptr, s);
+      cell_apply_simt<T>(c, c->Bk32.as<T>(), 0, X, ldx, Y + nb, ldy, nb, -alpha, nullptr, s);
+    }
   }
 }
 

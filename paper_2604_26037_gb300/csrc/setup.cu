@@ -124,6 +124,21 @@ void build_tables(paw_context *c) {
     }
   c->M1 = M1;
   c->D1 = D1;
+  // C1[a][b] = int l_a l_b' dxi (exact with p+1 Gauss points); its skew part is
+  // centro-antisymmetric and carries the k . grad term of Eq. hij
+  c->C1s.assign((size_t)np1 * np1, 0.0);
+  {
+    std::vector<double> C1((size_t)np1 * np1, 0.0);
+    for (int a = 0; a < np1; ++a)
+      for (int b = 0; b < np1; ++b) {
+        double acc = 0.0;
+        for (int q = 0; q < p + 1; ++q) acc += w1[q] * phi[(size_t)q * np1 + a] * dphi[(size_t)q * np1 + b];
+        C1[(size_t)a * np1 + b] = acc;
+      }
+    for (int a = 0; a < np1; ++a)
+      for (int b = 0; b < np1; ++b)
+        c->C1s[(size_t)a * np1 + b] = 0.5 * (C1[(size_t)a * np1 + b] - C1[(size_t)b * np1 + a]);
+  }
   const double hh = c->h / 2.0;
   c->K_ref.assign((size_t)nc * nc, 0.0);
   c->M_ref.assign((size_t)nc * nc, 0.0);
@@ -136,6 +151,30 @@ void build_tables(paw_context *c) {
       c->K_ref[(size_t)I * nc + J] = 0.5 * hh * (dx * my * mz + mx * dy * mz + mx * my * dz);
       c->M_ref[(size_t)I * nc + J] = hh * hh * hh * mx * my * mz;
     }
+  }
+  // Bloch cell matrix B^e = sum_d k_d G_d, G_x = (h/2)^2 C1s (x) M1 (x) M1 (and
+  // cyclic): the skew form of int N_I dN_J/dx_d per cell, whose assembly equals
+  // that of int N_I dN_J/dx_d on the periodic box (Eq. hij: H_loc(k) = A - i B)
+  if (c->kc) {
+    std::vector<double> B((size_t)nc * nc);
+    std::vector<float> Bf((size_t)nc * nc);
+    const double s2 = hh * hh;
+    const std::vector<double> &Cs = c->C1s;
+    for (int I = 0; I < nc; ++I) {
+      const int a = I % np1, b = (I / np1) % np1, cc = I / (np1 * np1);
+      for (int J = 0; J < nc; ++J) {
+        const int a2 = J % np1, b2 = (J / np1) % np1, c2 = J / (np1 * np1);
+        const double mx = M1[a * np1 + a2], my = M1[b * np1 + b2], mz = M1[cc * np1 + c2];
+        const double gx = Cs[a * np1 + a2] * my * mz, gy = mx * Cs[b * np1 + b2] * mz, gz = mx * my * Cs[cc * np1 + c2];
+        const double v = s2 * (c->kvec[0] * gx + c->kvec[1] * gy + c->kvec[2] * gz);
+        B[(size_t)I * nc + J] = v;
+        Bf[(size_t)I * nc + J] = (float)v;
+      }
+    }
+    c->Bk64.ensure(sizeof(double) * B.size(), &c->dev_bytes);
+    c->Bk32.ensure(sizeof(float) * Bf.size(), &c->dev_bytes);
+    PAW_CUDA(cudaMemcpy(c->Bk64.ptr, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice));
+    PAW_CUDA(cudaMemcpy(c->Bk32.ptr, Bf.data(), sizeof(float) * Bf.size(), cudaMemcpyHostToDevice));
   }
   // (p+2)-point rule: interpolation matrix node -> quadrature point and weights
   std::vector<double> g2, w2, phi2, dphi2;
@@ -228,8 +267,10 @@ __global__ void k_potential(int ncells, int n, int nq1, double h, double L, cons
   Vq[idx] = v;
 }
 
-// H^e[I][J] = K[I][J] + sum_q Nq[q][I] Nq[q][J] wq[q] V[e][q], tiles of 32 x 32
+// H^e[I][J] = K[I][J] + kmass Me[I][J] + sum_q Nq[q][I] Nq[q][J] wq[q] V[e][q], tiles of 32 x 32
+// (kmass = 1/2 |k|^2 at a Bloch wavevector k, Eq. hij)
 __global__ void __launch_bounds__(256) k_build_He(int nc, int nq, const double *__restrict__ K,
+                                                  const double *__restrict__ Me, double kmass,
                                                   const double *__restrict__ Nq,
                                                   const double *__restrict__ wq,
                                                   const double *__restrict__ Vq,
@@ -264,7 +305,7 @@ __global__ void __launch_bounds__(256) k_build_He(int nc, int nq, const double *
   for (int u = 0; u < 4; ++u) {
     const int I = I0 + ty * 4 + u;
     if (I < nc && J < nc) {
-      const double v = acc[u] + K[(size_t)I * nc + J];
+      const double v = acc[u] + K[(size_t)I * nc + J] + kmass * Me[(size_t)I * nc + J];
       He64[((size_t)e * nc + I) * nc + J] = v;
       if (He32) He32[((size_t)e * nc + I) * nc + J] = (float)v;
     }
@@ -313,7 +354,8 @@ __global__ void __launch_bounds__(256) k_projector_cells(
     int npairs, const int *__restrict__ pair_cell, const int *__restrict__ pair_atom,
     const int *__restrict__ pair_ent, int n, int nq1, int nc, int npj, double h, double L,
     const double *__restrict__ gq, const double *__restrict__ pos, ShellTable S,
-    const double *__restrict__ Nq, const double *__restrict__ wq, double *__restrict__ P) {
+    const double *__restrict__ Nq, const double *__restrict__ wq, double *__restrict__ P, int npjp, double kx,
+    double ky, double kz, int cplx) {
   extern __shared__ double pv[];   // [nq][npj]
   const int pr = blockIdx.x;
   const int e = pair_cell[pr], a = pair_atom[pr];
@@ -326,8 +368,20 @@ __global__ void __launch_bounds__(256) k_projector_cells(
     const double y = cy * h + (gq[j] + 1.0) * 0.5 * h;
     const double z = cz * h + (gq[k] + 1.0) * 0.5 * h;
     double vals[32];
-    projector_values(S, min_image(x - Rx, L), min_image(y - Ry, L), min_image(z - Rz, L), vals);
-    for (int al = 0; al < npj; ++al) pv[(size_t)q * npj + al] = vals[al] * wq[q];
+    const double dx = min_image(x - Rx, L), dy = min_image(y - Ry, L), dz = min_image(z - Rz, L);
+    projector_values(S, dx, dy, dz, vals);
+    if (cplx) {
+      // Bloch phase e^{-i k.(x - L_r)}, x - L_r = R_a + d (Eq. FEM Cmatrix): real and
+      // imaginary parts stored as projectors al and npjp + al
+      const double th = kx * (Rx + dx) + ky * (Ry + dy) + kz * (Rz + dz);
+      const double cr = cos(th), sn = sin(th);
+      for (int al = 0; al < npjp; ++al) {
+        pv[(size_t)q * npj + al] = vals[al] * wq[q] * cr;
+        pv[(size_t)q * npj + npjp + al] = -vals[al] * wq[q] * sn;
+      }
+    } else {
+      for (int al = 0; al < npj; ++al) pv[(size_t)q * npj + al] = vals[al] * wq[q];
+    }
   }
   __syncthreads();
   for (int o = threadIdx.x; o < nc * npj; o += blockDim.x) {
@@ -362,7 +416,7 @@ void rebuild_hamiltonian(paw_context *c) {
   c->He64.ensure(sizeof(double) * (size_t)c->ncells * nc * nc, &c->dev_bytes);
   c->He32.ensure(sizeof(float) * (size_t)c->ncells * nc * nc, &c->dev_bytes);
   dim3 grid((nc + 31) / 32, (nc + 31) / 32, c->ncells);
-  k_build_He<<<grid, 256>>>(nc, c->nq, c->K64.as<double>(), c->Nq64.as<double>(),
+  k_build_He<<<grid, 256>>>(nc, c->nq, c->K64.as<double>(), c->Me64.as<double>(), c->kmass, c->Nq64.as<double>(),
                             c->wq64.as<double>(), c->Vq.as<double>(), c->He64.as<double>(),
                             c->He32.as<float>());
   PAW_LAUNCH_CHECK("k_build_He");
@@ -403,7 +457,7 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
   rebuild_hamiltonian(c);
 
   // ---- projector supports
-  const int natoms = c->natoms, npj = c->npj, nc = c->nc;
+  const int natoms = c->natoms, npj = c->npjr, nc = c->nc;   // stored projectors (2 npj with k != 0)
   c->ent_off.assign(natoms + 1, 0);
   if (natoms == 0 || npj == 0) {
     c->nent = 0;
@@ -488,7 +542,7 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
     k_projector_cells<<<(unsigned)c->npairs, 256, shm>>>(
         (int)c->npairs, d_pc.as<int>(), d_pa.as<int>(), d_pe.as<int>(), c->n, c->nq1, nc, npj, c->h, c->L,
         d_gq.as<double>(), d_pos.as<double>(), S, c->Nq64.as<double>(), c->wq64.as<double>(),
-        c->P64.as<double>());
+        c->P64.as<double>(), c->npj, c->kvec[0], c->kvec[1], c->kvec[2], c->kc);
     PAW_LAUNCH_CHECK("k_projector_cells");
   }
   PAW_CUDA(cudaDeviceSynchronize());
@@ -685,11 +739,53 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
 }
 
 // Delta_Sinv^a = dS^a (I + G_a dS^a)^-1 and the positivity check of I + G^1/2 dS G^1/2.
+// Positivity check of I + G^1/2 dS G^1/2 (G symmetric positive semi-definite)
+// and Dsinv = dS (I + G dS)^-1 (Eq. Delta Sinv) for one atom, n x n row-major.
+static void dsinv_block(int n, const double *G, const double *dS, double *Dsinv, int atom) {
+  std::vector<double> Gm(G, G + (size_t)n * n), ev, V;
+  jacobi_eigh(n, Gm, ev, V);
+  std::vector<double> Gh((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += V[(size_t)i * n + k] * std::sqrt(std::max(ev[k], 0.0)) * V[(size_t)j * n + k];
+      Gh[(size_t)i * n + j] = s;
+    }
+  std::vector<double> Ms((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) s += Gh[(size_t)i * n + k] * dS[(size_t)k * n + l] * Gh[(size_t)l * n + j];
+      Ms[(size_t)i * n + j] = s;
+    }
+  std::vector<double> ev2, V2;
+  jacobi_eigh(n, Ms, ev2, V2);
+  PAW_REQUIRE(ev2[0] > 0.0, PAW_ERR_NOT_SPD,
+              "overlap block I + G^1/2 dS G^1/2 of atom " + std::to_string(atom) + " is not positive definite");
+  std::vector<double> A((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < n; ++k) s += G[(size_t)i * n + k] * dS[(size_t)k * n + j];
+      A[(size_t)i * n + j] = s;
+    }
+  PAW_REQUIRE(invert_small(n, A), PAW_ERR_NOT_SPD, "I + G dS is singular");
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += dS[(size_t)i * n + k] * A[(size_t)k * n + j];
+      Dsinv[(size_t)i * n + j] = s;
+    }
+}
+
 void build_couplings(paw_context *c) {
-  const int na = c->natoms, n = c->npj;
-  c->Dsinv.assign((size_t)na * n * n, 0.0);
+  const int na = c->natoms, n = c->npj, nr = c->npjr;
+  c->Dsinv.assign((size_t)na * n * n * (c->kc ? 2 : 1), 0.0);
+  std::vector<double> Gpp;
   if (c->opts.pp_overlap) {
-    // G_a = <p_al | p_be> for projectors on one centre (untruncated Gaussians)
+    // G_a = <p_al | p_be> for projectors on one centre (untruncated Gaussians;
+    // the Bloch phases of one centre cancel, so it stays real at k != 0)
     std::vector<int> ls, ms;
     std::vector<double> ws;
     for (size_t s = 0; s < c->shell_l.size(); ++s)
@@ -698,7 +794,7 @@ void build_couplings(paw_context *c) {
         ms.push_back(m);
         ws.push_back(c->shell_w[s]);
       }
-    std::vector<double> Gpp((size_t)n * n, 0.0);
+    Gpp.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j)
         if (ls[i] == ls[j] && ms[i] == ms[j]) {
@@ -708,53 +804,51 @@ void build_couplings(paw_context *c) {
           Gpp[(size_t)i * n + j] = radial_norm(l, w1) * radial_norm(l, w2) * 0.5 *
                                    std::tgamma(l + 1.5) * std::pow(we2, l + 1.5);
         }
-    for (int a = 0; a < na; ++a) std::copy(Gpp.begin(), Gpp.end(), c->G.begin() + (size_t)a * n * n);
+    if (!c->kc)
+      for (int a = 0; a < na; ++a) std::copy(Gpp.begin(), Gpp.end(), c->G.begin() + (size_t)a * n * n);
   }
   for (int a = 0; a < na; ++a) {
-    const double *G = c->G.data() + (size_t)a * n * n;
     const double *dS = c->dS.data() + (size_t)a * n * n;
-    // positivity: eigenvalues of I + G^1/2 dS G^1/2 (G is SPD)
-    std::vector<double> Gm(G, G + (size_t)n * n), ev, V;
-    jacobi_eigh(n, Gm, ev, V);
-    std::vector<double> Gh((size_t)n * n, 0.0);
+    if (!c->kc) {
+      const double *G = c->opts.pp_overlap ? Gpp.data() : c->G.data() + (size_t)a * n * n;
+      dsinv_block(n, G, dS, c->Dsinv.data() + (size_t)a * n * n, a);
+      continue;
+    }
+    // k != 0: the Gram matrix of the stored projectors [Re C | Im C] gives the
+    // complex G_a = C^dagger M_D^-1 C = (G_rr + G_ii) + i (G_ri - G_ir); the
+    // Hermitian algebra runs on the real 2n x 2n forms [[Re, -Im], [Im, Re]]
+    // (sums, products and inverses map to the same forms; eigenvalues double)
+    const int n2 = 2 * n;
+    std::vector<double> Gc((size_t)n2 * n2, 0.0), dS2((size_t)n2 * n2, 0.0), D2((size_t)n2 * n2, 0.0);
+    const double *Gs = c->G.data() + (size_t)a * nr * nr;
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) s += V[(size_t)i * n + k] * std::sqrt(std::max(ev[k], 0.0)) * V[(size_t)j * n + k];
-        Gh[(size_t)i * n + j] = s;
+        double gr, gi;
+        if (c->opts.pp_overlap) {
+          gr = Gpp[(size_t)i * n + j];
+          gi = 0.0;
+        } else {
+          gr = Gs[(size_t)i * nr + j] + Gs[(size_t)(n + i) * nr + n + j];
+          gi = Gs[(size_t)i * nr + n + j] - Gs[(size_t)(n + i) * nr + j];
+        }
+        Gc[(size_t)i * n2 + j] = gr;
+        Gc[(size_t)(n + i) * n2 + n + j] = gr;
+        Gc[(size_t)i * n2 + n + j] = -gi;
+        Gc[(size_t)(n + i) * n2 + j] = gi;
+        dS2[(size_t)i * n2 + j] = dS2[(size_t)(n + i) * n2 + n + j] = dS[(size_t)i * n + j];
       }
-    std::vector<double> Ms((size_t)n * n, 0.0);
+    dsinv_block(n2, Gc.data(), dS2.data(), D2.data(), a);
+    double *out = c->Dsinv.data() + (size_t)a * n * n * 2;   // interleaved (re, im)
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int k = 0; k < n; ++k)
-          for (int l = 0; l < n; ++l) s += Gh[(size_t)i * n + k] * dS[(size_t)k * n + l] * Gh[(size_t)l * n + j];
-        Ms[(size_t)i * n + j] = s;
-      }
-    std::vector<double> ev2, V2;
-    jacobi_eigh(n, Ms, ev2, V2);
-    PAW_REQUIRE(ev2[0] > 0.0, PAW_ERR_NOT_SPD,
-                "overlap block I + G^1/2 dS G^1/2 of atom " + std::to_string(a) + " is not positive definite");
-    // Dsinv = dS (I + G dS)^-1
-    std::vector<double> A((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int k = 0; k < n; ++k) s += G[(size_t)i * n + k] * dS[(size_t)k * n + j];
-        A[(size_t)i * n + j] = s;
-      }
-    PAW_REQUIRE(invert_small(n, A), PAW_ERR_NOT_SPD, "I + G dS is singular");
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) s += dS[(size_t)i * n + k] * A[(size_t)k * n + j];
-        c->Dsinv[((size_t)a * n + i) * n + j] = s;
+        out[2 * ((size_t)i * n + j)] = D2[(size_t)i * n2 + j];
+        out[2 * ((size_t)i * n + j) + 1] = D2[(size_t)(n + i) * n2 + j];
       }
   }
   const size_t bytes = sizeof(double) * std::max<size_t>(1, (size_t)na * n * n);
   c->DH64.ensure(bytes, &c->dev_bytes);
   c->DS64.ensure(bytes, &c->dev_bytes);
-  c->DSinv64.ensure(bytes, &c->dev_bytes);
+  c->DSinv64.ensure(bytes * (c->kc ? 2 : 1), &c->dev_bytes);
   if (na * n > 0) {
     PAW_CUDA(cudaMemcpy(c->DH64.ptr, c->D.data(), sizeof(double) * c->D.size(), cudaMemcpyHostToDevice));
     PAW_CUDA(cudaMemcpy(c->DS64.ptr, c->dS.data(), sizeof(double) * c->dS.size(), cudaMemcpyHostToDevice));

@@ -271,6 +271,113 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
   }
 }
 
+// Bloch term at a wavevector k: y = (h/2)^2 [k_x C (x) M (x) M + k_y M (x) C (x) M
+// + k_z M (x) M (x) C] x per cell (C = the skew 1D matrix (C1 - C1^T)/2,
+// C1[a][b] = int l_a l_b' dxi; M the 1D reference mass), accumulated into
+// Y with factor alpha.  Same chain of 1D contractions as the kinetic part of
+// k_local_sf (z, then y, then x), full 1D matrices.
+struct BlochTables {
+  double M[10 * 10], C[10 * 10];
+  double kx, ky, kz, scale;
+};
+
+template <int NP>
+__device__ __forceinline__ void line_mat(const double *A, const double *x, int s, double (&out)[NP]) {
+  double xv[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) xv[j] = x[j * s];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc = fma(A[i * NP + j], xv[j], acc);
+    out[i] = acc;
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(SF_THREADS, 1) k_bloch_sf(BlochTables tab, const int *__restrict__ cell_dofs,
+                                                        const double *__restrict__ X, int ldx,
+                                                        double *__restrict__ Y, int ldy, int ncols, double alpha) {
+  constexpr int VT = sf_vt<NP>();
+  constexpr int N3 = NP * NP * NP;
+  __shared__ BlochTables st;
+  __shared__ int dofs[N3];
+  extern __shared__ double sm[];
+  double *A0 = sm;               // x, then T
+  double *A1 = A0 + N3 * VT;     // P, then y
+  double *A2 = A1 + N3 * VT;     // Q
+  double *A3 = A2 + N3 * VT;     // S
+  const int e = blockIdx.x, v0 = blockIdx.y * VT, tid = threadIdx.x;
+  {
+    const double *src = reinterpret_cast<const double *>(&tab);
+    double *dst = reinterpret_cast<double *>(&st);
+    for (int i = tid; i < (int)(sizeof(BlochTables) / sizeof(double)); i += SF_THREADS) dst[i] = src[i];
+  }
+  for (int i = tid; i < N3; i += SF_THREADS) dofs[i] = cell_dofs[(size_t)e * N3 + i];
+  __syncthreads();
+  for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
+    const int r = idx / VT, v = idx - r * VT;
+    A0[idx] = (v0 + v < ncols) ? X[(size_t)dofs[r] * ldx + v0 + v] : 0.0;
+  }
+  __syncthreads();
+  // z lines: P = M_c x, Q = C_c x
+  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+    const int ab = idx / VT, v = idx - ab * VT;
+    double P[NP], Q[NP];
+    line_mat<NP>(st.M, A0 + ab * VT + v, NP * NP * VT, P);
+    line_mat<NP>(st.C, A0 + ab * VT + v, NP * NP * VT, Q);
+#pragma unroll
+    for (int c2 = 0; c2 < NP; ++c2) {
+      A1[(c2 * NP * NP + ab) * VT + v] = P[c2];
+      A2[(c2 * NP * NP + ab) * VT + v] = Q[c2];
+    }
+  }
+  __syncthreads();
+  // y lines: S = M_b P, T = k_y C_b P + k_z M_b Q
+  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+    const int ac = idx / VT, v = idx - ac * VT;
+    const int a = ac % NP, c = ac / NP;
+    const int base = (c * NP * NP + a) * VT + v;
+    double S[NP], T1[NP], T2[NP];
+    line_mat<NP>(st.M, A1 + base, NP * VT, S);
+    line_mat<NP>(st.C, A1 + base, NP * VT, T1);
+    line_mat<NP>(st.M, A2 + base, NP * VT, T2);
+#pragma unroll
+    for (int b2 = 0; b2 < NP; ++b2) {
+      A3[base + b2 * NP * VT] = S[b2];
+      A0[base + b2 * NP * VT] = fma(st.ky, T1[b2], st.kz * T2[b2]);
+    }
+  }
+  __syncthreads();
+  // x lines: y = k_x C_a S + M_a T
+  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+    const int bc = idx / VT, v = idx - bc * VT;
+    const int base = bc * NP * VT + v;
+    double Y1[NP], Y2[NP];
+    line_mat<NP>(st.C, A3 + base, VT, Y1);
+    line_mat<NP>(st.M, A0 + base, VT, Y2);
+#pragma unroll
+    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = st.scale * fma(st.kx, Y1[a2], Y2[a2]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
+    const int r = idx / VT, v = idx - r * VT;
+    if (v0 + v < ncols) atomicAdd(&Y[(size_t)dofs[r] * ldy + v0 + v], alpha * A1[idx]);
+  }
+}
+
+template <int NP>
+void launch_bloch(paw_context *c, const BlochTables &t, const double *X, int ldx, double *Y, int ldy, int ncols,
+                  double alpha, cudaStream_t s) {
+  constexpr int VT = sf_vt<NP>();
+  const size_t shm = sizeof(double) * 4 * (size_t)NP * NP * NP * VT;
+  PAW_CUDA(cudaFuncSetAttribute(k_bloch_sf<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  dim3 g(c->ncells, (ncols + VT - 1) / VT);
+  k_bloch_sf<NP><<<g, SF_THREADS, shm, s>>>(t, c->cell_dofs.as<int>(), X, ldx, Y, ldy, ncols, alpha);
+  PAW_LAUNCH_CHECK("k_bloch_sf");
+}
+
 template <int NP>
 size_t sf_smem() {
   constexpr int NQ = NP + 1;
@@ -312,6 +419,33 @@ static void eo_halves(const double *A, int m, int n, EoMat &out) {
   for (int i = 0; i < m / 2; ++i)
     for (int j = 0; j < no; ++j)
       out.o[i * no + j] = 0.5 * (A[(size_t)i * n + j] - A[(size_t)i * n + (n - 1 - j)]);
+}
+
+void bloch_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
+              cudaStream_t s) {
+  if (ncols <= 0 || !c->kc) return;
+  const int np1 = c->np1;
+  PAW_REQUIRE(np1 <= 10, PAW_ERR_UNSUPPORTED, "degree out of range for the Bloch kernel");
+  BlochTables t{};
+  for (int i = 0; i < np1 * np1; ++i) {
+    t.M[i] = c->M1[i];
+    t.C[i] = c->C1s[i];
+  }
+  t.kx = c->kvec[0];
+  t.ky = c->kvec[1];
+  t.kz = c->kvec[2];
+  t.scale = (c->h / 2.0) * (c->h / 2.0);
+  switch (np1) {
+    case 2: launch_bloch<2>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 3: launch_bloch<3>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 4: launch_bloch<4>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 5: launch_bloch<5>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 6: launch_bloch<6>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 7: launch_bloch<7>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 8: launch_bloch<8>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    case 9: launch_bloch<9>(c, t, X, ldx, Y, ldy, ncols, alpha, s); break;
+    default: throw Error{PAW_ERR_UNSUPPORTED, "degree out of range for the Bloch kernel"};
+  }
 }
 
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha, double cK,
