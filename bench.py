@@ -169,10 +169,12 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     cfg = inputs.CONFIGS[args.workload]
     sysd = inputs.make_system(args.workload)
-    fe = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32)
+    kp = tuple(args.kpoint) if args.kpoint else None
+    fe = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, kpoint=kp)
     M, N, m = fe.ndof, cfg["nvec"], cfg["degree"]
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
-    X = torch.randn((M, N), dtype=torch.float64, device="cuda", generator=g)
+    # at a Bloch wavevector k the vectors are complex (one complex vector = one vector of the metric)
+    X = torch.randn((M, N), dtype=torch.complex128 if fe.complex else torch.float64, device="cuda", generator=g)
     tmin, bU = fe.lanczos_bounds(20, 7)
     if args.start == "ritz":
         lam = fe.rayleigh_ritz(X)                   # S-orthonormal Ritz vectors of the random block
@@ -238,7 +240,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
         e2e = {"value": units_per_step * ws / t_e2e / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(Xh.numel() * 8 + N * 8), "d2h_bytes_per_step": int(Oh.numel() * 8)}
+               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + N * 8),
+               "d2h_bytes_per_step": int(Oh.numel() * Oh.element_size())}
 
     # Rayleigh-Ritz on the filtered block: FP64 rotation vs the mixed-precision one (rr_mixed)
     rrm = None
@@ -318,6 +321,8 @@ def run_ours(args, ws, rank, local):
                                f"M={M} DoFs, {sysd['natoms']} atoms x {sysd['nproj']} projectors, "
                                f"N={N} in blocks of {cfg['block']}, degree {m}",
                    "precision": args.prec, "y0_storage": "fp32" if args.y0_fp32 else "fp64",
+                   **({"kpoint_per_bohr": list(kp), "vectors": "complex (real blocks of 2 B columns inside)"}
+                      if kp else {}),
                    "start": args.start,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
         "gpu_launches": int(launches),
@@ -407,8 +412,13 @@ def sf_flops_per_cell_vec(n1):
 
 
 def phase_model(phase, fe, cfg, prec):
-    """Algorithmic (flops, bytes, compute kind) of one launch of a phase for one block."""
-    M, B = fe.ndof, cfg["block"]
+    """Algorithmic (flops, bytes, compute kind) of one launch of a phase for one block.
+
+    At a Bloch wavevector k a block of B complex vectors is processed as 2 B real
+    columns; the extra cell products of the -i k.grad term (a shared cell matrix)
+    are not in this model.
+    """
+    M, B = fe.ndof, cfg["block"] * (2 if fe.complex else 1)
     nc, ncells = fe.nodes_per_cell, fe.ncells
     n1 = fe_np1(nc)
     # algorithmic projector work: the nonzero entries of P^a on owned nodes
@@ -457,7 +467,8 @@ def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks, workload=None):
                 "traffic": None, "kernel": phase}
     sec = per_launch_ms / 1e3
     gbs = byts / sec / 1e9
-    traffic, tnote = measured_traffic(phase, prec, float(fe.ndof) * cfg["block"], workload)
+    traffic, tnote = (measured_traffic(phase, prec, float(fe.ndof) * cfg["block"], workload)
+                      if not fe.complex else (None, None))
     tfs = flops / sec / 1e12
     hbm_frac = gbs / peaks["hbm"]
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -600,6 +611,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--y0-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kpoint", type=float, nargs=3, default=None,
+                    help="Bloch wavevector k (1/bohr): complex vectors, throughput per complex vector")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grad", action="store_true",
                     help="also time the adjoint (gradient of tr(X^T H X)) at the filtered block, with checks")
@@ -620,7 +633,7 @@ def main():
         res = run_batch(args, ws, rank, local)
     else:
         res = run_ours(args, ws, rank, local)
-        if rank == 0 and not args.no_cpu_baseline:
+        if rank == 0 and not args.no_cpu_baseline and not args.kpoint:
             res["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)

@@ -257,30 +257,32 @@ __global__ void __launch_bounds__(NPAD * 32) k_own_couple_h(int npj, const int *
 
 // ------------------------------------------------------------------ Bloch wavevector (k != 0)
 // Complex multivectors are split blocks [Re X | Im X] (nb = ncols / 2 columns
-// each) and the projectors C^{a,k} are stored as 2 np real projectors
-// [Re C | Im C].  A projection of the split block then holds, per atom and
-// complex column v, a = Re C^T Re x, b = Im C^T Re x (column v) and
-// c = Re C^T Im x, d = Im C^T Im x (column v + nb), so that
+// each) and the projectors C^{a,k} are stored as 2 np real projectors,
+// Re C_al at 2 al and Im C_al at 2 al + 1.  A projection of the split block then
+// holds, per atom and complex column v, a = Re C^T Re x, b = Im C^T Re x
+// (column v) and c = Re C^T Im x, d = Im C^T Im x (column v + nb), so that
 // U = C^dagger x = (a + d) + i (c - b).  An expansion of coefficients W'
 // gives C W = (Re C Re W - Im C Im W) + i (Re C Im W + Im C Re W) when
-// W'[al] = Re W, W'[np + al] = -Im W (column v) and W'[al] = Im W,
-// W'[np + al] = Re W (column v + nb).
+// W'[2 al] = Re W, W'[2 al + 1] = -Im W (column v) and W'[2 al] = Im W,
+// W'[2 al + 1] = Re W (column v + nb).
+// (arithmetic in T, as in the real coupling kernels: FP32 for the FP32 / TF32 /
+// BF16 filter)
 template <typename T>
 __device__ __forceinline__ void cplx_u(const T *U, int npad, int ncols, int a, int np, int al, int v, int nb,
-                                       double &ur, double &ui) {
-  const size_t r0 = ((size_t)a * npad + al) * ncols, r1 = ((size_t)a * npad + np + al) * ncols;
-  ur = (double)U[r0 + v] + (double)U[r1 + v + nb];
-  ui = (double)U[r0 + v + nb] - (double)U[r1 + v];
+                                       T &ur, T &ui) {
+  const size_t r0 = ((size_t)a * npad + 2 * al) * ncols, r1 = r0 + ncols;
+  ur = U[r0 + v] + U[r1 + v + nb];
+  ui = U[r0 + v + nb] - U[r1 + v];
 }
 
 template <typename T>
-__device__ __forceinline__ void cplx_w_store(T *W, int npad, int ncols, int a, int np, int al, int v, int nb,
-                                             double wr, double wi) {
-  const size_t r0 = ((size_t)a * npad + al) * ncols, r1 = ((size_t)a * npad + np + al) * ncols;
-  W[r0 + v] = (T)wr;
-  W[r1 + v] = (T)(-wi);
-  W[r0 + v + nb] = (T)wi;
-  W[r1 + v + nb] = (T)wr;
+__device__ __forceinline__ void cplx_w_store(T *W, int npad, int ncols, int a, int np, int al, int v, int nb, T wr,
+                                             T wi) {
+  const size_t r0 = ((size_t)a * npad + 2 * al) * ncols, r1 = r0 + ncols;
+  W[r0 + v] = wr;
+  W[r1 + v] = -wi;
+  W[r0 + v + nb] = wi;
+  W[r1 + v + nb] = wr;
 }
 
 // W = coup_scale (C + cs[v] C2) U per atom and complex column: C complex
@@ -293,26 +295,26 @@ __global__ void k_couple_c(int np, const T *__restrict__ U, const double *__rest
   const int a = blockIdx.x, nb = ncols / 2;
   const int v = blockIdx.y * blockDim.x + threadIdx.x;
   if (v >= nb) return;
-  double ur[NPAD / 2], ui[NPAD / 2];
+  T ur[NPAD / 2], ui[NPAD / 2];
 #pragma unroll
   for (int be = 0; be < NPAD / 2; ++be) {
-    ur[be] = ui[be] = 0.0;
+    ur[be] = ui[be] = T(0);
     if (be < np) cplx_u(U, NPAD, ncols, a, np, be, v, nb, ur[be], ui[be]);
   }
   const double sv = cs ? cs[v] : 0.0;
   for (int al = 0; al < np; ++al) {
-    double wr = 0.0, wi = 0.0;
+    T wr = T(0), wi = T(0);
     if (C) {
 #pragma unroll
       for (int be = 0; be < NPAD / 2; ++be) {
         if (be >= np) break;
-        double kr, ki;
+        T kr, ki;
         if (cplxC) {
-          kr = C[2 * (((size_t)a * np + al) * np + be)];
-          ki = C[2 * (((size_t)a * np + al) * np + be) + 1];
+          kr = (T)C[2 * (((size_t)a * np + al) * np + be)];
+          ki = (T)C[2 * (((size_t)a * np + al) * np + be) + 1];
         } else {
-          kr = C[((size_t)a * np + al) * np + be] + (C2 ? sv * C2[((size_t)a * np + al) * np + be] : 0.0);
-          ki = 0.0;
+          kr = (T)(C[((size_t)a * np + al) * np + be] + (C2 ? sv * C2[((size_t)a * np + al) * np + be] : 0.0));
+          ki = T(0);
         }
         wr += kr * ur[be] - ki * ui[be];
         wi += kr * ui[be] + ki * ur[be];
@@ -325,7 +327,7 @@ __global__ void k_couple_c(int np, const T *__restrict__ U, const double *__rest
           wi = ui[be];
         }
     }
-    cplx_w_store(W, NPAD, ncols, a, np, al, v, nb, coup_scale * wr, coup_scale * wi);
+    cplx_w_store(W, NPAD, ncols, a, np, al, v, nb, (T)(coup_scale * (double)wr), (T)(coup_scale * (double)wi));
   }
   for (int j = 2 * np; j < NPAD; ++j) {
     W[((size_t)a * NPAD + j) * ncols + v] = T(0);
@@ -334,8 +336,9 @@ __global__ void k_couple_c(int np, const T *__restrict__ U, const double *__rest
 }
 
 // W_H = scale D_H (U - sum_b G_ab W_S[b]) with complex U, W_S and G_ab =
-// C^a^dagger M_D^-1 C^b (from the Gram block of the stored projectors:
-// (G_rr + G_ii) + i (G_ri - G_ir)); W_S in expansion form, W_H written in it.
+// C^a^dagger M_D^-1 C^b (from the Gram block of the stored projectors, rows and
+// columns 2 al (real part) and 2 al + 1 (imaginary part): (G_rr + G_ii) +
+// i (G_ri - G_ir)); W_S in expansion form, W_H written in it.
 // Block = (atom, 32 complex columns), warp al = projector al.
 template <typename T, int NPAD>
 __global__ void __launch_bounds__(NPAD / 2 * 32) k_couple_h_c(int np, const int *__restrict__ goff,
@@ -344,21 +347,22 @@ __global__ void __launch_bounds__(NPAD / 2 * 32) k_couple_h_c(int np, const int 
                                                               const T *__restrict__ WS,
                                                               const double *__restrict__ DH, double scale,
                                                               T *__restrict__ WH, int ncols) {
-  __shared__ double tr_s[NPAD / 2][32], ti_s[NPAD / 2][32];
+  __shared__ T tr_s[NPAD / 2][32], ti_s[NPAD / 2][32];
   const int a = blockIdx.x, lane = threadIdx.x & 31, al = threadIdx.x >> 5, nb = ncols / 2;
   const int v = blockIdx.y * 32 + lane;
   const int vc = v < nb ? v : nb - 1;
-  double tr = 0.0, ti = 0.0;
+  T tr = T(0), ti = T(0);
   if (al < np) {
     cplx_u(U, NPAD, ncols, a, np, al, vc, nb, tr, ti);
     for (int s = goff[a]; s < goff[a + 1]; ++s) {
       const int b = gatom[s];
       const T *Gs = G + (size_t)s * NPAD * NPAD;
+      const T *wb = WS + (size_t)b * NPAD * ncols + vc;
+      const T *g0 = Gs + (2 * al) * NPAD, *g1 = g0 + NPAD;
       for (int be = 0; be < np; ++be) {
-        const double gr = (double)Gs[al * NPAD + be] + (double)Gs[(np + al) * NPAD + np + be];
-        const double gi = (double)Gs[al * NPAD + np + be] - (double)Gs[(np + al) * NPAD + be];
-        const double wr = (double)WS[((size_t)b * NPAD + be) * ncols + vc];
-        const double wi = (double)WS[((size_t)b * NPAD + be) * ncols + vc + nb];
+        const T gr = g0[2 * be] + g1[2 * be + 1];
+        const T gi = g0[2 * be + 1] - g1[2 * be];
+        const T wr = wb[(size_t)(2 * be) * ncols], wi = wb[(size_t)(2 * be) * ncols + nb];
         tr -= gr * wr - gi * wi;
         ti -= gr * wi + gi * wr;
       }
@@ -368,13 +372,13 @@ __global__ void __launch_bounds__(NPAD / 2 * 32) k_couple_h_c(int np, const int 
   }
   __syncthreads();
   if (al < np && v < nb) {
-    double wr = 0.0, wi = 0.0;
+    T wr = T(0), wi = T(0);
     const double *Da = DH + ((size_t)a * np + al) * np;
     for (int be = 0; be < np; ++be) {
-      wr += Da[be] * tr_s[be][lane];
-      wi += Da[be] * ti_s[be][lane];
+      wr = fma(T(Da[be]), tr_s[be][lane], wr);
+      wi = fma(T(Da[be]), ti_s[be][lane], wi);
     }
-    cplx_w_store(WH, NPAD, ncols, a, np, al, v, nb, scale * wr, scale * wi);
+    cplx_w_store(WH, NPAD, ncols, a, np, al, v, nb, (T)(scale * (double)wr), (T)(scale * (double)wi));
   }
   if (v < nb)
     for (int j = 2 * np + al; j < NPAD; j += NPAD / 2) {

@@ -372,12 +372,13 @@ __global__ void __launch_bounds__(256) k_projector_cells(
     projector_values(S, dx, dy, dz, vals);
     if (cplx) {
       // Bloch phase e^{-i k.(x - L_r)}, x - L_r = R_a + d (Eq. FEM Cmatrix): real and
-      // imaginary parts stored as projectors al and npjp + al
+      // imaginary parts stored as projectors 2 al and 2 al + 1 (so that the stored
+      // projectors keep the order of decreasing width in pairs)
       const double th = kx * (Rx + dx) + ky * (Ry + dy) + kz * (Rz + dz);
       const double cr = cos(th), sn = sin(th);
       for (int al = 0; al < npjp; ++al) {
-        pv[(size_t)q * npj + al] = vals[al] * wq[q] * cr;
-        pv[(size_t)q * npj + npjp + al] = -vals[al] * wq[q] * sn;
+        pv[(size_t)q * npj + 2 * al] = vals[al] * wq[q] * cr;
+        pv[(size_t)q * npj + 2 * al + 1] = -vals[al] * wq[q] * sn;
       }
     } else {
       for (int al = 0; al < npj; ++al) pv[(size_t)q * npj + al] = vals[al] * wq[q];
@@ -814,8 +815,8 @@ void build_couplings(paw_context *c) {
       dsinv_block(n, G, dS, c->Dsinv.data() + (size_t)a * n * n, a);
       continue;
     }
-    // k != 0: the Gram matrix of the stored projectors [Re C | Im C] gives the
-    // complex G_a = C^dagger M_D^-1 C = (G_rr + G_ii) + i (G_ri - G_ir); the
+    // k != 0: the Gram matrix of the stored projectors (Re C_al, Im C_al at 2 al,
+    // 2 al + 1) gives G_a = C^dagger M_D^-1 C = (G_rr + G_ii) + i (G_ri - G_ir); the
     // Hermitian algebra runs on the real 2n x 2n forms [[Re, -Im], [Im, Re]]
     // (sums, products and inverses map to the same forms; eigenvalues double)
     const int n2 = 2 * n;
@@ -828,8 +829,8 @@ void build_couplings(paw_context *c) {
           gr = Gpp[(size_t)i * n + j];
           gi = 0.0;
         } else {
-          gr = Gs[(size_t)i * nr + j] + Gs[(size_t)(n + i) * nr + n + j];
-          gi = Gs[(size_t)i * nr + n + j] - Gs[(size_t)(n + i) * nr + j];
+          gr = Gs[(size_t)(2 * i) * nr + 2 * j] + Gs[(size_t)(2 * i + 1) * nr + 2 * j + 1];
+          gi = Gs[(size_t)(2 * i) * nr + 2 * j + 1] - Gs[(size_t)(2 * i + 1) * nr + 2 * j];
         }
         Gc[(size_t)i * n2 + j] = gr;
         Gc[(size_t)(n + i) * n2 + n + j] = gr;
