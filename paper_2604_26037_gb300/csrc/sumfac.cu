@@ -275,24 +275,28 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
 // + k_z M (x) M (x) C] x per cell (C = the skew 1D matrix (C1 - C1^T)/2,
 // C1[a][b] = int l_a l_b' dxi; M the 1D reference mass), accumulated into
 // Y with factor alpha.  Same chain of 1D contractions as the kinetic part of
-// k_local_sf (z, then y, then x), full 1D matrices.
+// k_local_sf (z, then y, then x), in the even/odd split: M is centro-symmetric,
+// C centro-antisymmetric (C[n-1-i][n-1-j] = -C[i][j]), which maps the odd part
+// of a line to the even part of the result and the even part to the odd one.
 struct BlochTables {
-  double M[10 * 10], C[10 * 10];
+  EoMat M, C;   // C: halves of the antisymmetric form (eo_acc_anti)
   double kx, ky, kz, scale;
 };
 
-template <int NP>
-__device__ __forceinline__ void line_mat(const double *A, const double *x, int s, double (&out)[NP]) {
-  double xv[NP];
+// E[i] += sum_j Ae[i][j] o[j] (i < ceil(M/2), j < N/2),  O[i] += sum_j Ao[i][j] e[j]
+// (i < M/2, j < ceil(N/2)) for a centro-antisymmetric M x N matrix
+template <int M, int N>
+__device__ __forceinline__ void eo_acc_anti(const EoMat &A, const Split<N> &x, double (&E)[(M + 1) / 2],
+                                            double (&O)[M / 2 > 0 ? M / 2 : 1]) {
+  constexpr int NE = (N + 1) / 2, NO = N / 2;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) xv[j] = x[j * s];
+  for (int i = 0; i < (M + 1) / 2; ++i)
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    double acc = 0.0;
+    for (int j = 0; j < NO; ++j) E[i] = fma(A.e[i * NO + j], x.o[j], E[i]);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc = fma(A[i * NP + j], xv[j], acc);
-    out[i] = acc;
-  }
+  for (int i = 0; i < M / 2; ++i)
+#pragma unroll
+    for (int j = 0; j < NE; ++j) O[i] = fma(A.o[i * NE + j], x.e[j], O[i]);
 }
 
 template <int NP>
@@ -324,13 +328,16 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_bloch_sf(BlochTables tab, con
   // z lines: P = M_c x, Q = C_c x
   for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int ab = idx / VT, v = idx - ab * VT;
-    double P[NP], Q[NP];
-    line_mat<NP>(st.M, A0 + ab * VT + v, NP * NP * VT, P);
-    line_mat<NP>(st.C, A0 + ab * VT + v, NP * NP * VT, Q);
+    const Split<NP> x = split_line<NP>(A0 + ab * VT + v, NP * NP * VT);
+    Half<NP> P, Q;
+    P.zero();
+    Q.zero();
+    eo_acc<NP, NP>(st.M, x, P.E, P.O);
+    eo_acc_anti<NP, NP>(st.C, x, Q.E, Q.O);
 #pragma unroll
     for (int c2 = 0; c2 < NP; ++c2) {
-      A1[(c2 * NP * NP + ab) * VT + v] = P[c2];
-      A2[(c2 * NP * NP + ab) * VT + v] = Q[c2];
+      A1[(c2 * NP * NP + ab) * VT + v] = P.out(c2);
+      A2[(c2 * NP * NP + ab) * VT + v] = Q.out(c2);
     }
   }
   __syncthreads();
@@ -339,14 +346,19 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_bloch_sf(BlochTables tab, con
     const int ac = idx / VT, v = idx - ac * VT;
     const int a = ac % NP, c = ac / NP;
     const int base = (c * NP * NP + a) * VT + v;
-    double S[NP], T1[NP], T2[NP];
-    line_mat<NP>(st.M, A1 + base, NP * VT, S);
-    line_mat<NP>(st.C, A1 + base, NP * VT, T1);
-    line_mat<NP>(st.M, A2 + base, NP * VT, T2);
+    const Split<NP> pl = split_line<NP>(A1 + base, NP * VT);
+    const Split<NP> ql = split_line<NP>(A2 + base, NP * VT);
+    Half<NP> S, T1, T2;
+    S.zero();
+    T1.zero();
+    T2.zero();
+    eo_acc<NP, NP>(st.M, pl, S.E, S.O);
+    eo_acc_anti<NP, NP>(st.C, pl, T1.E, T1.O);
+    eo_acc<NP, NP>(st.M, ql, T2.E, T2.O);
 #pragma unroll
     for (int b2 = 0; b2 < NP; ++b2) {
-      A3[base + b2 * NP * VT] = S[b2];
-      A0[base + b2 * NP * VT] = fma(st.ky, T1[b2], st.kz * T2[b2]);
+      A3[base + b2 * NP * VT] = S.out(b2);
+      A0[base + b2 * NP * VT] = fma(st.ky, T1.out(b2), st.kz * T2.out(b2));
     }
   }
   __syncthreads();
@@ -354,11 +366,15 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_bloch_sf(BlochTables tab, con
   for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int bc = idx / VT, v = idx - bc * VT;
     const int base = bc * NP * VT + v;
-    double Y1[NP], Y2[NP];
-    line_mat<NP>(st.C, A3 + base, VT, Y1);
-    line_mat<NP>(st.M, A0 + base, VT, Y2);
+    const Split<NP> sl = split_line<NP>(A3 + base, VT);
+    const Split<NP> tl = split_line<NP>(A0 + base, VT);
+    Half<NP> Y1, Y2;
+    Y1.zero();
+    Y2.zero();
+    eo_acc_anti<NP, NP>(st.C, sl, Y1.E, Y1.O);
+    eo_acc<NP, NP>(st.M, tl, Y2.E, Y2.O);
 #pragma unroll
-    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = st.scale * fma(st.kx, Y1[a2], Y2[a2]);
+    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = st.scale * fma(st.kx, Y1.out(a2), Y2.out(a2));
   }
   __syncthreads();
   for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
@@ -421,16 +437,30 @@ static void eo_halves(const double *A, int m, int n, EoMat &out) {
       out.o[i * no + j] = 0.5 * (A[(size_t)i * n + j] - A[(size_t)i * n + (n - 1 - j)]);
 }
 
+// even/odd halves of a centro-antisymmetric m x n matrix A (A[m-1-i][n-1-j] = -A[i][j]),
+// in the layout of eo_acc_anti:
+//   e[i][j] = (A[i][j] - A[i][n-1-j]) / 2      (i < ceil(m/2), j < n/2; pairs with o-lines),
+//   o[i][j] = (A[i][j] + A[i][n-1-j]) / 2      (i < m/2, j < n/2),  o[i][n/2] = A[i][n/2] for odd n.
+static void eo_halves_anti(const double *A, int m, int n, EoMat &out) {
+  const int ne = (n + 1) / 2, no = n / 2;
+  for (int i = 0; i < (m + 1) / 2; ++i)
+    for (int j = 0; j < no; ++j)
+      out.e[i * no + j] = 0.5 * (A[(size_t)i * n + j] - A[(size_t)i * n + (n - 1 - j)]);
+  for (int i = 0; i < m / 2; ++i) {
+    for (int j = 0; j < no; ++j)
+      out.o[i * ne + j] = 0.5 * (A[(size_t)i * n + j] + A[(size_t)i * n + (n - 1 - j)]);
+    if (n & 1) out.o[i * ne + no] = A[(size_t)i * n + no];
+  }
+}
+
 void bloch_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
               cudaStream_t s) {
   if (ncols <= 0 || !c->kc) return;
   const int np1 = c->np1;
   PAW_REQUIRE(np1 <= 10, PAW_ERR_UNSUPPORTED, "degree out of range for the Bloch kernel");
   BlochTables t{};
-  for (int i = 0; i < np1 * np1; ++i) {
-    t.M[i] = c->M1[i];
-    t.C[i] = c->C1s[i];
-  }
+  eo_halves(c->M1.data(), np1, np1, t.M);
+  eo_halves_anti(c->C1s.data(), np1, np1, t.C);
   t.kx = c->kvec[0];
   t.ky = c->kvec[1];
   t.kz = c->kvec[2];
