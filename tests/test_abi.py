@@ -55,8 +55,11 @@ def _create(lib, **kw):
     D = args["D"] if args["D"] is not None else np.zeros(1)
     dS = args["dS"] if args["dS"] is not None else np.zeros(1)
     h = C.c_void_p()
+    opts = None
+    if "kpoint" in args:
+        opts = C.byref(L._Opts(0, 0, 0, 0, (C.c_double * 3)(*args["kpoint"])))
     code = lib.paw_fe_create(C.byref(mesh), args["degree"], C.byref(atoms), C.byref(proj),
-                             D.ctypes.data_as(L._DP), dS.ctypes.data_as(L._DP), None, None, C.byref(h))
+                             D.ctypes.data_as(L._DP), dS.ctypes.data_as(L._DP), None, opts, C.byref(h))
     return code, lib.paw_last_error().decode()
 
 
@@ -75,6 +78,16 @@ def test_rejects_bad_arguments_before_device_work(lib):
     assert _create(lib, natoms=1, shells=((3, 0.5),), D=D, dS=D)[0] == 2
     # cutoff reaching half the box
     assert _create(lib, natoms=1, shells=((0, 1.0),), D=D, dS=D)[0] == 2
+
+
+def test_rejects_bad_kpoint_arguments_before_device_work(lib):
+    # a Bloch wavevector stores 2 nproj real projectors: at most 16 projectors per atom
+    shells = ((2, 0.5), (2, 0.5), (2, 0.5), (2, 0.5))
+    D = np.zeros((1, 20, 20))
+    code, msg = _create(lib, natoms=1, shells=shells, D=D, dS=D, kpoint=(0.1, 0.0, 0.0))
+    assert code == 2 and "16 projectors" in msg
+    code, msg = _create(lib, kpoint=(float("nan"), 0.0, 0.0))
+    assert code == 1 and "kpoint" in msg
 
 
 def test_null_handle_calls_fail_cleanly(lib):
