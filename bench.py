@@ -366,7 +366,6 @@ MEASURED_TRAFFIC = {
     ("residual_local", None): (39.38, "k_local_sf"),
     ("residual_nonlocal", None): (13.09 + 17.37, "k_own_project64 + k_own_expand64"),
     ("cell_products", "tf32"): (23.17, "k_tc_stream<CellStream>"),
-    ("projection", "tf32"): (7.24, "k_tc_stream<ProjStream>"),
     ("recurrence", "tf32"): (25.60, "k_exp_stream<2>"),
 }
 TRAFFIC_WORKLOAD = "mid"

@@ -263,9 +263,11 @@ void nl_recurrence_f64(paw_context *c, const double *WS, const double *WH, int n
 // tensor-core owner-cell kernels (nonlocal_tc.cu), T = float, TF32 operands
 bool nltc_supported(const paw_context *c);
 void nltc_prepare(paw_context *c, cudaStream_t s);
-// per-pair partials PP[k][al][v] = sum_o P[k][o][al] rowscale[o] X[o][v]
-void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
-                  cudaStream_t s);
+// U[a][al][v] = sum over the pairs k of atom a of sum_o P[k][o][al] rowscale[o] X[o][v]:
+// the persistent kernel reduces into U directly (FP32 reductions, returns true);
+// the one-CTA-per-tile form writes per-pair partials PP[k][al][v] (returns false)
+bool nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
+                  float *U, cudaStream_t s);
 // expansion with the output stage of mode (EXP_ADD / EXP_SINV / EXP_RECURRENCE)
 struct ExpArgs;
 void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, const float *W2, cudaStream_t s);

@@ -774,7 +774,7 @@ static T *project_U(paw_context *c, paw_precision prec, const T *X, int ldx, int
   T *U = c->ws_partial.as<T>(), *PP = c->ws_pp.as<T>();
   if constexpr (sizeof(T) == 4) {
     if (use_tc<T>(c, prec)) {
-      nltc_project(c, X, ldx, ncols, rowscale, PP, s);
+      if (nltc_project(c, X, ldx, ncols, rowscale, PP, U, s)) return U;   // reduced in the epilogue
       dim3 g((ncols + 31) / 32, c->npad, c->natoms);
       k_pair_reduce<T><<<g, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
       PAW_LAUNCH_CHECK("k_pair_reduce");

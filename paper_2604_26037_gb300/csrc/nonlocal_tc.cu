@@ -495,10 +495,10 @@ struct ProjStream {
   static constexpr uint32_t B_MAX = 192u * 128u;
   CUtensorMap tm[NW];   // rows of X (gathered with TMA)
   int ntiles, ncols, n, p, N1, own, npad, kc_own, ppt, vtiles, ldx;
-  const int *own_off;
+  const int *own_off, *own_atom;
   const uint8_t *B;
   const float *X;
-  float *PP;
+  float *U;             // per-atom sums (zeroed before the launch)
   struct Tile {
     int e, vt, k0, np;
     int64_t cb;
@@ -525,18 +525,23 @@ struct ProjStream {
     return B + (size_t)(T.k0 + sub * ppt) * npad * 128 * kc_own + (size_t)kc * ncol(T, sub) * 128;
   }
   __device__ uint32_t dcol(int) const { return 0; }
-  // partials PP[(k0 + sub ppt) npad + col][v]; four warps, one per lane quarter
+  // U[atom of pair][al][v] += column (pair, al) of the tile: FP32 reductions into
+  // the per-atom sums (no per-pair partials); four warps, one per lane quarter.
+  // Columns come in whole pairs of npad (a multiple of 16), so a 16-column
+  // group belongs to one pair.
   __device__ void epilogue(const Tile &T, int sub, uint32_t tl, int q, int, int lane, bool) const {
     const int nc = ncol(T, sub);
     const int v = T.vt * MT + q * 32 + lane;
-    float *dst = PP + (size_t)(T.k0 + sub * ppt) * npad * ncols + v;
-    for (int c0 = 0; c0 < nc; c0 += 32) {
-      uint32_t rr[32];
-      tmem_ld32(tl + (uint32_t)c0, rr);
+    const int kb = T.k0 + sub * ppt;
+    for (int c0 = 0; c0 < nc; c0 += 16) {
+      uint32_t rr[16];
+      tmem_ld16_nowait(tl + (uint32_t)c0, rr);
+      tmem_ld_wait();
+      const int kk = c0 / npad, al0 = c0 - kk * npad;
+      float *dst = U + ((size_t)own_atom[kb + kk] * npad + al0) * ncols + v;
       if (v < ncols) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < nc) dst[(size_t)(c0 + j) * ncols] = __uint_as_float(rr[j]);
+        for (int j = 0; j < 16; ++j) atomicAdd(dst + (size_t)j * ncols, __uint_as_float(rr[j]));
       }
     }
   }
@@ -1025,9 +1030,9 @@ static bool rows16(const void *p, int ld) {
   return reinterpret_cast<uintptr_t>(p) % 16 == 0 && ld % 4 == 0;
 }
 
-void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
-                  cudaStream_t s) {
-  if (ncols <= 0) return;
+bool nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
+                  float *U, cudaStream_t s) {
+  if (ncols <= 0) return false;
   nltc_prepare(c, s);
   const NlTcMats &N = c->nltc;
   const int vtiles = (ncols + MT - 1) / MT;
@@ -1046,12 +1051,14 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
     p.vtiles = vtiles;
     p.ldx = ldx;
     p.own_off = c->own_off.as<int>();
+    p.own_atom = c->own_atom.as<int>();
     p.B = scaled ? N.projBs.as<uint8_t>() : N.projB.as<uint8_t>();
     p.X = X;
-    p.PP = PP;
+    p.U = U;
+    PAW_CUDA(cudaMemsetAsync(U, 0, sizeof(float) * (size_t)c->natoms * c->npad * ncols, s));
     encode_row_map(&p.tm[0], X, c->ndof, ncols, ldx);
     launch_stream(c, p, s, "k_tc_stream<projection>");
-    return;
+    return true;   // U holds the per-atom sums
   }
   ProjTcArgs a;
   a.n = c->n;
@@ -1076,6 +1083,7 @@ void nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
   PAW_CUDA(cudaFuncSetAttribute(k_nl_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   k_nl_project_tc<<<(unsigned)blocks, THREADS, shm, s>>>(a);
   PAW_LAUNCH_CHECK("k_nl_project_tc");
+  return false;   // per-pair partials in PP
 }
 
 template <int MODE>
