@@ -170,7 +170,8 @@ def run_ours(args, ws, rank, local):
     cfg = inputs.CONFIGS[args.workload]
     sysd = inputs.make_system(args.workload)
     kp = tuple(args.kpoint) if args.kpoint else None
-    fe = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, kpoint=kp)
+    fe = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, kpoint=kp,
+                             y0_pair32=args.y0_pair32)
     M, N, m = fe.ndof, cfg["nvec"], cfg["degree"]
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     # at a Bloch wavevector k the vectors are complex (one complex vector = one vector of the metric)
@@ -186,25 +187,27 @@ def run_ours(args, ws, rank, local):
     out = torch.empty_like(X)
     stream = torch.cuda.current_stream()
 
-    def timed(prec, steps, warmup, profile=False):
+    def timed(prec, steps, warmup, profile=False, h=None, dst=None):
+        h = fe if h is None else h
+        dst = out if dst is None else dst
         for _ in range(warmup):
-            fe.cheb_filter(X, lam, m, bounds, prec=prec, out=out)
+            h.cheb_filter(X, lam, m, bounds, prec=prec, out=dst)
         torch.cuda.synchronize()
         _barrier(ws)
         if profile:
-            fe.profile_enable(True)
+            h.profile_enable(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(steps):
-                fe.cheb_filter(X, lam, m, bounds, prec=prec, out=out)
+                h.cheb_filter(X, lam, m, bounds, prec=prec, out=dst)
             e1.record(stream)
             torch.cuda.synchronize()
-        prof = fe.profile_read() if profile else None
+        prof = h.profile_read() if profile else None
         if profile:
-            fe.profile_enable(False)
+            h.profile_enable(False)
         _barrier(ws)
         ms = e0.elapsed_time(e1) / steps
         return _max_over_ranks(ms, ws), prof, clk.summary()
@@ -219,6 +222,30 @@ def run_ours(args, ws, rank, local):
         ms64, _, _ = timed("fp64", args.fp64_steps, 1)
         fp64 = {"value": units_per_step * ws / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
                 "steps": args.fp64_steps, "warmup": 1}
+
+    # the same filter with step 2 in pair-of-FP32 arithmetic (FP64-class accuracy on the FP32 pipes)
+    pair = None
+    if args.pair_steps > 0 and not kp and not args.y0_pair32:
+        fe_p = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, y0_pair32=True)
+        out_p = torch.empty_like(out)
+        ms_p, prof_p, clk_p = timed(args.prec, args.pair_steps, 1, profile=True, h=fe_p, dst=out_p)
+        # both handles filter the same input with the FP64 bracket: the outputs differ
+        # by the step-2 rounding only
+        fe.cheb_filter(X, lam, m, bounds, prec="fp64", out=out)
+        fe_p.cheb_filter(X, lam, m, bounds, prec="fp64", out=out_p)
+        diff64 = float((out_p - out).abs().max() / out.abs().max())
+        ph = {k: round(v["ms"] / args.pair_steps, 3) for k, v in prof_p.items() if isinstance(v, dict)}
+        ph64 = {k: v["ms"] / args.steps for k, v in prof.items() if isinstance(v, dict)}
+        s2 = ph["residual_local"] + ph["residual_nonlocal"]
+        s2_64 = ph64["residual_local"] + ph64["residual_nonlocal"]
+        pair = {"value": round(units_per_step * ws / (ms_p / 1e3) / 1e9, 4), "ms_per_step": round(ms_p, 3),
+                "steps": args.pair_steps, "warmup": 1, "phases_ms_per_step": ph,
+                "step2_ms": round(s2, 3), "step2_speedup_vs_fp64": round(s2_64 / s2, 3),
+                "fp64_bracket_output_rel_diff": diff64, "clocks": clk_p,
+                "arithmetic": "step 2 with every product and sum on pairs of FP32 numbers (about 48 bits); "
+                              "Y stored FP64; the rest of the call as the main measurement"}
+        del out_p
+        fe_p.close()
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -321,6 +348,7 @@ def run_ours(args, ws, rank, local):
                                f"M={M} DoFs, {sysd['natoms']} atoms x {sysd['nproj']} projectors, "
                                f"N={N} in blocks of {cfg['block']}, degree {m}",
                    "precision": args.prec, "y0_storage": "fp32" if args.y0_fp32 else "fp64",
+                   "step2_arithmetic": "pair-of-FP32" if args.y0_pair32 else "fp64",
                    **({"kpoint_per_bohr": list(kp), "vectors": "complex (real blocks of 2 B columns inside)"}
                       if kp else {}),
                    "start": args.start,
@@ -336,6 +364,8 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
         "bounds": [float(b) for b in bounds],
     }
+    if pair is not None:
+        res["step2_pair32"] = pair
     if rrm is not None:
         res["rayleigh_ritz"] = rrm
     if gradm is not None:
@@ -609,6 +639,11 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "bf16", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--y0-fp32", action="store_true")
+    ap.add_argument("--y0-pair32", action="store_true",
+                    help="form step 2 (Y = H X - S X Lambda) in pair-of-FP32 arithmetic in the main measurement")
+    ap.add_argument("--pair-steps", type=int, default=3,
+                    help="timed calls of the filter with a pair-of-FP32 step 2, reported beside the FP64 one "
+                         "(0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kpoint", type=float, nargs=3, default=None,
                     help="Bloch wavevector k (1/bohr): complex vectors, throughput per complex vector")

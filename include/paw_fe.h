@@ -80,8 +80,15 @@ typedef enum {
   PAW_TF32 = 2,  /* FP32 storage; cell products and projector contractions   */
                  /* on tcgen05 tensor cores (TF32 operands, FP32 accumulation */
                  /* in tensor memory)                                          */
-  PAW_BF16 = 3   /* as PAW_TF32 with BF16 cell-matrix and vector operands of  */
+  PAW_BF16 = 3,  /* as PAW_TF32 with BF16 cell-matrix and vector operands of  */
                  /* the cell products (projector contractions stay TF32)       */
+  PAW_F32X2 = 4  /* FP64 storage; every product and sum in pair-of-FP32      */
+                 /* arithmetic (a value is hi + lo, two FP32 numbers: about   */
+                 /* 48 significant bits, relative rounding about 2^-47) on    */
+                 /* the FP32 pipes, which GB300 issues 64x faster than FP64.  */
+                 /* Taken by paw_apply_H and paw_apply_S (k = 0); the filter's */
+                 /* step 2 uses it through paw_options.y0_pair32.  Other calls */
+                 /* return PAW_ERR_UNSUPPORTED.                               */
 } paw_precision;
 
 /* Periodic cubic box: L[0] = L[1] = L[2] and n_cells equal, periodic = 1. */
@@ -125,6 +132,10 @@ typedef struct {
                           mixed-precision subspace rotation)                    */
   double kpoint[3];    /* Bloch wavevector k (1/bohr); nonzero: complex vectors
                           (see the conventions at the top of this file)        */
+  int32_t y0_pair32;   /* 1: form Y = H X - S X Lambda of paw_cheb_filter (step
+                          2) in PAW_F32X2 arithmetic instead of FP64; Y keeps
+                          FP64 storage.  k = 0 only (else paw_fe_create returns
+                          PAW_ERR_UNSUPPORTED).  Default 0: FP64, as Algorithm 2 */
 } paw_options;
 
 /* Filter bounds (Algorithm 2 inputs): a0 lower end of the wanted spectrum,
@@ -191,7 +202,8 @@ paw_status paw_get_info(paw_handle h, paw_info *out);
  * not overlap.  FP64 and FP32 calls are asynchronous on `stream`; PAW_TF32
  * and PAW_BF16 calls wait for the stream and return TIMEOUT when a
  * tensor-core kernel gave up on one of its bounded waits (Y is then
- * incomplete).  The same holds for paw_apply_Sinv_approx. */
+ * incomplete).  The same holds for paw_apply_Sinv_approx.  PAW_F32X2: X, Y
+ * FP64 as for PAW_FP64, asynchronous, real vectors only (k = 0). */
 paw_status paw_apply_H(paw_handle h, paw_precision prec, const void *X, void *Y,
                        int ncols, int ldx, int ldy, void *stream);
 
@@ -234,7 +246,8 @@ paw_status paw_apply_Sinv_approx_noalloc(paw_handle h, paw_precision prec, const
  *   lambda_in : host FP64 ncols, the eigenvalue estimates Lambda
  *   degree    : m >= 1 (H applied m times, Shat^-1 applied m times)
  *   X_out     : device FP64 ndof x ncols (ld ldo); may not alias X_in
- * Y = H X - S X Lambda is formed in FP64 (step 2); for PAW_FP32/TF32/BF16 the
+ * Y = H X - S X Lambda is formed in FP64 (step 2; in PAW_F32X2 arithmetic when
+ * options.y0_pair32 is set); for PAW_FP32/TF32/BF16 the
  * recurrence bracket is evaluated in reduced precision, the term
  * (2 zeta/e) Y Lambda_Y is added in FP64 and R is stored in FP32 (Sec. 4.4,
  * mixed precision computation).  Errors: INVALID_ARG (a0 < bW < bU violated,

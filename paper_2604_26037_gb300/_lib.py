@@ -18,7 +18,8 @@ class Precision:
     FP32 = 1
     TF32 = 2
     BF16 = 3
-    names = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+    F32X2 = 4   # FP64 data, pair-of-FP32 arithmetic (apply_H / apply_S)
+    names = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "f32x2": 4}
 
     @classmethod
     def of(cls, p) -> int:
@@ -58,7 +59,7 @@ class _Vloc(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("block", C.c_int32), ("pp_overlap", C.c_int32), ("y0_fp32", C.c_int32),
-                ("rr_mixed", C.c_int32), ("kpoint", C.c_double * 3)]
+                ("rr_mixed", C.c_int32), ("kpoint", C.c_double * 3), ("y0_pair32", C.c_int32)]
 
 
 class _Bounds(C.Structure):
@@ -187,7 +188,8 @@ class PawFE:
     """One PAW finite-element problem on the current CUDA device."""
 
     def __init__(self, L, ncell, degree, positions=(), shells=(), D=None, dS=None,
-                 vloc=None, block=256, pp_overlap=False, y0_fp32=False, rr_mixed=False, kpoint=None):
+                 vloc=None, block=256, pp_overlap=False, y0_fp32=False, rr_mixed=False, kpoint=None,
+                 y0_pair32=False):
         self._lib = load_library()
         pos = np.ascontiguousarray(np.asarray(positions, float).reshape(-1, 3))
         na = pos.shape[0]
@@ -211,7 +213,7 @@ class PawFE:
             vp = C.pointer(_Vloc(cen.shape[0], _dptr(cen), _dptr(dep), _dptr(wid)))
         kp = (0.0, 0.0, 0.0) if kpoint is None else tuple(float(x) for x in kpoint)
         opts = _Opts(int(block), int(bool(pp_overlap)), int(bool(y0_fp32)), int(bool(rr_mixed)),
-                     (C.c_double * 3)(*kp))
+                     (C.c_double * 3)(*kp), int(bool(y0_pair32)))
         h = C.c_void_p()
         _check(self._lib.paw_fe_create(C.byref(mesh), int(degree), C.byref(atoms), C.byref(proj),
                                        _dptr(Dh), _dptr(dSh), vp, C.byref(opts), C.byref(h)))
@@ -274,9 +276,9 @@ class PawFE:
         import torch
         prec = Precision.of(prec)
         if self.complex:
-            dt = torch.complex128 if prec == Precision.FP64 else torch.complex64
+            dt = torch.complex128 if prec in (Precision.FP64, Precision.F32X2) else torch.complex64
         else:
-            dt = torch.float64 if prec == Precision.FP64 else torch.float32
+            dt = torch.float64 if prec in (Precision.FP64, Precision.F32X2) else torch.float32
         xp, rows, n, ldx = _mat(X, dt)
         if rows != self.ndof:
             raise ValueError(f"X has {rows} rows, expected {self.ndof}")

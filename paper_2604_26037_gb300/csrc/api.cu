@@ -205,21 +205,26 @@ static void merge_cplx(paw_context *c, const T *Xs, int n, T *Z, int ldz, cudaSt
   PAW_LAUNCH_CHECK("k_merge_cplx");
 }
 
-// Y = H X - S X Lambda in FP64 (Algorithm 2 step 2)
+// Y = H X - S X Lambda in FP64 (Algorithm 2 step 2), or in pair-of-FP32 arithmetic
+// with FP64 data when options.y0_pair32 is set
 static void residual_block(paw_context *c, const double *X, int ldx, const double *negLam_dev,
                            double *Y, int ldy, int ncols, cudaStream_t s) {
   zero_block<double>(Y, c->ndof, ncols, ldy, s);
   // (1/2 K^e + V^e + (1/2 |k|^2 - lambda_j) M^e) X_e in one sum-factorised pass;
   // at k != 0 the Bloch term -i B of Eq. hij on the split block [Re | Im]
+  const bool pair = c->opts.y0_pair32 != 0;   // pair-of-FP32 arithmetic (k = 0 only, checked at create)
   {
     PhaseScope ps(c, 0, s);
-    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, c->kmass, negLam_dev, s);
+    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, c->kmass, negLam_dev, s, pair);
     if (c->kc) {
       bloch_sf(c, X + ncols / 2, ldx, Y, ldy, ncols / 2, 1.0, s);
       bloch_sf(c, X, ldx, Y + ncols / 2, ldy, ncols / 2, -1.0, s);
     }
   }
-  if (c->nown_pairs > 0) {
+  if (c->nown_pairs > 0 && pair) {
+    PhaseScope ps(c, 4, s);
+    nl_residual_pair(c, X, ldx, ncols, c->DH64.as<double>(), c->DS64.as<double>(), negLam_dev, Y, ldy, s);
+  } else if (c->nown_pairs > 0) {
     PhaseScope ps(c, 4, s);
     // sum_a P^a (D_H^a - lambda_j dS^a) P^a^T x_j: one projection, one expansion
     c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
@@ -651,6 +656,11 @@ static void apply_cplx(paw_context *c, paw_precision prec, int which, const T *X
 
 static void apply_any(paw_context *c, paw_precision prec, int which, const void *X, int ldx, void *Y, int ldy,
                       int ncols, cudaStream_t s) {
+  if (prec == PAW_F32X2) {
+    PAW_REQUIRE(!c->kc, PAW_ERR_UNSUPPORTED, "PAW_F32X2 is implemented for real vectors (k = 0)");
+    op_pair(c, which, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
+    return;
+  }
   if (c->kc) {
     if (prec == PAW_FP64)
       apply_cplx<double>(c, prec, which, (const double *)X, ldx, (double *)Y, ldy, ncols, s);
@@ -767,6 +777,8 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
     c->kc = (c->kvec[0] != 0.0 || c->kvec[1] != 0.0 || c->kvec[2] != 0.0) ? 1 : 0;
     c->kmass = 0.5 * (c->kvec[0] * c->kvec[0] + c->kvec[1] * c->kvec[1] + c->kvec[2] * c->kvec[2]);
     PAW_REQUIRE(!c->kc || npj <= 16, PAW_ERR_UNSUPPORTED, "at most 16 projectors per atom with a Bloch wavevector");
+    PAW_REQUIRE(!c->kc || !c->opts.y0_pair32, PAW_ERR_UNSUPPORTED,
+                "pair-of-FP32 step 2 (y0_pair32) is implemented for real vectors (k = 0)");
     c->npjr = c->kc ? 2 * npj : npj;
     if (npj == 0) c->natoms = 0;   // atoms without projectors carry no nonlocal term
     c->status_dev.ensure(sizeof(int), &c->dev_bytes);
@@ -805,7 +817,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
                     &c->own_lg, &c->own_sidx, &c->own_cnt, &c->Bk64, &c->Bk32, &c->tc_bk_tf32.He,
                     &c->tc_bk_bf16.He, &c->ws_cx, &c->ws_cy,
-                    &c->nltc.eoff};
+                    &c->nltc.eoff, &c->ownPx2, &c->ws_Wx2};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   if (c->cublas) cublasDestroy(c->cublas);
@@ -869,15 +881,18 @@ static void check_tc_status(paw_context *c, paw_precision prec) {
   PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
 }
 
-static void check_prec(paw_precision prec) {
-  PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16, PAW_ERR_INVALID_ARG,
-              "unknown precision");
+// pair_ok: the call takes PAW_F32X2 (paw_apply_H, paw_apply_S)
+static void check_prec(paw_precision prec, bool pair_ok = false) {
+  PAW_REQUIRE(pair_ok || prec != PAW_F32X2, PAW_ERR_UNSUPPORTED,
+              "PAW_F32X2 applies to paw_apply_H and paw_apply_S (step 2 of the filter: options.y0_pair32)");
+  PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16 || prec == PAW_F32X2,
+              PAW_ERR_INVALID_ARG, "unknown precision");
 }
 
 paw_status paw_apply_H(paw_handle c, paw_precision prec, const void *X, void *Y, int ncols, int ldx, int ldy,
                        void *stream) {
   PAW_TRY_BEGIN
-  check_prec(prec);
+  check_prec(prec, true);
   check_block_args(c, X, Y, ncols, ldx, ldy);
   if (ncols == 0) return PAW_OK;
   auto s = (cudaStream_t)stream;
@@ -891,7 +906,7 @@ paw_status paw_apply_H(paw_handle c, paw_precision prec, const void *X, void *Y,
 paw_status paw_apply_S(paw_handle c, paw_precision prec, const void *X, void *Y, int ncols, int ldx, int ldy,
                        void *stream) {
   PAW_TRY_BEGIN
-  check_prec(prec);
+  check_prec(prec, true);
   check_block_args(c, X, Y, ncols, ldx, ldy);
   if (ncols == 0) return PAW_OK;
   auto s = (cudaStream_t)stream;

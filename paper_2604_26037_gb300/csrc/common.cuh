@@ -174,6 +174,8 @@ struct paw_context {
   pawfe::DevBuf own_off;                      // int32 ncells+1
   pawfe::DevBuf own_atom;                     // int32 nown_pairs
   pawfe::DevBuf ownP64, ownP32;               // nown_pairs * own * npad
+  pawfe::DevBuf ownPx2;                       // the same as pairs of FP32 numbers (built on first use)
+  pawfe::DevBuf ws_Wx2;                       // pair-of-FP32 coefficients of the nonlocal step-2 part
   pawfe::DevBuf own_ngrp;                     // int32 per pair: projector groups of 4 with a nonzero value
   // per pair and owned node o: index of the last projector group of 4 with a
   // nonzero value at o (-1: none); the owned nodes sorted by that index
@@ -268,13 +270,18 @@ void nltc_prepare(paw_context *c, cudaStream_t s);
 // the one-CTA-per-tile form writes per-pair partials PP[k][al][v] (returns false)
 bool nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
                   float *U, cudaStream_t s);
+// nonlocal part of step 2 in pair-of-FP32 arithmetic (k = 0):
+// Y += sum_a P^a (C^a + cs_j C2^a) P^a^T x_j (C2, cs may be NULL), X and Y FP64
+void nl_residual_pair(paw_context *c, const double *X, int ldx, int ncols, const double *C, const double *C2,
+                      const double *cs, double *Y, int ldy, cudaStream_t s);
 // expansion with the output stage of mode (EXP_ADD / EXP_SINV / EXP_RECURRENCE)
 struct ExpArgs;
 void nltc_expand(paw_context *c, int mode, const ExpArgs &A, const float *W1, const float *W2, cudaStream_t s);
 // FP64 sum-factorised local operator (sumfac.cu):
-// Y += alpha * (cK K^e + cV V^e + (cM + cMcol[j]) M^e) X, cell by cell with assembly
+// Y += alpha * (cK K^e + cV V^e + (cM + cMcol[j]) M^e) X, cell by cell with assembly;
+// pair32: the contractions in pair-of-FP32 arithmetic (f32x2.cuh), X and Y FP64
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
-              double cK, double cV, double cM, const double *cMcol, cudaStream_t s);
+              double cK, double cV, double cM, const double *cMcol, cudaStream_t s, bool pair32 = false);
 // FP64 sum-factorised Bloch term: Y += alpha * B X, B = sum_d k_d G_d cell by cell
 // (G_d the skew cell form of int N_I dN_J/dx_d, Eq. hij), with assembly
 void bloch_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha,
@@ -301,6 +308,8 @@ void op_S(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols,
 template <typename T>
 void op_Sinv(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols,
              cudaStream_t s);
+// H X (which = 0) or S X (which = 1) in pair-of-FP32 arithmetic, FP64 data, k = 0
+void op_pair(paw_context *c, int which, const double *X, int ldx, double *Y, int ldy, int ncols, cudaStream_t s);
 
 // tensor-core cell products (cell_tc.cu)
 void tc_prepare(paw_context *c, paw_precision prec, cudaStream_t s);

@@ -22,6 +22,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 #include "nonlocal_common.cuh"
 
 namespace pawfe {
@@ -563,17 +564,38 @@ __global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__res
 // = vector (32 per CTA), and every FP64 instruction of a warp belongs to one
 // owned node and one group of 4 projectors (warp-uniform control flow), taken
 // only up to the last group with a nonzero value on that node (own_lg).
+// The same kernels run in pair-of-FP32 arithmetic (R = f32x2, f32x2.cuh) for
+// the FP64-class step 2 on the FP32 pipes: projector values and coefficients
+// then come as pairs, X and Y stay FP64.
+
+// two consecutive numbers through the read-only path
+__device__ __forceinline__ void ldg2(const double *p, double &a, double &b) {
+  const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ldg2(const f32x2 *p, f32x2 &a, f32x2 &b) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  a = {v.x, v.y};
+  b = {v.z, v.w};
+}
+__device__ __forceinline__ double ldg1(const double *p) { return __ldg(p); }
+__device__ __forceinline__ f32x2 ldg1(const f32x2 *p) {
+  const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+  return {v.x, v.y};
+}
 
 // Projection: warp w takes positions w, w + 8, ... of each pair's node list
 // sorted by descending last nonzero group, so the eight warps share every pair
 // evenly; their partial sums are added in a fixed order through shared memory.
-template <int NPAD>
+template <int NPAD, typename R>
 __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, const int *__restrict__ own_off,
                                                        const int *__restrict__ own_cnt,
                                                        const int16_t *__restrict__ own_sidx,
-                                                       const double *__restrict__ oP, const double *__restrict__ X,
+                                                       const R *__restrict__ oP, const double *__restrict__ X,
                                                        int ldx, int ncols, const double *__restrict__ rowscale,
                                                        double *__restrict__ U) {
+  using A = Ar<R>;
   constexpr int NG = NPAD / 4, NWARP = 8;
   __shared__ int ooff[OWN_MAX];
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -581,8 +603,8 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
   const int k0 = own_off[e], k1 = own_off[e + 1];
   if (k0 == k1) return;
   const int own = p * p * p;
-  double *Xs = reinterpret_cast<double *>(sm_raw);   // [own][32]
-  double *red = Xs + (size_t)own * 32;               // [NWARP][NPAD][32]
+  R *Xs = reinterpret_cast<R *>(sm_raw);   // [own][32]
+  R *red = Xs + (size_t)own * 32;          // [NWARP][NPAD][32]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t base = owned_table(e, n, p, N1, ooff, own);
   __syncthreads();
@@ -591,7 +613,7 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
     const int64_t d = base + ooff[o];
     double x = (v < ncols) ? X[d * ldx + v] : 0.0;
     if (rowscale) x *= rowscale[d];
-    Xs[o * 32 + lane] = x;
+    Xs[o * 32 + lane] = A::from(x);
   }
   __syncthreads();
   for (int k = k0; k < k1; ++k) {
@@ -599,25 +621,27 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
 #pragma unroll
     for (int g = 0; g < NG; ++g) cg[g] = own_cnt[(size_t)k * NG + g];
     const int16_t *sidx = own_sidx + (size_t)k * own;
-    const double *Pk = oP + (size_t)k * own * NPAD;
-    double acc[NPAD];
+    const R *Pk = oP + (size_t)k * own * NPAD;
+    R acc[NPAD];
 #pragma unroll
-    for (int al = 0; al < NPAD; ++al) acc[al] = 0.0;
+    for (int al = 0; al < NPAD; ++al) acc[al] = A::zero();
     int o = (warp < cg[0]) ? sidx[warp] : 0;
     for (int i = warp; i < cg[0]; i += NWARP) {
       const int onext = (i + NWARP < cg[0]) ? sidx[i + NWARP] : 0;   // index of the next node in flight
-      const double x = Xs[o * 32 + lane];
-      const double2 *Pr = reinterpret_cast<const double2 *>(Pk + (size_t)o * NPAD);
+      const R x = Xs[o * 32 + lane];
+      const R *Pr = Pk + (size_t)o * NPAD;
       // a real branch (not predication): FP64 instructions of groups that are
       // zero on the node would still occupy the FP64 pipe
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         if (i >= cg[g]) break;   // this and the later groups are zero on the node
-        const double2 a = __ldg(Pr + 2 * g), b = __ldg(Pr + 2 * g + 1);
-        acc[4 * g + 0] = fma(a.x, x, acc[4 * g + 0]);
-        acc[4 * g + 1] = fma(a.y, x, acc[4 * g + 1]);
-        acc[4 * g + 2] = fma(b.x, x, acc[4 * g + 2]);
-        acc[4 * g + 3] = fma(b.y, x, acc[4 * g + 3]);
+        R p0, p1, p2, p3;
+        ldg2(Pr + 4 * g, p0, p1);
+        ldg2(Pr + 4 * g + 2, p2, p3);
+        acc[4 * g + 0] = A::fma(p0, x, acc[4 * g + 0]);
+        acc[4 * g + 1] = A::fma(p1, x, acc[4 * g + 1]);
+        acc[4 * g + 2] = A::fma(p2, x, acc[4 * g + 2]);
+        acc[4 * g + 3] = A::fma(p3, x, acc[4 * g + 3]);
       }
       o = onext;
     }
@@ -637,12 +661,12 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
     for (int idx = tid; idx < NPAD * 32; idx += 256) {
       const int al = idx >> 5, l = idx & 31;
       if (v0 + l < ncols) {
-        double sum = 0.0;
+        R sum = A::zero();
         if (al < nact) {
           sum = red[idx];
-          for (int w = 1; w < nwk; ++w) sum += red[(size_t)w * NPAD * 32 + idx];
+          for (int w = 1; w < nwk; ++w) sum = A::add(sum, red[(size_t)w * NPAD * 32 + idx]);
         }
-        U[((size_t)k * NPAD + al) * ncols + v0 + l] = sum;
+        U[((size_t)k * NPAD + al) * ncols + v0 + l] = A::to(sum);
       }
     }
     __syncthreads();
@@ -653,10 +677,11 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
 // cell the groups up to the node's last nonzero one are multiplied (four
 // accumulators, one per projector of a group, added in a fixed order), then the
 // output stage of k_own_expand (MODE) is applied to the node row.
-template <int NPAD, int MODE>
-__global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const double *__restrict__ oP,
+template <int NPAD, int MODE, typename R>
+__global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const R *__restrict__ oP,
                                                       const int8_t *__restrict__ own_lg,
-                                                      const double *__restrict__ W1, const double *__restrict__ W2) {
+                                                      const R *__restrict__ W1, const R *__restrict__ W2) {
+  using Q = Ar<R>;
   constexpr int NG = NPAD / 4, NWARP = 8;
   constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
   __shared__ int ooff[OWN_MAX];
@@ -676,28 +701,30 @@ __global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const double *_
   const int vc = vok ? v : ncols - 1;   // in-range column for the loads of idle lanes
   const int8_t *lgc = own_lg + (size_t)k0 * own;
   for (int o = warp; o < own; o += NWARP) {
-    double s1[4] = {0.0, 0.0, 0.0, 0.0}, s2[4] = {0.0, 0.0, 0.0, 0.0};   // four independent FMA chains per sum
+    R s1[4] = {Q::zero(), Q::zero(), Q::zero(), Q::zero()};   // four independent FMA chains per sum
+    R s2[4] = {Q::zero(), Q::zero(), Q::zero(), Q::zero()};
     for (int kk = 0; kk < np; ++kk) {
       const int lg = lgc[(size_t)kk * own + o];   // warp-uniform
       if (lg < 0) continue;
-      const double2 *Pr = reinterpret_cast<const double2 *>(oP + ((size_t)(k0 + kk) * own + o) * NPAD);
-      const double *w1 = W1 + (size_t)patom[kk] * NPAD * ncols + vc;
-      const double *w2 = (NW == 2) ? W2 + (size_t)patom[kk] * NPAD * ncols + vc : nullptr;
+      const R *Pr = oP + ((size_t)(k0 + kk) * own + o) * NPAD;
+      const R *w1 = W1 + (size_t)patom[kk] * NPAD * ncols + vc;
+      const R *w2 = (NW == 2) ? W2 + (size_t)patom[kk] * NPAD * ncols + vc : nullptr;
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         if (g > lg) break;
-        const double2 a = __ldg(Pr + 2 * g), b = __ldg(Pr + 2 * g + 1);
-        const double pv[4] = {a.x, a.y, b.x, b.y};
+        R pv[4];
+        ldg2(Pr + 4 * g, pv[0], pv[1]);
+        ldg2(Pr + 4 * g + 2, pv[2], pv[3]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) s1[j] = fma(pv[j], __ldg(w1 + (size_t)(4 * g + j) * ncols), s1[j]);
+        for (int j = 0; j < 4; ++j) s1[j] = Q::fma(pv[j], ldg1(w1 + (size_t)(4 * g + j) * ncols), s1[j]);
         if constexpr (NW == 2) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) s2[j] = fma(pv[j], __ldg(w2 + (size_t)(4 * g + j) * ncols), s2[j]);
+          for (int j = 0; j < 4; ++j) s2[j] = Q::fma(pv[j], ldg1(w2 + (size_t)(4 * g + j) * ncols), s2[j]);
         }
       }
     }
-    const double S1 = (s1[0] + s1[1]) + (s1[2] + s1[3]);
-    const double S2 = (NW == 2) ? (s2[0] + s2[1]) + (s2[2] + s2[3]) : 0.0;
+    const double S1 = Q::to(Q::add(Q::add(s1[0], s1[1]), Q::add(s1[2], s1[3])));
+    const double S2 = (NW == 2) ? Q::to(Q::add(Q::add(s2[0], s2[1]), Q::add(s2[2], s2[3]))) : 0.0;
     if (!vok) continue;
     const int64_t d = base + ooff[o];
     const double *Xin = static_cast<const double *>(A.Xin);
@@ -735,9 +762,10 @@ static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T
     const size_t shm = sizeof(double) * ((size_t)c->own * 32 + (size_t)8 * NPAD * 32);
     PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
                 "projection tile exceeds shared memory (degree too high)");
-    PAW_CUDA(cudaFuncSetAttribute(k_own_project64<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    PAW_CUDA(cudaFuncSetAttribute(k_own_project64<NPAD, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shm));
     dim3 g((ncols + 31) / 32, c->ncells);
-    k_own_project64<NPAD><<<g, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_cnt.as<int>(),
+    k_own_project64<NPAD, double><<<g, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_cnt.as<int>(),
                                              c->own_sidx.as<int16_t>(), c->ownP64.as<double>(), X, ldx, ncols,
                                              rowscale, U);
     PAW_LAUNCH_CHECK("k_own_project64");
@@ -828,6 +856,72 @@ void nl_project_residual(paw_context *c, const T *X, int ldx, int ncols, const d
   couple<T>(c, U, c->DH64.as<double>(), c->DS64.as<double>(), cs, 1.0, W, ncols, s);
 }
 
+// FP64 values to pairs of FP32 numbers (the tables and coefficients of the pair form)
+__global__ void k_to_pair(int64_t n, const double *__restrict__ x, f32x2 *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x2_from(x[i]);
+}
+
+static void to_pair(const double *x, int64_t n, f32x2 *y, cudaStream_t s) {
+  if (n <= 0) return;
+  k_to_pair<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
+  PAW_LAUNCH_CHECK("k_to_pair");
+}
+
+static ExpArgs exp_args(paw_context *c, int ncols);
+
+// Nonlocal part of step 2 in pair-of-FP32 arithmetic:
+//   Y += sum_a P^a (C^a + cs_j C2^a) P^a^T x_j   (step 2: C = D_H, C2 = dS, cs = -lambda)
+// projection and expansion (the FP64 kernels with R = f32x2) on the owner-cell
+// layout; per-atom sums and the 13 x 13 couplings stay FP64 (a small share).
+void nl_residual_pair(paw_context *c, const double *X, int ldx, int ncols, const double *C, const double *C2,
+                      const double *cs, double *Y, int ldy, cudaStream_t s) {
+  if (c->nown_pairs == 0 || ncols <= 0) return;
+  PAW_REQUIRE(!c->kc, PAW_ERR_UNSUPPORTED, "pair-of-FP32 arithmetic is implemented for real vectors (k = 0)");
+  PAW_REQUIRE(c->max_own_pairs <= 64 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+              "too many atoms on one cell for the expansion kernel");
+  const int64_t ntab = (int64_t)c->nown_pairs * c->own * c->npad;
+  if (!c->ownPx2.ptr) {   // built on first use from the FP64 table
+    c->ownPx2.ensure(sizeof(f32x2) * std::max<int64_t>(1, ntab), &c->dev_bytes);
+    to_pair(c->ownP64.as<double>(), ntab, c->ownPx2.as<f32x2>(), s);
+  }
+  const f32x2 *oP = c->ownPx2.as<f32x2>();
+  const size_t ub = sizeof(double) * (size_t)c->natoms * c->npad * ncols;
+  c->ws_partial.ensure(ub, &c->dev_bytes);
+  c->ws_pp.ensure(sizeof(double) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
+  double *U = c->ws_partial.as<double>(), *PP = c->ws_pp.as<double>();
+  const size_t shm = sizeof(f32x2) * ((size_t)c->own * 32 + (size_t)8 * c->npad * 32);
+  PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+              "projection tile exceeds shared memory (degree too high)");
+  dim3 gp((ncols + 31) / 32, c->ncells);
+  auto proj = (c->npad == 16) ? k_own_project64<16, f32x2> : k_own_project64<32, f32x2>;
+  PAW_CUDA(cudaFuncSetAttribute(proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  proj<<<gp, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_cnt.as<int>(), c->own_sidx.as<int16_t>(),
+                            oP, X, ldx, ncols, nullptr, PP);
+  PAW_LAUNCH_CHECK("k_own_project64");
+  dim3 gr((ncols + 31) / 32, c->npad, c->natoms);
+  k_pair_reduce<double><<<gr, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
+  PAW_LAUNCH_CHECK("k_pair_reduce");
+  const int64_t nw = (int64_t)c->natoms * c->npad * ncols;
+  c->ws_W2.ensure(sizeof(double) * std::max<int64_t>(1, nw), &c->dev_bytes);
+  c->ws_Wx2.ensure(sizeof(f32x2) * std::max<int64_t>(1, nw), &c->dev_bytes);
+  double *W = c->ws_W2.as<double>();
+  couple<double>(c, U, C, C2, cs, 1.0, W, ncols, s);
+  to_pair(W, nw, c->ws_Wx2.as<f32x2>(), s);
+  ExpArgs A = exp_args(c, ncols);
+  A.Y = Y;
+  A.ldy = ldy;
+  A.ldx = ldy;
+  A.ldy0 = 4;
+  dim3 ge((ncols + 31) / 32, c->ncells);
+  const f32x2 *Wx = c->ws_Wx2.as<f32x2>();
+  if (c->npad == 16)
+    k_own_expand64<16, EXP_ADD, f32x2><<<ge, 256, 0, s>>>(A, oP, c->own_lg.as<int8_t>(), Wx, nullptr);
+  else
+    k_own_expand64<32, EXP_ADD, f32x2><<<ge, 256, 0, s>>>(A, oP, c->own_lg.as<int8_t>(), Wx, nullptr);
+  PAW_LAUNCH_CHECK("k_own_expand64");
+}
+
 // atom-pair Gram blocks in the element type of the filter
 template <typename T>
 static const T *gram(paw_context *c);
@@ -877,9 +971,9 @@ static void own_expand(paw_context *c, paw_precision prec, ExpArgs A, const T *W
                 "too many atoms on one cell for the expansion kernel");
     dim3 g((A.ncols + 31) / 32, c->ncells);
     if (c->npad == 16)
-      k_own_expand64<16, MODE><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
+      k_own_expand64<16, MODE, double><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
     else
-      k_own_expand64<32, MODE><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
+      k_own_expand64<32, MODE, double><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
     PAW_LAUNCH_CHECK("k_own_expand64");
   } else {
     constexpr int VT = ExpCfg<T>::VT;

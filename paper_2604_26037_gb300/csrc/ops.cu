@@ -235,6 +235,18 @@ void op_S(paw_context *c, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStr
   }
 }
 
+void op_pair(paw_context *c, int which, const double *X, int ldx, double *Y, int ldy, int ncols, cudaStream_t s) {
+  PAW_REQUIRE(!c->kc && (which == 0 || which == 1), PAW_ERR_UNSUPPORTED,
+              "pair-of-FP32 arithmetic covers H and S of real vectors");
+  zero_block<double>(Y, c->ndof, ncols, ldy, s);
+  if (which == 0)
+    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, c->kmass, nullptr, s, true);
+  else
+    local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 0.0, 0.0, 1.0, nullptr, s, true);
+  const double *C = (which == 0) ? c->DH64.as<double>() : c->DS64.as<double>();
+  nl_residual_pair(c, X, ldx, ncols, C, nullptr, nullptr, Y, ldy, s);
+}
+
 template <typename T>
 void op_Sinv(paw_context *c, paw_precision prec, const T *X, int ldx, T *Y, int ldy, int ncols, cudaStream_t s) {
   if (c->nown_pairs == 0) {

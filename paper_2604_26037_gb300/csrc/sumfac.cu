@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace pawfe {
 
@@ -43,69 +44,79 @@ constexpr int SF_THREADS = 512;
 // The GLL nodes and Gauss points are symmetric about the cell centre, so the 1D mass and
 // stiffness matrices and the Lagrange values at the Gauss points are all of this form.
 constexpr int EOMAX = 5;   // ceil(10 / 2): up to 10 points per direction
-struct EoMat {
-  double e[EOMAX * EOMAX];   // [i < ceil(m/2)][j < ceil(n/2)]
-  double o[EOMAX * EOMAX];   // [i < m/2][j < n/2]
+template <typename R = double>
+struct EoMatT {
+  R e[EOMAX * EOMAX];   // [i < ceil(m/2)][j < ceil(n/2)]
+  R o[EOMAX * EOMAX];   // [i < m/2][j < n/2]
 };
+using EoMat = EoMatT<double>;
 
-struct SfTables {
-  EoMat M, D, phi, phit;   // M, D: np1 x np1; phi: nq1 x np1 (Lagrange at Gauss points); phit = phi^T
+template <typename R>
+struct SfTablesT {
+  EoMatT<R> M, D, phi, phit;   // M, D: np1 x np1; phi: nq1 x np1 (Lagrange at Gauss points); phit = phi^T
   double kfac, mfac;
 };
+using SfTables = SfTablesT<double>;
 
-template <int N>
+// The number type R of the contractions is double (the FP64 form) or f32x2
+// (pair-of-FP32 arithmetic with about 48 significant bits on the FP32 pipes);
+// Ar<R> supplies the operations.
+template <int N, typename R = double>
 struct Split {
   static constexpr int NE = (N + 1) / 2, NO = N / 2;
-  double e[NE], o[NO > 0 ? NO : 1];
+  R e[NE], o[NO > 0 ? NO : 1];
 };
 
 // split the line x[0], x[s], ..., x[(N-1) s]
-template <int N>
-__device__ __forceinline__ Split<N> split_line(const double *x, int s) {
-  Split<N> r;
+template <int N, typename R = double>
+__device__ __forceinline__ Split<N, R> split_line(const R *x, int s) {
+  using A = Ar<R>;
+  Split<N, R> r;
 #pragma unroll
   for (int j = 0; j < N / 2; ++j) {
-    const double a = x[j * s], b = x[(N - 1 - j) * s];
-    r.e[j] = a + b;
-    r.o[j] = a - b;
+    const R a = x[j * s], b = x[(N - 1 - j) * s];
+    r.e[j] = A::add(a, b);
+    r.o[j] = A::sub(a, b);
   }
   if (N & 1) r.e[N / 2] = x[(N / 2) * s];
   return r;
 }
 
 // E[i] += sum_j Ae[i][j] e[j],  O[i] += sum_j Ao[i][j] o[j]  for A of size M x N (in shared memory)
-template <int M, int N>
-__device__ __forceinline__ void eo_acc(const EoMat &A, const Split<N> &x, double (&E)[(M + 1) / 2],
-                                       double (&O)[M / 2 > 0 ? M / 2 : 1]) {
+template <int M, int N, typename R = double>
+__device__ __forceinline__ void eo_acc(const EoMatT<R> &A, const Split<N, R> &x, R (&E)[(M + 1) / 2],
+                                       R (&O)[M / 2 > 0 ? M / 2 : 1]) {
+  using Q = Ar<R>;
   constexpr int NE = (N + 1) / 2, NO = N / 2;
 #pragma unroll
   for (int i = 0; i < (M + 1) / 2; ++i)
 #pragma unroll
-    for (int j = 0; j < NE; ++j) E[i] = fma(A.e[i * NE + j], x.e[j], E[i]);
+    for (int j = 0; j < NE; ++j) E[i] = Q::fma(A.e[i * NE + j], x.e[j], E[i]);
 #pragma unroll
   for (int i = 0; i < M / 2; ++i)
 #pragma unroll
-    for (int j = 0; j < NO; ++j) O[i] = fma(A.o[i * NO + j], x.o[j], O[i]);
+    for (int j = 0; j < NO; ++j) O[i] = Q::fma(A.o[i * NO + j], x.o[j], O[i]);
 }
 
-template <int M>
+template <int M, typename R = double>
 struct Half {
-  double E[(M + 1) / 2], O[M / 2 > 0 ? M / 2 : 1];
+  using A = Ar<R>;
+  R E[(M + 1) / 2], O[M / 2 > 0 ? M / 2 : 1];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int i = 0; i < (M + 1) / 2; ++i) E[i] = 0.0;
+    for (int i = 0; i < (M + 1) / 2; ++i) E[i] = A::zero();
 #pragma unroll
-    for (int i = 0; i < (M / 2 > 0 ? M / 2 : 1); ++i) O[i] = 0.0;
+    for (int i = 0; i < (M / 2 > 0 ? M / 2 : 1); ++i) O[i] = A::zero();
   }
-  // output i of the line
-  __device__ __forceinline__ double out(int i) const {
-    if (2 * i + 1 == M) return E[i];
-    return (i < M / 2) ? E[i] + O[i] : E[M - 1 - i] - O[M - 1 - i];
+  // output i of the line (normalised)
+  __device__ __forceinline__ R out(int i) const {
+    if (2 * i + 1 == M) return A::norm(E[i]);
+    return (i < M / 2) ? A::add(E[i], O[i]) : A::sub(E[M - 1 - i], O[M - 1 - i]);
   }
 };
 
-template <int NP>
-__global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int ncells, const int *__restrict__ cell_dofs,
+template <int NP, typename R>
+__global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
                                                   const double *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
                                                   const double *__restrict__ X, int ldx, double *__restrict__ Y,
                                                   int ldy, int ncols, double alpha, double cK, double cV,
@@ -116,41 +127,44 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
   constexpr int S1 = (NQ * NP * NP > N3) ? NQ * NP * NP : N3;
   constexpr int S2 = (NQ * NQ * NP > N3) ? NQ * NQ * NP : N3;
   constexpr int S3 = (NQ * NQ * NQ > N3) ? NQ * NQ * NQ : N3;
-  __shared__ SfTables st;
+  using A = Ar<R>;
+  static_assert(sizeof(R) == sizeof(double), "shared-memory layout assumes 8-byte numbers");
+  __shared__ SfTablesT<R> st;
   __shared__ int dofs[N3];
   extern __shared__ double sm[];
-  double *A0 = sm;                 // x                  [N3][VT]
-  double *A1 = A0 + N3 * VT;       // P, then y          [N3][VT]
-  double *A2 = A1 + N3 * VT;       // Q, then U1, B1     [S1][VT]
-  double *A3 = A2 + S1 * VT;       // S, then U2, B2     [S2][VT]
-  double *A4 = A3 + S2 * VT;       // R, then U3         [S3][VT]
-  double *sw = A4 + S3 * VT;       // w_q V_q            [NQ^3]
+  R *A0 = reinterpret_cast<R *>(sm);   // x                  [N3][VT]
+  R *A1 = A0 + N3 * VT;                // P, then y          [N3][VT]
+  R *A2 = A1 + N3 * VT;                // Q, then U1, B1     [S1][VT]
+  R *A3 = A2 + S1 * VT;                // S, then U2, B2     [S2][VT]
+  R *A4 = A3 + S2 * VT;                // R, then U3         [S3][VT]
+  R *sw = A4 + S3 * VT;                // w_q V_q            [NQ^3]
   const int e = blockIdx.x, v0 = blockIdx.y * VT, tid = threadIdx.x;
   {
     const double *src = reinterpret_cast<const double *>(&tab);
     double *dst = reinterpret_cast<double *>(&st);
-    for (int i = tid; i < (int)(sizeof(SfTables) / sizeof(double)); i += SF_THREADS) dst[i] = src[i];
+    for (int i = tid; i < (int)(sizeof(SfTablesT<R>) / sizeof(double)); i += SF_THREADS) dst[i] = src[i];
   }
   for (int i = tid; i < N3; i += SF_THREADS) dofs[i] = cell_dofs[(size_t)e * N3 + i];
   const bool doV = cV != 0.0;
   if (doV)
-    for (int i = tid; i < NQ * NQ * NQ; i += SF_THREADS) sw[i] = cV * wV[(size_t)e * NQ * NQ * NQ + i];
+    for (int i = tid; i < NQ * NQ * NQ; i += SF_THREADS) sw[i] = A::from(cV * wV[(size_t)e * NQ * NQ * NQ + i]);
   __syncthreads();
   for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
     const int r = idx / VT, v = idx - r * VT;
-    A0[idx] = (v0 + v < ncols) ? X[(size_t)dofs[r] * ldx + v0 + v] : 0.0;
+    A0[idx] = (v0 + v < ncols) ? A::from(X[(size_t)dofs[r] * ldx + v0 + v]) : A::zero();
   }
   __syncthreads();
-  const double kf = cK * st.kfac, mf = st.mfac;
+  const double mf = st.mfac;
+  const R kf = A::from(cK * st.kfac);
   // c-contractions, one (a, b) line per thread: P = M_c x, Q = D_c x
   for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int ab = idx / VT, v = idx - ab * VT;
-    const Split<NP> x = split_line<NP>(A0 + ab * VT + v, NP * NP * VT);
-    Half<NP> P, Q;
+    const Split<NP, R> x = split_line<NP, R>(A0 + ab * VT + v, NP * NP * VT);
+    Half<NP, R> P, Q;
     P.zero();
     Q.zero();
-    eo_acc<NP, NP>(st.M, x, P.E, P.O);
-    eo_acc<NP, NP>(st.D, x, Q.E, Q.O);
+    eo_acc<NP, NP, R>(st.M, x, P.E, P.O);
+    eo_acc<NP, NP, R>(st.D, x, Q.E, Q.O);
 #pragma unroll
     for (int c2 = 0; c2 < NP; ++c2) {
       A1[(c2 * NP * NP + ab) * VT + v] = P.out(c2);
@@ -163,20 +177,20 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
     const int ac = idx / VT, v = idx - ac * VT;
     const int a = ac % NP, c = ac / NP;
     const int base = (c * NP * NP + a) * VT + v;
-    const Split<NP> p = split_line<NP>(A1 + base, NP * VT);
-    const Split<NP> q = split_line<NP>(A2 + base, NP * VT);
-    Half<NP> S, T;
+    const Split<NP, R> p = split_line<NP, R>(A1 + base, NP * VT);
+    const Split<NP, R> q = split_line<NP, R>(A2 + base, NP * VT);
+    Half<NP, R> S, T;
     S.zero();
     T.zero();
-    eo_acc<NP, NP>(st.M, p, S.E, S.O);
-    eo_acc<NP, NP>(st.D, p, T.E, T.O);
-    eo_acc<NP, NP>(st.M, q, T.E, T.O);
-    const double cmv = (cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0)) * mf;
+    eo_acc<NP, NP, R>(st.M, p, S.E, S.O);
+    eo_acc<NP, NP, R>(st.D, p, T.E, T.O);
+    eo_acc<NP, NP, R>(st.M, q, T.E, T.O);
+    const R cmv = A::from((cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0)) * mf);
 #pragma unroll
     for (int b2 = 0; b2 < NP; ++b2) {
-      const double sv = S.out(b2);
+      const R sv = S.out(b2);
       A3[base + b2 * NP * VT] = sv;
-      A4[base + b2 * NP * VT] = fma(kf, T.out(b2), cmv * sv);
+      A4[base + b2 * NP * VT] = A::norm(A::fma(kf, T.out(b2), A::mul(cmv, sv)));
     }
   }
   __syncthreads();
@@ -184,25 +198,25 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
   for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
     const int bc = idx / VT, v = idx - bc * VT;
     const int base = bc * NP * VT + v;
-    const Split<NP> sl = split_line<NP>(A3 + base, VT);
-    const Split<NP> rl = split_line<NP>(A4 + base, VT);
-    Half<NP> YD, YM;
+    const Split<NP, R> sl = split_line<NP, R>(A3 + base, VT);
+    const Split<NP, R> rl = split_line<NP, R>(A4 + base, VT);
+    Half<NP, R> YD, YM;
     YD.zero();
     YM.zero();
-    eo_acc<NP, NP>(st.D, sl, YD.E, YD.O);
-    eo_acc<NP, NP>(st.M, rl, YM.E, YM.O);
+    eo_acc<NP, NP, R>(st.D, sl, YD.E, YD.O);
+    eo_acc<NP, NP, R>(st.M, rl, YM.E, YM.O);
 #pragma unroll
-    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = fma(kf, YD.out(a2), YM.out(a2));
+    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = A::norm(A::fma(kf, YD.out(a2), YM.out(a2)));
   }
   if (doV) {
     __syncthreads();
     // U1[c][b][i] = sum_a phi[i][a] x[c][b][a]            (line (b, c), NP -> NQ)
     for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
       const int bc = idx / VT, v = idx - bc * VT;
-      const Split<NP> x = split_line<NP>(A0 + bc * NP * VT + v, VT);
-      Half<NQ> U;
+      const Split<NP, R> x = split_line<NP, R>(A0 + bc * NP * VT + v, VT);
+      Half<NQ, R> U;
       U.zero();
-      eo_acc<NQ, NP>(st.phi, x, U.E, U.O);
+      eo_acc<NQ, NP, R>(st.phi, x, U.E, U.O);
 #pragma unroll
       for (int i = 0; i < NQ; ++i) A2[(bc * NQ + i) * VT + v] = U.out(i);
     }
@@ -211,10 +225,10 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
     for (int idx = tid; idx < NQ * NP * VT; idx += SF_THREADS) {
       const int ic = idx / VT, v = idx - ic * VT;
       const int i = ic % NQ, c = ic / NQ;
-      const Split<NP> x = split_line<NP>(A2 + (c * NP * NQ + i) * VT + v, NQ * VT);
-      Half<NQ> U;
+      const Split<NP, R> x = split_line<NP, R>(A2 + (c * NP * NQ + i) * VT + v, NQ * VT);
+      Half<NQ, R> U;
       U.zero();
-      eo_acc<NQ, NP>(st.phi, x, U.E, U.O);
+      eo_acc<NQ, NP, R>(st.phi, x, U.E, U.O);
 #pragma unroll
       for (int j = 0; j < NQ; ++j) A3[((c * NQ + j) * NQ + i) * VT + v] = U.out(j);
     }
@@ -222,21 +236,21 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
     // U3[k][j][i] = w_q V_q sum_c phi[k][c] U2[c][j][i]    (line (i, j))
     for (int idx = tid; idx < NQ * NQ * VT; idx += SF_THREADS) {
       const int ji = idx / VT, v = idx - ji * VT;
-      const Split<NP> x = split_line<NP>(A3 + ji * VT + v, NQ * NQ * VT);
-      Half<NQ> U;
+      const Split<NP, R> x = split_line<NP, R>(A3 + ji * VT + v, NQ * NQ * VT);
+      Half<NQ, R> U;
       U.zero();
-      eo_acc<NQ, NP>(st.phi, x, U.E, U.O);
+      eo_acc<NQ, NP, R>(st.phi, x, U.E, U.O);
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) A4[(k * NQ * NQ + ji) * VT + v] = U.out(k) * sw[k * NQ * NQ + ji];
+      for (int k = 0; k < NQ; ++k) A4[(k * NQ * NQ + ji) * VT + v] = A::mul(U.out(k), sw[k * NQ * NQ + ji]);
     }
     __syncthreads();
     // B2[c][j][i] = sum_k phi[k][c] U3[k][j][i]            (line (i, j), NQ -> NP)
     for (int idx = tid; idx < NQ * NQ * VT; idx += SF_THREADS) {
       const int ji = idx / VT, v = idx - ji * VT;
-      const Split<NQ> x = split_line<NQ>(A4 + ji * VT + v, NQ * NQ * VT);
-      Half<NP> B;
+      const Split<NQ, R> x = split_line<NQ, R>(A4 + ji * VT + v, NQ * NQ * VT);
+      Half<NP, R> B;
       B.zero();
-      eo_acc<NP, NQ>(st.phit, x, B.E, B.O);
+      eo_acc<NP, NQ, R>(st.phit, x, B.E, B.O);
 #pragma unroll
       for (int c = 0; c < NP; ++c) A3[(c * NQ * NQ + ji) * VT + v] = B.out(c);
     }
@@ -245,10 +259,10 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
     for (int idx = tid; idx < NQ * NP * VT; idx += SF_THREADS) {
       const int ic = idx / VT, v = idx - ic * VT;
       const int i = ic % NQ, c = ic / NQ;
-      const Split<NQ> x = split_line<NQ>(A3 + (c * NQ * NQ + i) * VT + v, NQ * VT);
-      Half<NP> B;
+      const Split<NQ, R> x = split_line<NQ, R>(A3 + (c * NQ * NQ + i) * VT + v, NQ * VT);
+      Half<NP, R> B;
       B.zero();
-      eo_acc<NP, NQ>(st.phit, x, B.E, B.O);
+      eo_acc<NP, NQ, R>(st.phit, x, B.E, B.O);
 #pragma unroll
       for (int b = 0; b < NP; ++b) A2[((c * NP + b) * NQ + i) * VT + v] = B.out(b);
     }
@@ -256,18 +270,18 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTables tab, int nc
     // y[c][b][a] += sum_i phi[i][a] B1[c][b][i]            (line (b, c))
     for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
       const int bc = idx / VT, v = idx - bc * VT;
-      const Split<NQ> x = split_line<NQ>(A2 + bc * NQ * VT + v, VT);
-      Half<NP> B;
+      const Split<NQ, R> x = split_line<NQ, R>(A2 + bc * NQ * VT + v, VT);
+      Half<NP, R> B;
       B.zero();
-      eo_acc<NP, NQ>(st.phit, x, B.E, B.O);
+      eo_acc<NP, NQ, R>(st.phit, x, B.E, B.O);
 #pragma unroll
-      for (int a = 0; a < NP; ++a) A1[(bc * NP + a) * VT + v] += B.out(a);
+      for (int a = 0; a < NP; ++a) A1[(bc * NP + a) * VT + v] = A::add(A1[(bc * NP + a) * VT + v], B.out(a));
     }
   }
   __syncthreads();
   for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
     const int r = idx / VT, v = idx - r * VT;
-    if (v0 + v < ncols) atomicAdd(&Y[(size_t)dofs[r] * ldy + v0 + v], alpha * A1[idx]);
+    if (v0 + v < ncols) atomicAdd(&Y[(size_t)dofs[r] * ldy + v0 + v], alpha * A::to(A1[idx]));
   }
 }
 
@@ -404,15 +418,47 @@ size_t sf_smem() {
   return sizeof(double) * ((size_t)(2 * N3 + S1 + S2 + S3) * sf_vt<NP>() + NQ * NQ * NQ);
 }
 
-template <int NP>
-void launch_sf(paw_context *c, const SfTables &t, const double *wV, const double *X, int ldx, double *Y, int ldy,
+template <int NP, typename R>
+void launch_sf(paw_context *c, const SfTablesT<R> &t, const double *wV, const double *X, int ldx, double *Y, int ldy,
                int ncols, double alpha, double cK, double cV, double cM, const double *cMcol, cudaStream_t s) {
   const size_t shm = sf_smem<NP>();
-  PAW_CUDA(cudaFuncSetAttribute(k_local_sf<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  PAW_CUDA(cudaFuncSetAttribute(k_local_sf<NP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 g(c->ncells, (ncols + sf_vt<NP>() - 1) / sf_vt<NP>());
-  k_local_sf<NP><<<g, SF_THREADS, shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy, ncols, alpha, cK, cV,
-                                     cM, cMcol);
+  k_local_sf<NP, R><<<g, SF_THREADS, shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy, ncols, alpha,
+                                              cK, cV, cM, cMcol);
   PAW_LAUNCH_CHECK("k_local_sf");
+}
+
+template <typename R>
+void dispatch_sf(paw_context *c, const SfTablesT<R> &t, const double *wV, const double *X, int ldx, double *Y,
+                 int ldy, int ncols, double alpha, double cK, double cV, double cM, const double *cMcol,
+                 cudaStream_t s) {
+  switch (c->np1) {
+    case 2: launch_sf<2, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 3: launch_sf<3, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 4: launch_sf<4, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 5: launch_sf<5, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 6: launch_sf<6, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 7: launch_sf<7, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 8: launch_sf<8, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    case 9: launch_sf<9, R>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
+    default: throw Error{PAW_ERR_UNSUPPORTED, "degree out of range for the sum-factorised kernel"};
+  }
+}
+
+// nearest pair of FP32 numbers to each table entry (hi = fl32(x), lo = fl32(x - hi))
+static f32x2 host_pair(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+
+static EoMatT<f32x2> pair_table(const EoMat &m) {
+  EoMatT<f32x2> r{};
+  for (int i = 0; i < EOMAX * EOMAX; ++i) {
+    r.e[i] = host_pair(m.e[i]);
+    r.o[i] = host_pair(m.o[i]);
+  }
+  return r;
 }
 
 __global__ void k_wV(int64_t n, int nq, const double *__restrict__ wq, const double *__restrict__ Vq,
@@ -479,7 +525,7 @@ void bloch_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int 
 }
 
 void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int ncols, double alpha, double cK,
-              double cV, double cM, const double *cMcol, cudaStream_t s) {
+              double cV, double cM, const double *cMcol, cudaStream_t s, bool pair32) {
   if (ncols <= 0) return;
   SfTables t{};
   const int np1 = c->np1, nq1 = c->nq1;
@@ -503,17 +549,18 @@ void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int 
     c->wV_valid = 1;
   }
   const double *wV = c->wV.as<double>();
-  switch (np1) {
-    case 2: launch_sf<2>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 3: launch_sf<3>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 4: launch_sf<4>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 5: launch_sf<5>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 6: launch_sf<6>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 7: launch_sf<7>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 8: launch_sf<8>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    case 9: launch_sf<9>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s); break;
-    default: throw Error{PAW_ERR_UNSUPPORTED, "degree out of range for the sum-factorised kernel"};
+  if (!pair32) {
+    dispatch_sf<double>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s);
+    return;
   }
+  SfTablesT<f32x2> tp{};
+  tp.M = pair_table(t.M);
+  tp.D = pair_table(t.D);
+  tp.phi = pair_table(t.phi);
+  tp.phit = pair_table(t.phit);
+  tp.kfac = t.kfac;
+  tp.mfac = t.mfac;
+  dispatch_sf<f32x2>(c, tp, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s);
 }
 
 }  // namespace pawfe

@@ -57,7 +57,7 @@ def _create(lib, **kw):
     h = C.c_void_p()
     opts = None
     if "kpoint" in args:
-        opts = C.byref(L._Opts(0, 0, 0, 0, (C.c_double * 3)(*args["kpoint"])))
+        opts = C.byref(L._Opts(0, 0, 0, 0, (C.c_double * 3)(*args["kpoint"]), int(args.get("y0_pair32", 0))))
     code = lib.paw_fe_create(C.byref(mesh), args["degree"], C.byref(atoms), C.byref(proj),
                              D.ctypes.data_as(L._DP), dS.ctypes.data_as(L._DP), None, opts, C.byref(h))
     return code, lib.paw_last_error().decode()
@@ -88,6 +88,9 @@ def test_rejects_bad_kpoint_arguments_before_device_work(lib):
     assert code == 2 and "16 projectors" in msg
     code, msg = _create(lib, kpoint=(float("nan"), 0.0, 0.0))
     assert code == 1 and "kpoint" in msg
+    # pair-of-FP32 step 2 is implemented for real vectors only
+    code, msg = _create(lib, kpoint=(0.1, 0.0, 0.0), y0_pair32=1)
+    assert code == 2 and "y0_pair32" in msg
 
 
 def test_null_handle_calls_fail_cleanly(lib):
@@ -101,3 +104,21 @@ def test_null_handle_calls_fail_cleanly(lib):
 
 def test_precision_names():
     assert L.Precision.of("tf32") == 2 and L.Precision.of("FP64") == 0
+    assert L.Precision.of("f32x2") == L.Precision.F32X2 == 4
+
+
+def _header():
+    return open(os.path.join(ROOT, "include", "paw_fe.h")).read()
+
+
+def test_options_struct_matches_header():
+    """paw_options field order in the header is the binding's ctypes layout."""
+    body = re.search(r"typedef struct \{([^{}]*)\} paw_options;", _header()).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(\w+)(?:\[\d+\])?;", body)
+    assert fields == [f for f, _ in L._Opts._fields_]
+
+
+def test_precision_enum_matches_header():
+    vals = dict((k, int(v)) for k, v in re.findall(r"PAW_(FP64|FP32|TF32|BF16|F32X2) = (\d+)", _header()))
+    assert vals == {k: getattr(L.Precision, k) for k in vals} and len(vals) == 5

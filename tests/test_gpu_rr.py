@@ -73,17 +73,19 @@ def _rchfsi_gpu(fe, X0, m, iters, prec, nwanted):
     return X, lam, hist
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32-y32", "tf32-rrmix"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32-y32", "tf32-rrmix", "tf32-pair"])
 def test_rchfsi_converges_to_dense(prec):
     """tiny workload: 10 iterations, degree 20; 8 lowest eigenvalues within 1e-6 Ha of
     the dense FP64 generalised eigensolve of the oracle's matrices ("-y32": the
-    residual block Y kept in FP32 only; "-rrmix": mixed-precision subspace rotation)."""
+    residual block Y kept in FP32 only; "-rrmix": mixed-precision subspace rotation;
+    "-pair": step 2 in pair-of-FP32 arithmetic)."""
     op = oracle_ops("tiny")
     lam_ex, V_ex = rr.dense_eigs(op, 8)
     y32 = prec.endswith("-y32")
     rrmix = prec.endswith("-rrmix")
+    pair = prec.endswith("-pair")
     prec = prec.split("-")[0]
-    fe = gpu_fe("tiny", block=16, y0_fp32=y32, rr_mixed=rrmix)
+    fe = gpu_fe("tiny", block=16, y0_fp32=y32, rr_mixed=rrmix, y0_pair32=pair)
     X0 = inputs.start_columns("tiny", range(16))
     X, lam, hist = _rchfsi_gpu(fe, X0, 20, 10, prec, 8)
     err = np.abs(lam[:8] - lam_ex).max()
