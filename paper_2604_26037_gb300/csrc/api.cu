@@ -817,7 +817,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
                     &c->own_lg, &c->own_sidx, &c->own_cnt, &c->Bk64, &c->Bk32, &c->tc_bk_tf32.He,
                     &c->tc_bk_bf16.He, &c->ws_cx, &c->ws_cy,
-                    &c->nltc.eoff, &c->ownPx2, &c->ws_Wx2};
+                    &c->nltc.eoff, &c->ownPx2, &c->ws_Wx2, &c->wVx2};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   if (c->cublas) cublasDestroy(c->cublas);

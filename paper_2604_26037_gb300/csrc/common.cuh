@@ -154,6 +154,8 @@ struct paw_context {
   pawfe::DevBuf Vq;                           // ncells*nq
   pawfe::DevBuf wV;                           // ncells*nq: w_q detJ V_q (sum-factorised V^e)
   int wV_valid = 0;
+  int wVx2_valid = 0;                          // wVx2 = wV as pairs of FP32 numbers
+  pawfe::DevBuf wVx2;
   pawfe::TcMats tc_tf32, tc_bf16;
   pawfe::TcMats tc_bk_tf32, tc_bk_bf16;       // tcgen05 images of B^e (one shared matrix)
   pawfe::NlTcMats nltc;

@@ -48,10 +48,14 @@ __device__ __forceinline__ double x2_to(f32x2 a) { return (double)a.hi + (double
 
 __device__ __forceinline__ f32x2 x2_norm(f32x2 a) { return two_sum(a.hi, a.lo); }
 
-// a + b, normalised
+// a + b, normalised: the high parts error-free, the low parts rounded, then
+// Dekker's renormalisation.  After a cancellation of the high parts (|s.hi| <
+// |lo| is then possible) fast_two_sum still returns fl(s.hi + lo) and an
+// estimate of its error, so the absolute error stays at about 2^-47 (|a| + |b|)
+// (the "sloppy" double-word sum of the QD library, Hida-Li-Bailey 2001).
 __device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
   const f32x2 s = two_sum(a.hi, b.hi);
-  return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 
 __device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) { return x2_add(a, f32x2{-b.hi, -b.lo}); }

@@ -630,18 +630,22 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
       const int onext = (i + NWARP < cg[0]) ? sidx[i + NWARP] : 0;   // index of the next node in flight
       const R x = Xs[o * 32 + lane];
       const R *Pr = Pk + (size_t)o * NPAD;
-      // a real branch (not predication): FP64 instructions of groups that are
-      // zero on the node would still occupy the FP64 pipe
+      // the loads of every nonzero group first (predicated, all in flight at
+      // once), then the arithmetic behind a real branch: the FMAs of groups
+      // that are zero on the node would still occupy the FP64 pipe (or the
+      // issue slots of the pair form) under predication
+      R pv[NPAD];
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+        if (i < cg[g]) {
+          ldg2(Pr + 4 * g, pv[4 * g], pv[4 * g + 1]);
+          ldg2(Pr + 4 * g + 2, pv[4 * g + 2], pv[4 * g + 3]);
+        }
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         if (i >= cg[g]) break;   // this and the later groups are zero on the node
-        R p0, p1, p2, p3;
-        ldg2(Pr + 4 * g, p0, p1);
-        ldg2(Pr + 4 * g + 2, p2, p3);
-        acc[4 * g + 0] = A::fma(p0, x, acc[4 * g + 0]);
-        acc[4 * g + 1] = A::fma(p1, x, acc[4 * g + 1]);
-        acc[4 * g + 2] = A::fma(p2, x, acc[4 * g + 2]);
-        acc[4 * g + 3] = A::fma(p3, x, acc[4 * g + 3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[4 * g + j] = A::fma(pv[4 * g + j], x, acc[4 * g + j]);
       }
       o = onext;
     }

@@ -424,6 +424,7 @@ void rebuild_hamiltonian(paw_context *c) {
   c->tc_tf32.valid = 0;
   c->tc_bf16.valid = 0;
   c->wV_valid = 0;
+  c->wVx2_valid = 0;
   PAW_CUDA(cudaDeviceSynchronize());
 }
 

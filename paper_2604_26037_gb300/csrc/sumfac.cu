@@ -20,6 +20,7 @@
 // split of the centro-symmetric 1D matrices (about 25.7k FP64 operations per
 // cell and vector at p = 6 instead of 35.7k).  Shared-memory tensors are
 // stored [node][vector] so that consecutive threads touch consecutive words.
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -35,6 +36,15 @@ constexpr int sf_vt() { return NP >= 9 ? 4 : 8; }
 // allows one), so that every line of a contraction stage runs in one pass and
 // the FP64 pipe sees twice the warps of a 256-thread block
 constexpr int SF_THREADS = 512;
+// The pair-of-FP32 form issues about 12 FP32 instructions per FP64 FMA, so
+// issue slots, not a pipe, bound it: two blocks of 256 threads (half the
+// vectors each) per SM, whose barriers and gathers overlap.
+template <int NP, typename R>
+constexpr int sf_vt_r() { return std::is_same<R, double>::value ? sf_vt<NP>() : sf_vt<NP>() / 2; }
+template <typename R>
+constexpr int sf_threads() { return std::is_same<R, double>::value ? SF_THREADS : SF_THREADS / 2; }
+template <typename R>
+constexpr int sf_min_blocks() { return std::is_same<R, double>::value ? 1 : 2; }
 
 // Even/odd halves of a centro-symmetric 1D matrix A (m x n, A[m-1-i][n-1-j] = A[i][j]):
 //   Ae[i][j] = (A[i][j] + A[i][n-1-j]) / 2   (j < n/2),  Ae[i][n/2] = A[i][n/2] for odd n,
@@ -116,13 +126,14 @@ struct Half {
 };
 
 template <int NP, typename R>
-__global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
-                                                  const double *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
+__global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<R>()) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
+                                                  const R *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
                                                   const double *__restrict__ X, int ldx, double *__restrict__ Y,
                                                   int ldy, int ncols, double alpha, double cK, double cV,
                                                   double cM, const double *__restrict__ cMcol) {
   constexpr int NQ = NP + 1;
-  constexpr int VT = sf_vt<NP>();
+  constexpr int VT = sf_vt_r<NP, R>();
+  constexpr int NT = sf_threads<R>();
   constexpr int N3 = NP * NP * NP;
   constexpr int S1 = (NQ * NP * NP > N3) ? NQ * NP * NP : N3;
   constexpr int S2 = (NQ * NQ * NP > N3) ? NQ * NQ * NP : N3;
@@ -142,22 +153,35 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
   {
     const double *src = reinterpret_cast<const double *>(&tab);
     double *dst = reinterpret_cast<double *>(&st);
-    for (int i = tid; i < (int)(sizeof(SfTablesT<R>) / sizeof(double)); i += SF_THREADS) dst[i] = src[i];
+    for (int i = tid; i < (int)(sizeof(SfTablesT<R>) / sizeof(double)); i += NT) dst[i] = src[i];
   }
-  for (int i = tid; i < N3; i += SF_THREADS) dofs[i] = cell_dofs[(size_t)e * N3 + i];
+  for (int i = tid; i < N3; i += NT) dofs[i] = cell_dofs[(size_t)e * N3 + i];
   const bool doV = cV != 0.0;
   if (doV)
-    for (int i = tid; i < NQ * NQ * NQ; i += SF_THREADS) sw[i] = A::from(cV * wV[(size_t)e * NQ * NQ * NQ + i]);
+    for (int i = tid; i < NQ * NQ * NQ; i += NT) {
+      const R w = wV[(size_t)e * NQ * NQ * NQ + i];
+      sw[i] = (cV == 1.0) ? w : A::mul(A::from(cV), w);
+    }
   __syncthreads();
-  for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
-    const int r = idx / VT, v = idx - r * VT;
-    A0[idx] = (v0 + v < ncols) ? A::from(X[(size_t)dofs[r] * ldx + v0 + v]) : A::zero();
+  {
+    // gather: every load of the thread in flight before the first use
+    constexpr int NPER = (N3 * VT + NT - 1) / NT;
+    double xv[NPER];
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {
+      const int idx = tid + k * NT;
+      const int r = idx / VT, v = idx - r * VT;
+      xv[k] = (idx < N3 * VT && v0 + v < ncols) ? X[(size_t)dofs[r] * ldx + v0 + v] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < NPER; ++k)
+      if (tid + k * NT < N3 * VT) A0[tid + k * NT] = A::from(xv[k]);
   }
   __syncthreads();
   const double mf = st.mfac;
   const R kf = A::from(cK * st.kfac);
   // c-contractions, one (a, b) line per thread: P = M_c x, Q = D_c x
-  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
     const int ab = idx / VT, v = idx - ab * VT;
     const Split<NP, R> x = split_line<NP, R>(A0 + ab * VT + v, NP * NP * VT);
     Half<NP, R> P, Q;
@@ -173,7 +197,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
   }
   __syncthreads();
   // b-contractions, one (a, c) line per thread: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S
-  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
     const int ac = idx / VT, v = idx - ac * VT;
     const int a = ac % NP, c = ac / NP;
     const int base = (c * NP * NP + a) * VT + v;
@@ -195,7 +219,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
   }
   __syncthreads();
   // a-contractions, one (b, c) line per thread: y = kf D_a S + M_a R
-  for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
     const int bc = idx / VT, v = idx - bc * VT;
     const int base = bc * NP * VT + v;
     const Split<NP, R> sl = split_line<NP, R>(A3 + base, VT);
@@ -211,7 +235,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
   if (doV) {
     __syncthreads();
     // U1[c][b][i] = sum_a phi[i][a] x[c][b][a]            (line (b, c), NP -> NQ)
-    for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+    for (int idx = tid; idx < NP * NP * VT; idx += NT) {
       const int bc = idx / VT, v = idx - bc * VT;
       const Split<NP, R> x = split_line<NP, R>(A0 + bc * NP * VT + v, VT);
       Half<NQ, R> U;
@@ -222,7 +246,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
     }
     __syncthreads();
     // U2[c][j][i] = sum_b phi[j][b] U1[c][b][i]           (line (i, c))
-    for (int idx = tid; idx < NQ * NP * VT; idx += SF_THREADS) {
+    for (int idx = tid; idx < NQ * NP * VT; idx += NT) {
       const int ic = idx / VT, v = idx - ic * VT;
       const int i = ic % NQ, c = ic / NQ;
       const Split<NP, R> x = split_line<NP, R>(A2 + (c * NP * NQ + i) * VT + v, NQ * VT);
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
     }
     __syncthreads();
     // U3[k][j][i] = w_q V_q sum_c phi[k][c] U2[c][j][i]    (line (i, j))
-    for (int idx = tid; idx < NQ * NQ * VT; idx += SF_THREADS) {
+    for (int idx = tid; idx < NQ * NQ * VT; idx += NT) {
       const int ji = idx / VT, v = idx - ji * VT;
       const Split<NP, R> x = split_line<NP, R>(A3 + ji * VT + v, NQ * NQ * VT);
       Half<NQ, R> U;
@@ -245,7 +269,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
     }
     __syncthreads();
     // B2[c][j][i] = sum_k phi[k][c] U3[k][j][i]            (line (i, j), NQ -> NP)
-    for (int idx = tid; idx < NQ * NQ * VT; idx += SF_THREADS) {
+    for (int idx = tid; idx < NQ * NQ * VT; idx += NT) {
       const int ji = idx / VT, v = idx - ji * VT;
       const Split<NQ, R> x = split_line<NQ, R>(A4 + ji * VT + v, NQ * NQ * VT);
       Half<NP, R> B;
@@ -256,7 +280,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
     }
     __syncthreads();
     // B1[c][b][i] = sum_j phi[j][b] B2[c][j][i]            (line (i, c))
-    for (int idx = tid; idx < NQ * NP * VT; idx += SF_THREADS) {
+    for (int idx = tid; idx < NQ * NP * VT; idx += NT) {
       const int ic = idx / VT, v = idx - ic * VT;
       const int i = ic % NQ, c = ic / NQ;
       const Split<NQ, R> x = split_line<NQ, R>(A3 + (c * NQ * NQ + i) * VT + v, NQ * VT);
@@ -268,7 +292,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
     }
     __syncthreads();
     // y[c][b][a] += sum_i phi[i][a] B1[c][b][i]            (line (b, c))
-    for (int idx = tid; idx < NP * NP * VT; idx += SF_THREADS) {
+    for (int idx = tid; idx < NP * NP * VT; idx += NT) {
       const int bc = idx / VT, v = idx - bc * VT;
       const Split<NQ, R> x = split_line<NQ, R>(A2 + bc * NQ * VT + v, VT);
       Half<NP, R> B;
@@ -279,7 +303,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_local_sf(SfTablesT<R> tab, in
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < N3 * VT; idx += SF_THREADS) {
+  for (int idx = tid; idx < N3 * VT; idx += NT) {
     const int r = idx / VT, v = idx - r * VT;
     if (v0 + v < ncols) atomicAdd(&Y[(size_t)dofs[r] * ldy + v0 + v], alpha * A::to(A1[idx]));
   }
@@ -408,29 +432,29 @@ void launch_bloch(paw_context *c, const BlochTables &t, const double *X, int ldx
   PAW_LAUNCH_CHECK("k_bloch_sf");
 }
 
-template <int NP>
+template <int NP, typename R>
 size_t sf_smem() {
   constexpr int NQ = NP + 1;
   constexpr int N3 = NP * NP * NP;
   constexpr int S1 = (NQ * NP * NP > N3) ? NQ * NP * NP : N3;
   constexpr int S2 = (NQ * NQ * NP > N3) ? NQ * NQ * NP : N3;
   constexpr int S3 = (NQ * NQ * NQ > N3) ? NQ * NQ * NQ : N3;
-  return sizeof(double) * ((size_t)(2 * N3 + S1 + S2 + S3) * sf_vt<NP>() + NQ * NQ * NQ);
+  return sizeof(double) * ((size_t)(2 * N3 + S1 + S2 + S3) * sf_vt_r<NP, R>() + NQ * NQ * NQ);
 }
 
 template <int NP, typename R>
-void launch_sf(paw_context *c, const SfTablesT<R> &t, const double *wV, const double *X, int ldx, double *Y, int ldy,
+void launch_sf(paw_context *c, const SfTablesT<R> &t, const R *wV, const double *X, int ldx, double *Y, int ldy,
                int ncols, double alpha, double cK, double cV, double cM, const double *cMcol, cudaStream_t s) {
-  const size_t shm = sf_smem<NP>();
+  const size_t shm = sf_smem<NP, R>();
   PAW_CUDA(cudaFuncSetAttribute(k_local_sf<NP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  dim3 g(c->ncells, (ncols + sf_vt<NP>() - 1) / sf_vt<NP>());
-  k_local_sf<NP, R><<<g, SF_THREADS, shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy, ncols, alpha,
+  dim3 g(c->ncells, (ncols + sf_vt_r<NP, R>() - 1) / sf_vt_r<NP, R>());
+  k_local_sf<NP, R><<<g, sf_threads<R>(), shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy, ncols, alpha,
                                               cK, cV, cM, cMcol);
   PAW_LAUNCH_CHECK("k_local_sf");
 }
 
 template <typename R>
-void dispatch_sf(paw_context *c, const SfTablesT<R> &t, const double *wV, const double *X, int ldx, double *Y,
+void dispatch_sf(paw_context *c, const SfTablesT<R> &t, const R *wV, const double *X, int ldx, double *Y,
                  int ldy, int ncols, double alpha, double cK, double cV, double cM, const double *cMcol,
                  cudaStream_t s) {
   switch (c->np1) {
@@ -465,6 +489,11 @@ __global__ void k_wV(int64_t n, int nq, const double *__restrict__ wq, const dou
                      double *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = wq[i % nq] * Vq[i];
+}
+
+__global__ void k_wV_pair(int64_t n, const double *__restrict__ wV, f32x2 *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x2_from(wV[i]);
 }
 
 }  // namespace
@@ -553,6 +582,12 @@ void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int 
     dispatch_sf<double>(c, t, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s);
     return;
   }
+  if (!c->wVx2_valid) {   // w_q V_q as pairs of FP32 numbers, rebuilt with wV
+    c->wVx2.ensure(sizeof(f32x2) * nwv, &c->dev_bytes);
+    k_wV_pair<<<(unsigned)((nwv + 255) / 256), 256, 0, s>>>((int64_t)nwv, wV, c->wVx2.as<f32x2>());
+    PAW_LAUNCH_CHECK("k_wV_pair");
+    c->wVx2_valid = 1;
+  }
   SfTablesT<f32x2> tp{};
   tp.M = pair_table(t.M);
   tp.D = pair_table(t.D);
@@ -560,7 +595,7 @@ void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int 
   tp.phit = pair_table(t.phit);
   tp.kfac = t.kfac;
   tp.mfac = t.mfac;
-  dispatch_sf<f32x2>(c, tp, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s);
+  dispatch_sf<f32x2>(c, tp, c->wVx2.as<f32x2>(), X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s);
 }
 
 }  // namespace pawfe
