@@ -558,7 +558,7 @@ struct ProjStream {
 //   warp 1      MMA (lane 0), TMEM allocation
 //   warps 2..5  A gather (thread = vector row)
 //   warp 6      output-stage loader: lane 4 k + q gathers rows 4 q .. 4 q + 3
-//               of array k; lanes 16, 17 copy M_D^-1 and the DoF indices
+//               of array k (the epilogue reads M_D^-1 and the DoF indices itself)
 //   warp 7      idle
 //   warps 8..15 epilogue: lane quarter warp % 4, half (warp - 8) / 4 of each 16-row group
 namespace xs {
@@ -573,9 +573,7 @@ struct Geo {
   static constexpr int S = (MODE == EXP_RECURRENCE) ? 2 : 3;    // A/B stages
   static constexpr int NA = (MODE == EXP_RECURRENCE) ? 4 : 1;   // staged arrays
   static constexpr uint32_t STAGE = NW * A_BYTES + 128u * 128u;
-  static constexpr uint32_t MOFF = NA * 16u * ROWB;               // M_D^-1 of the 16 rows
-  static constexpr uint32_t DOFF = MOFF + 64u;                    // their DoF indices (int32)
-  static constexpr uint32_t GROUP = MOFF + 128u;
+  static constexpr uint32_t GROUP = NA * 16u * ROWB;              // 16 staged rows of each array
 };
 
 struct Shared {
@@ -788,7 +786,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const __grid_constant
     int na = 0;
 #pragma unroll
     for (int k = 0; k < G::NA; ++k) na += (a.amask >> k) & 1;
-    const uint32_t gbytes = (uint32_t)na * 16u * ROWB + 128u;   // row gathers + M_D^-1 + DoF indices
+    const uint32_t gbytes = (uint32_t)na * 16u * ROWB;   // row gathers
     const int k = lane >> 2, q = lane & 3;
     const bool mine = k < G::NA && ((a.amask >> k) & 1);
     uint32_t gc = 0;
@@ -818,9 +816,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const __grid_constant
         if (mine)
           tma_gather4(smem_u32(grp) + (uint32_t)(k * 16 + 4 * q) * ROWB, &a.tm[k], x, r4[0], r4[1], r4[2], r4[3],
                       full);
-        const size_t oo = ((size_t)T.e * a.nh + T.h) * a.ntile + gi * 16;
-        if (lane == 16) bulk_g2s(smem_u32(grp + G::MOFF), a.mdo + oo, 64u, full);
-        if (lane == 17) bulk_g2s(smem_u32(grp + G::DOFF), a.odof + oo, 64u, full);
       }
     }
     if (lane == 0)
@@ -859,6 +854,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const __grid_constant
       const uint32_t tl = tmem + (uint32_t)(b * 256) + ((uint32_t)(q * 32) << 16);
       for (int gi = 0; gi < T.ngroups; ++gi, ++gc) {
         const int gb = (int)(gc % NBUF);
+        // M_D^-1 and DoF index of the warp's 8 rows (owner order, padded to whole
+        // groups), read before the wait so that the loads overlap it
+        const size_t oo = ((size_t)T.e * a.nh + T.h) * a.ntile + gi * 16 + part * 8;
+        float mj[8];
+        int dj[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          mj[j] = (MODE != EXP_ADD) ? __ldg(a.mdo + oo + j) : 0.f;
+          dj[j] = __ldg(a.odof + oo + j);
+        }
         if (!tcs::warp_wait(smem_u32(&sh->sfull[gb]), (gc / NBUF) & 1u, abort, lane)) {
           run = false;
           break;
@@ -874,25 +879,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_stream(const __grid_constant
           for (int j = 0; j < 8; ++j) s1[j] = s2[j] = 0u;
         }
         const float *sg = reinterpret_cast<const float *>(stg + (size_t)gb * G::GROUP);
-        const float *sm = reinterpret_cast<const float *>(stg + (size_t)gb * G::GROUP + G::MOFF);
-        const int *sd = reinterpret_cast<const int *>(stg + (size_t)gb * G::GROUP + G::DOFF);
         const int nv = min(8, T.nrows - (gi * 16 + part * 8));   // rows of this warp in the group
         if (vok) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int jr = part * 8 + j;   // staged row
             if (j >= nv) break;
-            const int64_t d = sd[jr];
+            const int64_t d = dj[j];
             if (MODE == EXP_RECURRENCE) {
               const float ry = sg[(0 * 16 + jr) * MT + vl], rx = sg[(1 * 16 + jr) * MT + vl];
               const float yh = sg[(2 * 16 + jr) * MT + vl];
               const float yl = has_lo ? sg[(3 * 16 + jr) * MT + vl] : 0.f;
-              const float m = sm[jr];
+              const float m = mj[j];
               Y[d * a.A.ldy + v] = m * (ry - __uint_as_float(s1[j]));
               const float bracket = -be * ry - ga * rx + __uint_as_float(s2[j]);
               RX[d * a.A.ldx + v] = add_product_df(bracket, chi, clo, yh, yl);
             } else if (MODE == EXP_SINV) {
-              Y[d * a.A.ldy + v] = sm[jr] * (sg[jr * MT + vl] - __uint_as_float(s1[j]));
+              Y[d * a.A.ldy + v] = mj[j] * (sg[jr * MT + vl] - __uint_as_float(s1[j]));
             } else {
               Y[d * a.A.ldy + v] = fmaf(csv, __uint_as_float(s1[j]), sg[jr * MT + vl]);
             }
