@@ -108,13 +108,21 @@ def _dist():
 
 
 def _max_over_ranks(x, ws):
+    """The largest x over the ranks (the slowest replica's time); x itself at ws = 1."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_step_per_rank, ws, ms_per_step):
+    """GDoF.vec/s of the whole job: every replica processes units_per_step_per_rank per step
+    and the step takes ms_per_step on the slowest one (weak scaling)."""
+    return units_per_step_per_rank * ws / (ms_per_step / 1e3) / 1e9
 
 
 def _barrier(ws):
@@ -214,13 +222,13 @@ def run_ours(args, ws, rank, local):
 
     ms, prof, clocks = timed(args.prec, args.steps, args.warmup, profile=True)
     units_per_step = float(M) * N * m
-    value = units_per_step * ws / (ms / 1e3) / 1e9
+    value = whole_job_rate(units_per_step, ws, ms)
 
     # FP64 form of the same filter (the plain method), fewer steps: it is slow on GB300
     fp64 = None
     if args.fp64_steps > 0:
         ms64, _, _ = timed("fp64", args.fp64_steps, 1)
-        fp64 = {"value": units_per_step * ws / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
+        fp64 = {"value": whole_job_rate(units_per_step, ws, ms64), "ms_per_step": ms64,
                 "steps": args.fp64_steps, "warmup": 1}
 
     # the same filter with step 2 in pair-of-FP32 arithmetic (FP64-class accuracy on the FP32 pipes)
@@ -238,7 +246,7 @@ def run_ours(args, ws, rank, local):
         ph64 = {k: v["ms"] / args.steps for k, v in prof.items() if isinstance(v, dict)}
         s2 = ph["residual_local"] + ph["residual_nonlocal"]
         s2_64 = ph64["residual_local"] + ph64["residual_nonlocal"]
-        pair = {"value": round(units_per_step * ws / (ms_p / 1e3) / 1e9, 4), "ms_per_step": round(ms_p, 3),
+        pair = {"value": round(whole_job_rate(units_per_step, ws, ms_p), 4), "ms_per_step": round(ms_p, 3),
                 "steps": args.pair_steps, "warmup": 1, "phases_ms_per_step": ph,
                 "step2_ms": round(s2, 3), "step2_speedup_vs_fp64": round(s2_64 / s2, 3),
                 "fp64_bracket_output_rel_diff": diff64, "clocks": clk_p,
@@ -290,7 +298,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(args.steps):
             e2e_step()
         t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
-        e2e = {"value": units_per_step * ws / t_e2e / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_rate(units_per_step, ws, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in Xh) + N * 8),
                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in Oh)),
                "chunks": len(cols), "chunk_columns": cw,
@@ -603,7 +611,7 @@ def run_batch(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
-    value = units * ws / (ms / 1e3) / 1e9
+    value = whole_job_rate(units, ws, ms)
     tun = [batch.tuning(i) for i in range(len(fes))]
     # the same instances one after another through paw_cheb_filter (no graph, no concurrency)
     for (X, lam, m, bd, out), fe in zip(probs, fes):
@@ -628,7 +636,7 @@ def run_batch(args, ws, rank, local):
                 Oh.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
         t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
-        e2e = {"value": units * ws / t_e2e / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_rate(units, ws, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(h[0].numel() * 8 for h in hosts)),
                "d2h_bytes_per_step": int(sum(h[1].numel() * 8 for h in hosts))}
     res = {
