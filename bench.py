@@ -467,8 +467,8 @@ def sf_flops_per_cell_vec(n1):
     lines = n1 * n1
     fl = 0
     fl += lines * (split(n1) + 2 * 2 * eo(n1, n1) + 2 * outs(n1))                  # P, Q
-    fl += lines * (2 * split(n1) + 3 * 2 * eo(n1, n1) + n1 * (2 + 1 + 2))        # S, R
-    fl += lines * (2 * split(n1) + 2 * 2 * eo(n1, n1) + n1 * (2 + 2))            # y
+    fl += lines * (2 * split(n1) + 3 * 2 * eo(n1, n1) + 2 * n1 + 2 * outs(n1))  # S, R (R = kf T + c S on the halves)
+    fl += lines * (2 * split(n1) + 2 * 2 * eo(n1, n1) + outs(n1))                # y (one accumulator)
     fl += n1 * n1 * (split(n1) + 2 * eo(q1, n1) + outs(q1))                      # U1
     fl += q1 * n1 * (split(n1) + 2 * eo(q1, n1) + outs(q1))                      # U2
     fl += q1 * q1 * (split(n1) + 2 * eo(q1, n1) + outs(q1) + q1)                 # U3 (times w V)

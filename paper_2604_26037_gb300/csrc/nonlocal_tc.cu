@@ -551,9 +551,9 @@ struct ProjStream {
 // gathered by the transposer threads straight from global memory; the node
 // rows the output stage reads (R_Y, R_X, Y hi/lo, or X, or Y) are prefetched
 // 16 rows at a time into a four-deep staging ring with TMA row gathers
-// (tile::gather4 from one tensor map per array), together with the rows'
-// M_D^-1 and DoF indices (owner order, bulk copies), so the epilogue warps
-// only read shared memory and store.
+// (tile::gather4 from one tensor map per array); the epilogue warps read the
+// rows' M_D^-1 and DoF indices (owner order) from global memory before they
+// wait for a group, then read shared memory and store.
 //   warp 0      B loader (one bulk copy per K-chunk)
 //   warp 1      MMA (lane 0), TMEM allocation
 //   warps 2..5  A gather (thread = vector row)

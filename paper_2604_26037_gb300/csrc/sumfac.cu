@@ -15,11 +15,14 @@
 // GB300 has little FP64 throughput, so the FP64 paths (Y = H X - S X Lambda,
 // the FP64 filter form, Rayleigh-Ritz products, residuals) use this form.
 //
-// Block: one cell, VT vectors, SF_THREADS threads; each 1D contraction handles one
-// line (all points along the contracted direction) per thread, in the even/odd
-// split of the centro-symmetric 1D matrices (about 25.7k FP64 operations per
-// cell and vector at p = 6 instead of 35.7k).  Shared-memory tensors are
-// stored [node][vector] so that consecutive threads touch consecutive words.
+// Block: one cell, VT vectors; each 1D contraction handles one line (all
+// points along the contracted direction) per thread, in the even/odd split of
+// the centro-symmetric 1D matrices (about 26.9k FP64 instructions, 45.3k flops,
+// per cell and vector at p = 6 instead of 35.7k instructions).  Terms that
+// share an output line are summed on the halves before the one recombination
+// (the kinetic factor is folded into the tables kD, kM).  Shared-memory
+// tensors are stored [node][vector] so that consecutive threads touch
+// consecutive words.
 #include <type_traits>
 #include <vector>
 
@@ -37,15 +40,16 @@ constexpr int sf_vt() { return NP >= 9 ? 4 : 8; }
 // the FP64 pipe sees twice the warps of a 256-thread block
 constexpr int SF_THREADS = 512;
 // The pair-of-FP32 form issues about 12 FP32 instructions per FP64 FMA, so
-// issue slots, not a pipe, bound it: two blocks of 256 threads (half the
+// issue slots, not a pipe, bound it: several blocks of 256 threads (half the
 // vectors each) per SM, whose gathers, barriers and scatters overlap the
-// contractions of the other (the FP64 form measured 1% slower that way).
+// contractions of the others (the FP64 form measured 1% slower that way).
 template <int NP, typename R>
 constexpr int sf_vt_r() { return std::is_same<R, double>::value ? sf_vt<NP>() : sf_vt<NP>() / 2; }
 template <typename R>
 constexpr int sf_threads() { return std::is_same<R, double>::value ? SF_THREADS : SF_THREADS / 2; }
-template <typename R>
-constexpr int sf_min_blocks() { return std::is_same<R, double>::value ? 1 : 2; }
+// (three blocks up to degree 6: 80 registers without spills; two above)
+template <int NP, typename R>
+constexpr int sf_min_blocks() { return std::is_same<R, double>::value ? 1 : (NP <= 7 ? 3 : 2); }
 
 // Even/odd halves of a centro-symmetric 1D matrix A (m x n, A[m-1-i][n-1-j] = A[i][j]):
 //   Ae[i][j] = (A[i][j] + A[i][n-1-j]) / 2   (j < n/2),  Ae[i][n/2] = A[i][n/2] for odd n,
@@ -65,6 +69,7 @@ using EoMat = EoMatT<double>;
 template <typename R>
 struct SfTablesT {
   EoMatT<R> M, D, phi, phit;   // M, D: np1 x np1; phi: nq1 x np1 (Lagrange at Gauss points); phit = phi^T
+  EoMatT<R> kD, kM;            // kf D and kf M, kf = cK (h/4) of the call (the kinetic factor folded in)
   double kfac, mfac;
 };
 using SfTables = SfTablesT<double>;
@@ -127,7 +132,7 @@ struct Half {
 };
 
 template <int NP, typename R>
-__global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<R>()) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
+__global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<NP, R>()) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
                                                   const R *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
                                                   const double *__restrict__ X, int ldx, double *__restrict__ Y,
                                                   int ldy, int ncols, double alpha, double cK, double cV,
@@ -180,7 +185,6 @@ __global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<R>()) k_local_s
   }
   __syncthreads();
   const double mf = st.mfac;
-  const R kf = A::from(cK * st.kfac);
   // c-contractions, one (a, b) line per thread: P = M_c x, Q = D_c x
   for (int idx = tid; idx < NP * NP * VT; idx += NT) {
     const int ab = idx / VT, v = idx - ab * VT;
@@ -197,7 +201,8 @@ __global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<R>()) k_local_s
     }
   }
   __syncthreads();
-  // b-contractions, one (a, c) line per thread: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S
+  // b-contractions, one (a, c) line per thread: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S,
+  // R formed on the even/odd halves (kf folded into the tables kD, kM)
   for (int idx = tid; idx < NP * NP * VT; idx += NT) {
     const int ac = idx / VT, v = idx - ac * VT;
     const int a = ac % NP, c = ac / NP;
@@ -208,30 +213,32 @@ __global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<R>()) k_local_s
     S.zero();
     T.zero();
     eo_acc<NP, NP, R>(st.M, p, S.E, S.O);
-    eo_acc<NP, NP, R>(st.D, p, T.E, T.O);
-    eo_acc<NP, NP, R>(st.M, q, T.E, T.O);
+    eo_acc<NP, NP, R>(st.kD, p, T.E, T.O);
+    eo_acc<NP, NP, R>(st.kM, q, T.E, T.O);
     const R cmv = A::from((cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0)) * mf);
 #pragma unroll
+    for (int i = 0; i < (NP + 1) / 2; ++i) T.E[i] = A::fma(cmv, A::norm(S.E[i]), T.E[i]);
+#pragma unroll
+    for (int i = 0; i < NP / 2; ++i) T.O[i] = A::fma(cmv, A::norm(S.O[i]), T.O[i]);
+#pragma unroll
     for (int b2 = 0; b2 < NP; ++b2) {
-      const R sv = S.out(b2);
-      A3[base + b2 * NP * VT] = sv;
-      A4[base + b2 * NP * VT] = A::norm(A::fma(kf, T.out(b2), A::mul(cmv, sv)));
+      A3[base + b2 * NP * VT] = S.out(b2);
+      A4[base + b2 * NP * VT] = T.out(b2);
     }
   }
   __syncthreads();
-  // a-contractions, one (b, c) line per thread: y = kf D_a S + M_a R
+  // a-contractions, one (b, c) line per thread: y = kf D_a S + M_a R (one accumulator)
   for (int idx = tid; idx < NP * NP * VT; idx += NT) {
     const int bc = idx / VT, v = idx - bc * VT;
     const int base = bc * NP * VT + v;
     const Split<NP, R> sl = split_line<NP, R>(A3 + base, VT);
     const Split<NP, R> rl = split_line<NP, R>(A4 + base, VT);
-    Half<NP, R> YD, YM;
-    YD.zero();
-    YM.zero();
-    eo_acc<NP, NP, R>(st.D, sl, YD.E, YD.O);
-    eo_acc<NP, NP, R>(st.M, rl, YM.E, YM.O);
+    Half<NP, R> Yl;
+    Yl.zero();
+    eo_acc<NP, NP, R>(st.kD, sl, Yl.E, Yl.O);
+    eo_acc<NP, NP, R>(st.M, rl, Yl.E, Yl.O);
 #pragma unroll
-    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = A::norm(A::fma(kf, YD.out(a2), YM.out(a2)));
+    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = Yl.out(a2);
   }
   if (doV) {
     __syncthreads();
@@ -569,6 +576,14 @@ void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int 
   const double hh = c->h / 2.0;
   t.kfac = 0.5 * hh;
   t.mfac = hh * hh * hh;
+  {
+    const double kf = cK * t.kfac;
+    std::vector<double> kD(c->D1), kM(c->M1);
+    for (double &x : kD) x *= kf;
+    for (double &x : kM) x *= kf;
+    eo_halves(kD.data(), np1, np1, t.kD);
+    eo_halves(kM.data(), np1, np1, t.kM);
+  }
   // w_q V_q per cell (rebuilt lazily after a potential change)
   const size_t nwv = (size_t)c->ncells * c->nq;
   if (!c->wV_valid) {
@@ -594,6 +609,8 @@ void local_sf(paw_context *c, const double *X, int ldx, double *Y, int ldy, int 
   tp.D = pair_table(t.D);
   tp.phi = pair_table(t.phi);
   tp.phit = pair_table(t.phit);
+  tp.kD = pair_table(t.kD);
+  tp.kM = pair_table(t.kM);
   tp.kfac = t.kfac;
   tp.mfac = t.mfac;
   dispatch_sf<f32x2>(c, tp, c->wVx2.as<f32x2>(), X, ldx, Y, ldy, ncols, alpha, cK, cV, cM, cMcol, s);
