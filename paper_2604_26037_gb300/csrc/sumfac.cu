@@ -42,7 +42,8 @@ constexpr int SF_THREADS = 512;
 // The pair-of-FP32 form issues about 12 FP32 instructions per FP64 FMA, so
 // issue slots, not a pipe, bound it: several blocks of 256 threads (half the
 // vectors each) per SM, whose gathers, barriers and scatters overlap the
-// contractions of the others (the FP64 form measured 1% slower that way).
+// contractions of the others (the FP64 form measured 1-1.5% slower with two or
+// three such blocks than with one block of 512 threads).
 template <int NP, typename R>
 constexpr int sf_vt_r() { return std::is_same<R, double>::value ? sf_vt<NP>() : sf_vt<NP>() / 2; }
 template <typename R>
