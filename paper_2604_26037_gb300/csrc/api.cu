@@ -106,20 +106,47 @@ void DevBuf::release(int64_t *counter) {
 // ============================================================== filter kernels
 // R_Y = (zeta_1/e) Y, R_X = 0 (Algorithm 2 step 3).  For the FP32 recurrence Y is
 // also split into two FP32 words hi + lo (lo omitted when Y is kept in FP32 only).
+// y = hi + lo with hi = y truncated to 24 significant bits and lo = y - hi (29
+// bits, exact) rounded to FP32, by integer operations on the FP64 bit pattern:
+// the FP64 pipe (which also carries the FP64 <-> FP32 conversions) runs at 1/64
+// of the FP32 rate on GB300 and would bound this pass.  Exponents outside
+// [2^-74, 2^127) (zero, tiny, huge, Inf/NaN) take the conversions.
+__device__ __forceinline__ void split_hi_lo(double y, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const int e = (int)((b >> 52) & 0x7ffull);
+  if (e < 949 || e > 1150) {
+    hi = (float)y;
+    lo = (float)(y - (double)hi);
+    return;
+  }
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned int hb = sign | ((unsigned int)(e - 896) << 23) | (unsigned int)((b >> 29) & 0x7fffffull);
+  hi = __uint_as_float(hb);
+  const float r = __uint2float_rn((unsigned int)(b & 0x1fffffffull));   // low 29 fraction bits
+  const float scale = __uint_as_float((unsigned int)(e - 948) << 23);   // 2^(e - 1075)
+  lo = __uint_as_float(__float_as_uint(__fmul_rn(r, scale)) | sign);
+}
+
 template <typename TR>
 __global__ void k_cheb_init(int64_t rows, int ncols, const double *__restrict__ Y0, int ldy,
-                            double s, TR *__restrict__ RY, TR *__restrict__ RX, int ldr,
-                            float *__restrict__ Yhi, float *__restrict__ Ylo) {
+                            double s, float s_hi, float s_lo, TR *__restrict__ RY, TR *__restrict__ RX,
+                            int ldr, float *__restrict__ Yhi, float *__restrict__ Ylo) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
   const int v = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= rows || v >= ncols) return;
   const double y = Y0[i * ldy + v];
-  RY[i * ldr + v] = (TR)(s * y);
   RX[i * ldr + v] = TR(0);
-  if (Yhi) {
-    const float h = (float)y;
-    Yhi[i * ldr + v] = h;
-    if (Ylo) Ylo[i * ldr + v] = (float)(y - (double)h);
+  if constexpr (sizeof(TR) == 8) {
+    RY[i * ldr + v] = (TR)(s * y);
+  } else {
+    float h, l;
+    split_hi_lo(y, h, l);
+    // s y to within an FP32 ulp: s_hi h + (s_hi l + s_lo h)
+    RY[i * ldr + v] = fmaf(s_hi, h, fmaf(s_hi, l, s_lo * h));
+    if (Yhi) {
+      Yhi[i * ldr + v] = h;
+      if (Ylo) Ylo[i * ldr + v] = l;
+    }
   }
 }
 
@@ -334,7 +361,9 @@ static void cheb_block_issue(paw_context *c, paw_precision prec, const double *X
   const dim3 blk(32, 8);
   {
     PhaseScope ps(c, 1, s);
-    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, 1.0 / (a0 - cc), RY, RX, ldr, Yhi, Ylo);
+    const double sc = 1.0 / (a0 - cc);
+    const float sc_hi = (float)sc, sc_lo = (float)(sc - (double)sc_hi);
+    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, sc, sc_hi, sc_lo, RY, RX, ldr, Yhi, Ylo);
     PAW_LAUNCH_CHECK("k_cheb_init");
   }
   const TR *mdinv = mdinv_of<TR>(c);
