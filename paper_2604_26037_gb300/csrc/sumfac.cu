@@ -132,6 +132,8 @@ struct Half {
   }
 };
 
+// cK reaches the kernel folded into tab.kD and tab.kM (the host scales the tables);
+// the parameter stays in the launch signature for the call sites.
 template <int NP, typename R>
 __global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<NP, R>()) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
                                                   const R *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
