@@ -429,9 +429,8 @@ PHASE_KERNELS = {
 # (dram__bytes_read.sum + dram__bytes_write.sum, single pass) of a full 256-vector launch on the
 # 884,736-DoF workload with the kernels of this version; a launch of another size is scaled by its
 # DoF.vectors.  Keyed by (phase, precision); None = the same kernel in every precision.
+# (the FP64 step-2 kernels changed after their capture: no entry, traffic reported as null)
 MEASURED_TRAFFIC = {
-    ("residual_local", None): (39.38, "k_local_sf"),
-    ("residual_nonlocal", None): (13.09 + 17.37, "k_own_project64 + k_own_expand64"),
     ("cell_products", "tf32"): (23.17, "k_tc_stream<CellStream>"),
     ("recurrence", "tf32"): (25.60, "k_exp_stream<2>"),
     ("projection", "tf32"): (5.584, "k_tc_stream<ProjStream>"),
