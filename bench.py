@@ -556,18 +556,20 @@ def run_reference(args, ws, rank):
         return None
     cfg = inputs.CONFIGS[args.workload]
     ncols, m = 1, 3
-    vals = []
+    vals, dts = [], []
     for _ in range(args.warmup):
         oracle_sample(args.workload, ncols, m)
     for _ in range(args.steps):
         u, dt = oracle_sample(args.workload, ncols, m)
         vals.append(u / dt / 1e9)
+        dts.append(dt)
     v = statistics.median(vals)
     cb = {"value": v, "unit": UNIT, "cores": _threads(), "kind": "oracle",
           "sample": f"{args.workload}: {ncols} vector, Chebyshev degree {m} per step (Algorithm 2, FP64 "
                     f"numpy/scipy); operator set-up excluded"}
     return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.median(dts) * 1e3, 3),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": {"workload": args.workload, "precision": "fp64", "parallelism": "cpu"},
             "cpu_baseline": cb, "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
