@@ -119,6 +119,16 @@ def _max_over_ranks(x, ws):
     return float(t.item())
 
 
+def workload_desc(name):
+    """The workload as named in the config of both arms' JSON lines."""
+    cfg = inputs.CONFIGS[name]
+    sysd = inputs.make_system(name)
+    M = (cfg["ncell"] * cfg["p"]) ** 3
+    return (f"{name}: L={sysd['L']} bohr, {cfg['ncell']}^3 cells, p={cfg['p']}, M={M} DoFs, "
+            f"{sysd['natoms']} atoms x {sysd['nproj']} projectors, N={cfg['nvec']} in blocks of {cfg['block']}, "
+            f"degree {cfg['degree']}")
+
+
 def whole_job_rate(units_per_step_per_rank, ws, ms_per_step):
     """GDoF.vec/s of the whole job: every replica processes units_per_step_per_rank per step
     and the step takes ms_per_step on the slowest one (weak scaling)."""
@@ -381,9 +391,7 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"tf32": "tf32", "fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.prec],
         "data": "synthetic (seeded), inputs resident in HBM and larger than L2",
-        "config": {"workload": f"{args.workload}: L={sysd['L']} bohr, {cfg['ncell']}^3 cells, p={cfg['p']}, "
-                               f"M={M} DoFs, {sysd['natoms']} atoms x {sysd['nproj']} projectors, "
-                               f"N={N} in blocks of {cfg['block']}, degree {m}",
+        "config": {"workload": workload_desc(args.workload),
                    "precision": args.prec, "y0_storage": "fp32" if args.y0_fp32 else "fp64",
                    "step2_arithmetic": "pair-of-FP32" if args.y0_pair32 else "fp64",
                    **({"kpoint_per_bohr": list(kp), "vectors": "complex (real blocks of 2 B columns inside)"}
@@ -571,7 +579,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.median(dts) * 1e3, 3),
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": args.workload, "precision": "fp64", "parallelism": "cpu"},
+            "config": {"workload": workload_desc(args.workload), "precision": "fp64", "parallelism": "cpu"},
             "cpu_baseline": cb, "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 
