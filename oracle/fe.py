@@ -200,7 +200,11 @@ def gaussian_potential(pts: np.ndarray, L: float, centers, depth, width,
                        image_cut: float = 8.0) -> np.ndarray:
     """V(x) = -sum_atoms sum_images A exp(-|x - R - L n|^2 / (2 w^2)).
 
-    Images within image_cut * w of x contribute (synthetic local potential).
+    Images within image_cut * w of x contribute (synthetic local potential;
+    w is the standard deviation of the Gaussian).  Pinned by
+    test_oracle_fe::test_gaussian_potential_values (values at the centre, at
+    w and at the cut, wrap-around) and ::test_gaussian_potential_*_poisson
+    (both branches against the Poisson-summed periodic Gaussian).
     """
     pts = np.asarray(pts)
     V = np.zeros(pts.shape[:-1])

@@ -74,14 +74,33 @@ def dense_eigs(ops, nev: int):
 
 
 def subspace_angles_S(S_apply, U, V):
-    """Principal angles between span(U) and span(V) in the S inner product."""
+    """Principal angles between span(U) and span(V) in the S inner product.
+
+    Both bases are made S-orthonormal (Cholesky of their S-Gram matrices).
+    The cosines are the singular values of U_o^T S V_o; the sines are the
+    S-norms of the part of V_o that is S-orthogonal to span(U_o), i.e. the
+    square roots of the eigenvalues of R^T S R with R = V_o - U_o (U_o^T S V_o).
+    Angles below pi/4 are taken from the sines and the others from the cosines:
+    arccos of a cosine near 1 resolves an angle t only to about eps / t, the
+    sine keeps its relative accuracy (Knyazev and Argentati, SIAM J. Sci.
+    Comput. 23 (2002)).  Returns min(dim U, dim V) angles in ascending order.
+    Pinned by test_oracle_rr::test_subspace_angles_* (same span, S-orthogonal
+    spans, constructed spans with known angles).
+    """
     def orth(A):
         G = A.T @ S_apply(A)
         L = np.linalg.cholesky(0.5 * (G + G.T))
         return np.linalg.solve(L, A.T).T
     Uo, Vo = orth(U), orth(V)
-    s = np.linalg.svd(Uo.T @ S_apply(Vo), compute_uv=False)
-    return np.arccos(np.clip(s, -1.0, 1.0))
+    if Vo.shape[1] > Uo.shape[1]:
+        Uo, Vo = Vo, Uo
+    C = Uo.T @ S_apply(Vo)
+    cos = np.sort(np.clip(np.linalg.svd(C, compute_uv=False), 0.0, 1.0))[::-1]   # ascending angles
+    R = Vo - Uo @ C
+    G = R.T @ S_apply(R)
+    sin = np.sqrt(np.clip(np.sort(np.linalg.eigvalsh(0.5 * (G + G.T))), 0.0, 1.0))
+    small = sin < np.sqrt(0.5)
+    return np.where(small, np.arcsin(sin), np.arccos(cos))
 
 
 def rchfsi(ops, X0, m: int, iters: int, nwanted: int, sinv="approx", history=None):

@@ -197,3 +197,75 @@ def test_mesh_dof_map():
     org = m.cell_xyz[e] * m.h
     rel = np.mod(loc - org + 1e-12, m.L) - 1e-12
     assert rel.min() >= -1e-12 and rel.max() <= m.h + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Synthetic local potential (reading of the configs: V = -sum A exp(-r^2 / (2 w^2))
+# over periodic images within 8 w).  Pinned by values fixed by that definition and by
+# the Poisson-summation closed form of the fully periodic Gaussian, which the oracle
+# does not compute: sum_n exp(-(x - n L)^2 / (2 w^2))
+#   = (w sqrt(2 pi) / L) [1 + 2 sum_{k>=1} exp(-2 pi^2 k^2 w^2 / L^2) cos(2 pi k x / L)].
+# ---------------------------------------------------------------------------
+def _theta_periodic(x, L, w, kmax=200):
+    k = np.arange(1, kmax + 1)
+    terms = np.exp(-2.0 * math.pi ** 2 * (k * w / L) ** 2)[None, :] * np.cos(2.0 * math.pi * np.outer(x, k) / L)
+    return (w * math.sqrt(2.0 * math.pi) / L) * (1.0 + 2.0 * terms.sum(1))
+
+
+def _poisson_potential(pts, L, centers, depth, width):
+    V = np.zeros(len(pts))
+    for R, A, w in zip(centers, depth, width):
+        d = pts - np.asarray(R)
+        V -= A * _theta_periodic(d[:, 0], L, w) * _theta_periodic(d[:, 1], L, w) * _theta_periodic(d[:, 2], L, w)
+    return V
+
+
+def test_gaussian_potential_values():
+    """V at the centre is -A, at distance w it is -A e^{-1/2} (w is the standard deviation,
+    not the 1/e radius), at 7.9 w it is -A e^{-7.9^2/2}, and beyond the 8 w image cut it is 0;
+    the minimum image wraps across the box."""
+    L, A, w = 40.0, 2.0, 1.0
+    R = np.array([3.0, 20.0, 17.5])
+    ex = np.array([1.0, 0.0, 0.0])
+    pts = np.array([R, R + w * ex, R + 7.9 * w * ex, R + 8.1 * w * ex, R - w * ex + [L, 0.0, 0.0],
+                    R + [0.0, L - w, 0.0], R + [0.0, 0.0, L]])
+    V = fe.gaussian_potential(pts, L, [R], [A], [w])
+    np.testing.assert_allclose(V[0], -A, rtol=1e-15)
+    np.testing.assert_allclose(V[1], -A * math.exp(-0.5), rtol=1e-14)
+    np.testing.assert_allclose(V[2], -A * math.exp(-7.9 ** 2 / 2), rtol=1e-12)
+    assert V[3] == 0.0
+    np.testing.assert_allclose(V[4:6], -A * math.exp(-0.5), rtol=1e-14)   # wrap by L, and by L - w
+    np.testing.assert_allclose(V[6], -A, rtol=1e-15)                        # a lattice translate of the centre
+    # superposition of two centres with their own depth and width
+    R2, A2, w2 = np.array([5.0, 21.0, 17.5]), 1.5, 0.7
+    V2 = fe.gaussian_potential(pts[:2], L, [R, R2], [A, A2], [w, w2])
+    d2 = np.sum((pts[:2] - R2) ** 2, 1)
+    np.testing.assert_allclose(V2, V[:2] - A2 * np.exp(-d2 / (2 * w2 * w2)), rtol=1e-14)
+
+
+@pytest.mark.parametrize("L,cut", [(3.0, 12.0), (4.5, 12.0)])
+def test_gaussian_potential_images_poisson(L, cut):
+    """Image-sum branch (cut radius above L/2): with a cut far out in the tail the oracle's
+    sum over periodic images equals the Poisson-summed closed form."""
+    rng = np.random.default_rng(5)
+    centers = rng.uniform(0, L, (2, 3))
+    depth, width = [2.0, 1.3], [1.0, 0.8]
+    assert cut * min(width) >= L / 2
+    pts = rng.uniform(0, L, (40, 3))
+    V = fe.gaussian_potential(pts, L, centers, depth, width, image_cut=cut)
+    ref = _poisson_potential(pts, L, centers, depth, width)
+    np.testing.assert_allclose(V, ref, rtol=1e-12, atol=0)
+
+
+def test_gaussian_potential_minimum_image_poisson():
+    """Minimum-image branch (the configs' boxes): the 8 w cut drops only the tail beyond 8 w,
+    below A e^{-32}, so V agrees with the full periodic sum to 1e-12 A everywhere."""
+    L = 40.0
+    rng = np.random.default_rng(6)
+    centers = rng.uniform(0, L, (3, 3))
+    depth, width = [2.0, 2.0, 1.0], [1.0, 0.9, 1.2]
+    pts = np.concatenate([centers + rng.normal(0, 1.5, (3, 3)), rng.uniform(0, L, (60, 3))])
+    V = fe.gaussian_potential(pts, L, centers, depth, width)
+    ref = _poisson_potential(pts, L, centers, depth, width)
+    np.testing.assert_allclose(V, ref, rtol=0, atol=1e-12 * max(depth))
+    assert np.abs(V).max() > 0.1      # the sample reaches the wells
