@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -45,6 +46,14 @@ def _peaks():
                     bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
     except Exception:
         return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+def _n_sm():
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        return 152
 
 
 class ClockSampler:
@@ -172,11 +181,149 @@ def _threads():
         return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def cpu_info():
+    """CPU model, online core count and architecture of the host that runs the oracle."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    nproc = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": nproc,
+            "arch": platform.machine(), "blas_threads": _threads()}
+
+
+def _timed_cpu(fn):
+    """(result, wall seconds, threads actually used = process CPU time / wall time)."""
+    c0, t0 = time.process_time(), time.perf_counter()
+    r = fn()
+    dt = time.perf_counter() - t0
+    return r, dt, (time.process_time() - c0) / max(dt, 1e-9)
+
+
+def tiny_full_oracle():
+    """Config 1 timed in full: the oracle's R-ChFSI on the tiny workload (16 vectors, Chebyshev
+    degree 20, 10 iterations of Algorithm 2 + Rayleigh-Ritz), FP64 numpy/scipy."""
+    from oracle import cheb, rr
+    from oracle import ops as O
+    cfg = inputs.CONFIGS["tiny"]
+    op = O.PawOperators(inputs.make_system("tiny"))
+    X0 = inputs.start_columns("tiny", range(cfg["nvec"]))
+    tmin, bU = rr.lanczos_bounds(lambda x: op.apply_Sinv_exact(op.apply_H(x)), op.apply_S, op.mesh.ndof)
+    Psi, lam = rr.rayleigh_ritz(op, X0)
+    t_cf = 0.0
+    c0, t0 = time.process_time(), time.perf_counter()
+    for _ in range(cfg["iters"]):
+        a = time.perf_counter()
+        Xf = cheb.rchfsi_filter(op.apply_H, op.apply_S, op.apply_Sinv_approx, Psi, lam, cfg["degree"],
+                                min(lam[0], tmin), lam[-1], bU)
+        t_cf += time.perf_counter() - a
+        Psi, lam = rr.rayleigh_ritz(op, Xf)
+    dt = time.perf_counter() - t0
+    units = float(op.mesh.ndof) * cfg["nvec"] * cfg["degree"] * cfg["iters"]
+    return {"value": units / t_cf / 1e9, "unit": UNIT, "filter_s": round(t_cf, 3), "rchfsi_s": round(dt, 3),
+            "threads_used": round((time.process_time() - c0) / max(dt, 1e-9), 2),
+            "workload": f"tiny in full: {op.mesh.ndof} DoFs, {cfg['nvec']} vectors, degree {cfg['degree']}, "
+                        f"{cfg['iters']} R-ChFSI iterations (filter time only in value)"}
+
+
 def cpu_baseline(workload, ncols=2, m=8):
-    units, dt = oracle_sample(workload, ncols, m)
-    return {"value": units / dt / 1e9, "unit": UNIT, "cores": _threads(), "kind": "oracle",
-            "sample": f"{workload}: {ncols} vectors, Chebyshev degree {m} (Algorithm 2, FP64 numpy/scipy), "
-                      f"{dt:.1f} s; operator set-up excluded"}
+    (units, dt), _, used = _timed_cpu(lambda: oracle_sample(workload, ncols, m))
+    info = cpu_info()
+    out = {"value": units / dt / 1e9, "unit": UNIT, "cores": round(used, 2), "kind": "oracle",
+           "sample": f"{workload}: {ncols} vectors, Chebyshev degree {m} (Algorithm 2, FP64 numpy/scipy), "
+                     f"{dt:.1f} s; operator set-up excluded; cores = process CPU time / wall time",
+           **info}
+    try:
+        out["tiny_full"] = tiny_full_oracle()
+    except Exception as ex:   # the sample above is the baseline; this is context
+        out["tiny_full"] = {"error": str(ex)[:200]}
+    return out
+
+
+# ----------------------------------------------------------------------------- accuracy
+def gap_index(lam, k0, gap_min=1e-4):
+    """The state count nearest to k0 whose gap lam[k] - lam[k-1] exceeds gap_min (Ha), so
+    that a (near-)degenerate level is never split between compared and uncompared states."""
+    n = len(lam)
+    for d in range(n):
+        for k in (k0 - d, k0 + d):
+            if 1 <= k < n and lam[k] - lam[k - 1] > gap_min:
+                return k
+    return n
+
+
+def s_angles(fe, A, B):
+    """Principal angles between span(A) and span(B) (S-orthonormal blocks) in the S inner
+    product; angles below pi/4 from their sines, the others from their cosines."""
+    import torch
+    SB = fe.apply_S(B)
+    C = A.T @ SB
+    cos = torch.linalg.svdvals(C).clamp(0.0, 1.0).flip(0)          # ascending angles
+    R = B - A @ C                                                   # part of span(B) S-orthogonal to span(A)
+    G = R.T @ fe.apply_S(R)
+    sin = torch.linalg.eigvalsh(0.5 * (G + G.T)).clamp(0.0, 1.0).sqrt()
+    ang = torch.where(sin < 0.5 ** 0.5, torch.asin(sin), torch.acos(cos))
+    return ang.cpu().numpy()
+
+
+def accuracy_leg(fe, X0, lam0, tmin, bU, m, iters, prec, k_target):
+    """R-ChFSI (Algorithm 1 with Algorithm 2 as the filter) from one S-orthonormal start, the
+    same number of iterations with the mixed-precision filter and with the FP64 filter (both
+    with the FP64 Rayleigh-Ritz step); the lowest k states compared.  The FP64 arm's filter
+    calls are timed on the stream (CUDA events) and give the FP64 form's throughput."""
+    import torch
+    stream = torch.cuda.current_stream()
+    runs = {}
+    for arm in (prec, "fp64"):
+        X = X0.clone()
+        lam = lam0.copy()
+        out = torch.empty_like(X)
+        ms = []
+        for _ in range(iters):
+            bounds = (min(lam[0], tmin), float(lam[-1]), bU)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fe.cheb_filter(X, lam, m, bounds, prec=arm, out=out)
+            e1.record(stream)
+            X, out = out, X
+            lam = fe.rayleigh_ritz(X)                  # synchronises
+            fe.sync_status()
+            ms.append(e0.elapsed_time(e1))
+        del out
+        runs[arm] = (X, lam, fe.residuals(X, lam), ms)
+    (Xa, la, ra, msa), (Xb, lb, rb, msb) = runs[prec], runs["fp64"]
+    k = gap_index(lb, k_target)
+    ang = s_angles(fe, Xa[:, :k], Xb[:, :k])
+    k2 = gap_index(lb, k_target // 2)
+    ang2 = s_angles(fe, Xa[:, :k2], Xb[:, :k2])
+    res = {"iterations": iters, "degree": m, "start": "Ritz vectors of the random block (FP64 Rayleigh-Ritz)",
+           "states_compared": k, "k_target": k_target, "gap_after_k_ha": float(lb[k] - lb[k - 1]) if k < len(lb) else None,
+           "eigval_err": float(np.abs(la[:k] - lb[:k]).max()), "max_angle": float(ang.max()),
+           "max_residual": {prec: float(ra[:k].max()), "fp64": float(rb[:k].max())},
+           "lowest_half": {"states": k2, "eigval_err": float(np.abs(la[:k2] - lb[:k2]).max()),
+                           "max_angle": float(ang2.max())},
+           "bounds": {"eigval_ha": 1e-6, "angle": 1e-5},
+           "reference": "the same iteration with the FP64 filter on the GPU (checked against the FP64 oracle "
+                        "at this size, tests/test_gpu_fullsize.py)",
+           "filter_ms": {prec: round(statistics.median(msa[1:] or msa), 3), "fp64": round(statistics.median(msb[1:] or msb), 3)}}
+    res["pass"] = bool(res["eigval_err"] <= 1e-6 and res["max_angle"] <= 1e-5)
+    fp64_ms = msb[1:] or msb
+    del runs, Xa, Xb
+    return res, fp64_ms
 
 
 # ----------------------------------------------------------------------------- ours
@@ -223,6 +370,7 @@ def run_ours(args, ws, rank, local):
                 h.cheb_filter(X, lam, m, bounds, prec=prec, out=dst)
             e1.record(stream)
             torch.cuda.synchronize()
+        h.sync_status()                 # a kernel that gave up on a bounded wait fails the run
         prof = h.profile_read() if profile else None
         if profile:
             h.profile_enable(False)
@@ -234,9 +382,18 @@ def run_ours(args, ws, rank, local):
     units_per_step = float(M) * N * m
     value = whole_job_rate(units_per_step, ws, ms)
 
-    # FP64 form of the same filter (the plain method), fewer steps: it is slow on GB300
+    # accuracy at this size: R-ChFSI with the mixed filter vs with the FP64 filter
+    acc = None
     fp64 = None
-    if args.fp64_steps > 0:
+    if args.accuracy_iters > 0 and not kp and args.start == "ritz":
+        acc, ms64s = accuracy_leg(fe, X, lam, tmin, bU, m, args.accuracy_iters, args.prec, N // 2)
+        ms64 = _max_over_ranks(statistics.median(ms64s), ws)
+        fp64 = {"value": whole_job_rate(units_per_step, ws, ms64), "ms_per_step": ms64, "steps": len(ms64s),
+                "warmup": 1, "source": "FP64-filter calls of the accuracy leg (CUDA events on the stream)"}
+        torch.cuda.empty_cache()
+
+    # FP64 form of the same filter (the plain method), fewer steps: it is slow on GB300
+    if fp64 is None and args.fp64_steps > 0:
         ms64, _, _ = timed("fp64", args.fp64_steps, 1)
         fp64 = {"value": whole_job_rate(units_per_step, ws, ms64), "ms_per_step": ms64,
                 "steps": args.fp64_steps, "warmup": 1}
@@ -409,6 +566,8 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
         "bounds": [float(b) for b in bounds],
     }
+    if acc is not None:
+        res["accuracy"] = acc
     if pair is not None:
         res["step2_pair32"] = pair
     if rrm is not None:
@@ -433,17 +592,18 @@ PHASE_KERNELS = {
     "recovery": "Shat^-1 of R_m + FP64 combination",
 }
 
-# DRAM bytes per DoF.vector moved by the main kernel of a phase, read off one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, single pass) of a full 256-vector launch on the
-# 884,736-DoF workload with the kernels of this version; a launch of another size is scaled by its
-# DoF.vectors.  Keyed by (phase, precision); None = the same kernel in every precision.
-# (the FP64 step-2 kernels changed after their capture: no entry, traffic reported as null)
+# DRAM bytes per DoF.vector moved by the main kernel(s) of a phase, read off one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, a single pass) of a full-width launch with the
+# kernels of this version, on the workload named in the entry; a launch of another size is scaled
+# by its DoF.vectors (the traffic of these kernels grows in proportion to it).  Keyed by (phase,
+# precision); None = the same kernels in every precision.  Summaries: profiles/.
 MEASURED_TRAFFIC = {
-    ("cell_products", "tf32"): (23.17, "k_tc_stream<CellStream>"),
-    ("recurrence", "tf32"): (25.60, "k_exp_stream<2>"),
-    ("projection", "tf32"): (5.584, "k_tc_stream<ProjStream>"),
+    ("cell_products", "tf32"): (23.17, "k_tc_stream<CellStream>", "mid"),
+    ("recurrence", "tf32"): (25.60, "k_exp_stream<2>", "mid"),
+    ("projection", "tf32"): (5.584, "k_tc_stream<ProjStream>", "mid"),
+    ("residual_local", None): (31.46, "k_local_sf<7,double>", "prof12"),
+    ("residual_nonlocal", None): (32.32, "k_own_project64<16,double> + k_own_expand64<16,0,double>", "prof12"),
 }
-TRAFFIC_WORKLOAD = "mid"
 
 
 def measured_traffic(phase, prec, units, workload):
@@ -451,8 +611,8 @@ def measured_traffic(phase, prec, units, workload):
     hit = MEASURED_TRAFFIC.get((phase, None)) or MEASURED_TRAFFIC.get((phase, prec))
     if not hit:
         return None, None
-    note = f"ncu capture of {hit[1]} on the {TRAFFIC_WORKLOAD} workload"
-    if workload != TRAFFIC_WORKLOAD:
+    note = f"ncu capture of {hit[1]} on the {hit[2]} workload ({hit[0]} B per DoF.vector)"
+    if workload != hit[2]:
         note += ", scaled by DoF.vectors"
     return round(hit[0] * units), note
 
@@ -522,14 +682,21 @@ def phase_model(phase, fe, cfg, prec):
 
 
 def compute_peak(kind, peaks, sm_mhz):
-    """TFLOP/s ceiling of a compute kind, from the measured bf16 peak or the unit counts."""
+    """(TFLOP/s ceiling, bound, source) of a compute kind: tensor formats from the measured BF16
+    burst (x the nominal dense ratio for TF32); plain ALU arithmetic from the unit counts and the
+    SM clock sampled during the timed region."""
+    nsm = _n_sm()
     if kind == "tf32":
-        return peaks["bf16"] * (1.1 / 2.25), "tensor"          # nominal TF32/BF16 dense ratio
+        return (peaks["bf16"] * (1.1 / 2.25), "tensor",
+                f"{peaks['src']} BF16 burst {peaks['bf16']} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25")
     if kind == "bf16":
-        return peaks["bf16"], "tensor"
+        return peaks["bf16"], "tensor", f"{peaks['src']} BF16 burst"
     if kind == "fp64":
-        return 1.25 * sm_mhz / 2070.0, "alu"                   # GB300 FP64 1.25 TFLOP/s at 2070 MHz
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "alu"          # FP32 FFMA: 152 SMs x 128 lanes x 2
+        # the FP64 pipe retires 2 FMA per SM per clock on GB300 (1.25 TFLOP/s nominal at 2070 MHz)
+        return (nsm * 2 * 2 * sm_mhz * 1e6 / 1e12, "alu",
+                f"derived: {nsm} SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)")
+    return (nsm * 128 * 2 * sm_mhz * 1e6 / 1e12, "alu",
+            f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)")
 
 
 def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks, workload=None):
@@ -538,24 +705,33 @@ def roofline(phase, pinfo, fe, sysd, cfg, prec, peaks, clocks, workload=None):
     flops, byts, kind = phase_model(phase, fe, cfg, prec)
     if flops is None or per_launch_ms <= 0:
         return {"bound": "hbm", "achieved": None, "peak": peaks["hbm"], "unit": "GB/s", "frac": None,
-                "traffic": None, "kernel": phase}
+                "traffic": None, "kernel": phase, "peak_source": f"{peaks['src']} HBM copy bandwidth"}
     sec = per_launch_ms / 1e3
     gbs = byts / sec / 1e9
     traffic, tnote = (measured_traffic(phase, prec, float(fe.ndof) * cfg["block"], workload)
                       if not fe.complex else (None, None))
     tfs = flops / sec / 1e12
     hbm_frac = gbs / peaks["hbm"]
-    sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    cpk, cbound = compute_peak(kind, peaks, sm_mhz)
+    sm_mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    cpk, cbound, csrc = compute_peak(kind, peaks, sm_mhz)
     c_frac = tfs / cpk
     common = {"traffic": traffic, "traffic_source": tnote, "kernel": phase, "kernels": PHASE_KERNELS.get(phase),
               "ms_per_launch": round(per_launch_ms, 4), "algorithmic_bytes_per_launch": byts,
-              "algorithmic_flops_per_launch": flops, "peak_source": peaks["src"]}
+              "algorithmic_flops_per_launch": flops}
     if c_frac >= hbm_frac:
-        return {"bound": cbound, "achieved": round(tfs, 3), "peak": round(cpk, 2), "unit": "TFLOP/s",
-                "frac": round(c_frac, 4), "hbm_frac": round(hbm_frac, 4), "compute": kind, **common}
+        out = {"bound": cbound, "achieved": round(tfs, 3), "peak": round(cpk, 4), "unit": "TFLOP/s",
+               "frac": round(c_frac, 4), "hbm_frac": round(hbm_frac, 4), "compute": kind, "peak_source": csrc,
+               **common}
+        if kind == "fp64":
+            # the same kernel against the other admissible ceiling: the measured BF16 burst x the
+            # nominal FP64/BF16 ratio (1.25 / 2250)
+            alt = peaks["bf16"] * 1.25 / 2250.0
+            out["peak_alt"] = {"peak": round(alt, 4), "frac": round(tfs / alt, 4),
+                               "source": f"{peaks['src']} BF16 burst x nominal FP64/BF16 ratio 1.25/2250"}
+        return out
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm"], "unit": "GB/s",
-            "frac": round(hbm_frac, 4), "compute_frac": round(c_frac, 4), "compute": kind, **common}
+            "frac": round(hbm_frac, 4), "compute_frac": round(c_frac, 4), "compute": kind,
+            "peak_source": f"{peaks['src']} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", **common}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -564,17 +740,19 @@ def run_reference(args, ws, rank):
         return None
     cfg = inputs.CONFIGS[args.workload]
     ncols, m = 1, 3
-    vals, dts = [], []
+    vals, dts, used = [], [], []
     for _ in range(args.warmup):
         oracle_sample(args.workload, ncols, m)
     for _ in range(args.steps):
-        u, dt = oracle_sample(args.workload, ncols, m)
+        (u, dt), _, th = _timed_cpu(lambda: oracle_sample(args.workload, ncols, m))
         vals.append(u / dt / 1e9)
         dts.append(dt)
+        used.append(th)
     v = statistics.median(vals)
-    cb = {"value": v, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+    cb = {"value": v, "unit": UNIT, "cores": round(statistics.median(used), 2), "kind": "oracle",
           "sample": f"{args.workload}: {ncols} vector, Chebyshev degree {m} per step (Algorithm 2, FP64 "
-                    f"numpy/scipy); operator set-up excluded"}
+                    f"numpy/scipy); operator set-up excluded; cores = process CPU time / wall time",
+          **cpu_info()}
     return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.median(dts) * 1e3, 3),
             "higher_is_better": True,
@@ -684,7 +862,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid", choices=sorted(inputs.CONFIGS) + ["batch32"])
     ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "bf16", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed FP64-filter calls when the accuracy leg does not run (it times them itself)")
+    ap.add_argument("--accuracy-iters", type=int, default=16,
+                    help="R-ChFSI iterations of the accuracy leg, mixed vs FP64 filter (0: skip)")
     ap.add_argument("--y0-fp32", action="store_true")
     ap.add_argument("--y0-pair32", action="store_true",
                     help="form step 2 (Y = H X - S X Lambda) in pair-of-FP32 arithmetic in the main measurement")

@@ -23,7 +23,15 @@
  *   eigenvalues, bounds) are HOST arrays, copied or read during the call.
  * - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
  *   void*; NULL = legacy default stream).  Calls that return host results
- *   (eigenvalues, norms, bounds) synchronise that stream.
+ *   (eigenvalues, norms, bounds) synchronise that stream.  paw_cheb_filter
+ *   returns as soon as its work is enqueued.  Consecutive calls on one
+ *   handle share its workspaces: issue them on one stream (or order the
+ *   streams yourself).
+ * - Device-detected failures (a bounded wait of a tensor-core kernel that
+ *   expired: its output is incomplete) are reported as PAW_ERR_TIMEOUT by
+ *   paw_sync_status and by the next call on the handle that synchronises:
+ *   paw_apply_H / paw_apply_Sinv_approx in PAW_TF32 or PAW_BF16,
+ *   paw_rayleigh_ritz, paw_residuals.
  * - The library owns the device memory behind a handle (operator data and
  *   workspaces); it is freed by paw_destroy().  Workspaces grow on demand,
  *   so the first call at a new block width may allocate.
@@ -235,22 +243,30 @@ paw_status paw_apply_Sinv_approx(paw_handle h, paw_precision prec, const void *X
  * sums in it; every value a call reads it has first written itself, so
  * nothing needs clearing, but calls whose GPU work overlaps (different
  * streams, or different handles on one device) race on the array and must be
- * serialised by the caller. */
+ * serialised by the caller.  The lookup is repeated when the current context
+ * of the device changes (after a device reset). */
 #define PAW_NOALLOC_SCRATCH_BYTES (32u << 20)
 paw_status paw_apply_Sinv_approx_noalloc(paw_handle h, paw_precision prec, const void *X,
                                          void *Y, int ncols, int ldx, int ldy, void *stream);
 
 /* Algorithm 2: Psi_f = Shat^-1 R_m + Psi_in C_m(Lambda~) for one or more
- * blocks of columns (processed opts.block columns at a time).
+ * blocks of columns (processed opts.block columns at a time).  Stream-ordered:
+ * the call enqueues every copy and kernel on `stream` and returns without
+ * waiting for them (the per-block scalars travel through pinned host memory
+ * owned by the handle; the host only waits when it is eight blocks ahead of
+ * the GPU).  Read failures with paw_sync_status.
  *   X_in      : device FP64 ndof x ncols (ld ldx), the block Psi_in
  *   lambda_in : host FP64 ncols, the eigenvalue estimates Lambda
  *   degree    : m >= 1 (H applied m times, Shat^-1 applied m times)
  *   X_out     : device FP64 ndof x ncols (ld ldo); may not alias X_in
  * Y = H X - S X Lambda is formed in FP64 (step 2; in PAW_F32X2 arithmetic when
- * options.y0_pair32 is set); for PAW_FP32/TF32/BF16 the
- * recurrence bracket is evaluated in reduced precision, the term
- * (2 zeta/e) Y Lambda_Y is added in FP64 and R is stored in FP32 (Sec. 4.4,
- * mixed precision computation).  Errors: INVALID_ARG (a0 < bW < bU violated,
+ * options.y0_pair32 is set); for PAW_FP32/TF32/BF16 the recurrence bracket
+ * is evaluated in reduced precision and R is stored in FP32 (Sec. 4.4, mixed
+ * precision computation).  The full-precision term (2 zeta/e) Y Lambda_Y is
+ * added to the FP32 bracket by error-free FP32 arithmetic (an exact product
+ * and a two-sum) on a hi + lo split of the FP64 Y (about 48 significant bits;
+ * the lo word is dropped when options.y0_fp32 is set), then rounded once to
+ * FP32; in PAW_FP64 it is an FP64 FMA.  Errors: INVALID_ARG (a0 < bW < bU violated,
  * degree < 1, sizes), NO_MEMORY, CUDA. */
 paw_status paw_cheb_filter(paw_handle h, paw_precision prec, const double *X_in,
                            int ldx, const double *lambda_in, int ncols, int degree,
@@ -332,11 +348,14 @@ paw_status paw_batch_destroy(paw_batch b);
  *   lambda_out : host FP64 N
  * H X and S X are formed block by block (opts.block columns) with the FP64
  * cell kernels; only the lower triangle of H^p and S^p is projected (column
- * block j0 gives rows j0..N-1, cuBLAS DGEMM), the projected problem is solved
- * by cuSOLVER dsygvd.  The rotation is a DGEMM over row chunks, or with
- * opts.rr_mixed = 1: X <- X diag(Q) in FP64 plus fl32(X) (Q - diag(Q)) as an
- * FP32 GEMM (Sec. 4.4: the off-diagonal part of Q is small near convergence).
- * Errors: NOT_SPD (S^p not positive definite), LIBRARY, NO_MEMORY. */
+ * block j0 gives rows j0..N-1; Sec. 4.5 RR-Projection), by the library's own
+ * split-contraction FP64 kernels; the projected problem is solved by cuSOLVER
+ * dsygvd (zhegvd at k != 0).  The rotation is an FP64 GEMM kernel of the
+ * library over row chunks, or with opts.rr_mixed = 1: X <- X diag(Q) in FP64
+ * plus fl32(X) (Q - diag(Q)) with FP32 products and sums (Sec. 4.5 RR-SR: the
+ * off-diagonal part of Q is small near convergence).
+ * Errors: NOT_SPD (S^p not positive definite), LIBRARY, NO_MEMORY, and
+ * TIMEOUT for a failure left by an earlier asynchronous call. */
 paw_status paw_rayleigh_ritz(paw_handle h, double *X, int ld, int N,
                              double *lambda_out, void *stream);
 
@@ -401,8 +420,24 @@ paw_status paw_profile_read(paw_handle h, paw_profile *out);
  * call; PAW_OK if none was raised.  Synchronises the handle's last stream. */
 paw_status paw_sync_status(paw_handle h);
 
+/* Bounded device waits of the persistent tensor-core pipelines (cell products
+ * and projector contractions of PAW_TF32 / PAW_BF16), for launches enqueued
+ * after this call (library engineering; the paper has no counterpart).
+ *   seconds : give-up bound of every pipeline wait, 1e-3 .. 60 (default 2)
+ *   probe   : 1 makes every such launch first wait on a device word that
+ *             nothing writes, before it issues any copy or MMA: the wait runs
+ *             out after `seconds`, the launch gives up, and the call that
+ *             reports device failures returns PAW_ERR_TIMEOUT.  This exercises
+ *             the failure path without faulting anything; 0 (default) off.
+ * The waits that let copies and MMAs already in flight finish before a CTA
+ * exits keep their fixed 2 s bound.  Graphs captured by paw_batch_* keep the
+ * setting they were captured with.  Errors: INVALID_ARG. */
+paw_status paw_set_wait_limit(paw_handle h, double seconds, int probe);
+
 paw_status paw_destroy(paw_handle h);
 
+/* Message of the last failing call made by the calling thread (thread-local
+ * rather than per handle: a handle is used by one thread at a time). */
 const char *paw_last_error(void);
 
 /* Library version string (static storage). */

@@ -155,12 +155,12 @@ def batch_systems(count: int = 32, n_range=(4, 12), degrees=(4, 5, 6), atoms_ran
     Instance i: n ~ U{n_range}, L = 2.5 n, p ~ U(degrees), the five projector
     shells of the mid workload (13 projectors), B ~ U(widths) vectors, filter
     degree `degree`.  Atoms are placed uniformly with a minimum periodic
-    separation of 2.5 bohr.  Two caps keep every instance valid for the
-    discretisation: the shell widths are scaled by min(1, 0.45 L / r_c,max)
-    so that every cutoff radius stays below L/2 (minimum image), and the atom
-    count is drawn up to min(atoms_range[1], L^3 / 40, 40 / f) with f the
-    fraction of the box within reach of one atom's projectors (so that at
-    most about 40 atoms touch one cell).
+    separation of 2.5 bohr; their count is drawn from atoms_range.  Two
+    geometric caps keep every instance valid: the shell widths are scaled by
+    min(1, 0.45 L / r_c,max) so that every cutoff radius stays below L/2
+    (minimum image), and the atom count is at most L^3 / 30 (spheres of the
+    minimum separation fill 27% of the box, below the 38% at which random
+    sequential placement jams; only the 10 bohr boxes are capped, at 33).
     """
     rng = _rng(99, 0, seed=seed)
     out = []
@@ -171,18 +171,12 @@ def batch_systems(count: int = 32, n_range=(4, 12), degrees=(4, 5, 6), atoms_ran
         rc_max = max(w for _, w in BASE_SHELLS) * _TRUNC
         scale = min(1.0, 0.45 * L / rc_max)
         shells = [(l, w * scale) for l, w in BASE_SHELLS]
-        reach = 4.0 / 3.0 * np.pi * (rc_max * scale + 2.5 * np.sqrt(3.0) / 2.0) ** 3 / L ** 3
-        cap = int(min(atoms_range[1], L ** 3 / 40.0, 40.0 / min(1.0, reach)))
+        cap = int(min(atoms_range[1], L ** 3 / 30.0))
         natoms = int(rng.integers(atoms_range[0], max(atoms_range[0], cap) + 1))
         B = int(rng.choice(np.asarray(widths)))
-        while True:
-            cfg = dict(index=100 + i, L=L, ncell=n, p=p, natoms=natoms, shells=shells, lattice=None,
-                       min_sep=2.5, nvec=B, block=B, degree=degree, iters=1, nwanted=B)
-            sysd = _build(cfg, f"batch{i}", seed)
-            if natoms <= 2 or _atoms_per_cell(sysd["positions"], L, n, rc_max * scale) <= 40:
-                break
-            natoms -= 2
-        out.append(sysd)
+        cfg = dict(index=100 + i, L=L, ncell=n, p=p, natoms=natoms, shells=shells, lattice=None,
+                   min_sep=2.5, nvec=B, block=B, degree=degree, iters=1, nwanted=B)
+        out.append(_build(cfg, f"batch{i}", seed))
     return out
 
 

@@ -120,6 +120,7 @@ SIGNATURES = {
     "paw_profile_enable": [_VP, _I],
     "paw_profile_read": [_VP, C.c_void_p],
     "paw_sync_status": [_VP],
+    "paw_set_wait_limit": [_VP, _D, _I],
     "paw_destroy": [_VP],
     "paw_last_error": [],
     "paw_version": [],
@@ -256,7 +257,14 @@ class PawFE:
         return {k: getattr(info, k) for k, _ in _Info._fields_}
 
     def sync_status(self):
+        """Raise PawError (PAW_ERR_TIMEOUT) if a kernel of an earlier, asynchronous call
+        (cheb_filter) gave up on a bounded wait; synchronises the handle's stream."""
         _check(self._lib.paw_sync_status(self._h))
+
+    def set_wait_limit(self, seconds=2.0, probe=False):
+        """Give-up bound of the tensor-core pipelines' waits; probe=True makes their
+        launches wait on a word nothing sets, so they give up (failure-path check)."""
+        _check(self._lib.paw_set_wait_limit(self._h, float(seconds), int(bool(probe))))
 
     PHASES = ("residual_local", "recurrence", "projection", "cell_products", "residual_nonlocal", "recovery")
 
@@ -305,6 +313,8 @@ class PawFE:
         return torch.complex128 if self.complex else torch.float64
 
     def cheb_filter(self, X, lam, degree, bounds, prec="tf32", out=None):
+        """Algorithm 2 on the columns of X (stream-ordered: returns once enqueued;
+        sync_status() reports a kernel that gave up on a bounded wait)."""
         import torch
         xp, rows, n, ldx = _mat(X, self._fp64())
         if out is None:

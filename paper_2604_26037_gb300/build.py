@@ -1,7 +1,7 @@
 """Build libpawfe.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Every translation unit is compiled in parallel, then linked with cuBLAS and
-cuSOLVER.  Rebuilds only when a source or header is newer than the library.
+Every translation unit is compiled in parallel, then linked with cuSOLVER
+(the projected generalised eigensolve of Rayleigh-Ritz).  Rebuilds only when a source or header is newer than the library.
 """
 from __future__ import annotations
 
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-L", _cuda_lib(),
-           "-lcublas", "-lcusolver", "-lcudart"]
+           "-lcusolver", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -416,18 +416,58 @@ void cheb_issue(paw_context *c, paw_precision prec, const double *X, int ldx, in
     cheb_block_issue<float>(c, prec, X, ldx, nb, bd.a0, cc, S, hd, hf, Xo, ldo, s);
 }
 
-// One block, synchronous: scalars in host memory, launches, wait, device status.
+// Next slot of the handle's pinned ring, large enough for `bytes`.  Waits only
+// for the GPU to pass the copies of the slot's previous use.
+static HostSlot &acquire_slot(paw_context *c, size_t bytes) {
+  HostRing &R = c->scal_ring;
+  if (R.slots.empty()) R.slots.resize(8);
+  HostSlot &sl = R.slots[R.next];
+  R.next = (R.next + 1) % R.slots.size();
+  if (sl.pending) {
+    PAW_CUDA(cudaEventSynchronize(sl.done));
+    sl.pending = false;
+  }
+  if (!sl.done) PAW_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  if (sl.bytes < bytes) {
+    if (sl.host) cudaFreeHost(sl.host);
+    sl.host = nullptr;
+    sl.bytes = 0;
+    PAW_CUDA(cudaHostAlloc(&sl.host, bytes, cudaHostAllocDefault));
+    sl.bytes = bytes;
+  }
+  return sl;
+}
+
+static void release_ring(paw_context *c) {
+  for (HostSlot &sl : c->scal_ring.slots) {
+    if (sl.host) cudaFreeHost(sl.host);
+    if (sl.done) cudaEventDestroy(sl.done);
+  }
+  c->scal_ring.slots.clear();
+}
+
+// One block, stream-ordered: the scalar images go to a pinned slot of the
+// handle's ring (valid until the GPU has read them), then copies and kernels
+// are enqueued; the host does not wait for the stream.  A bounded wait that
+// expires in a tensor-core kernel is reported by paw_sync_status or by the
+// next call that synchronises.
 static void cheb_block(paw_context *c, paw_precision prec, const double *X, int ldx, const double *lam, int nb,
                        int m, paw_bounds bd, double *Xo, int ldo, cudaStream_t s) {
   ChebScalars S;
-  std::vector<double> hd(cheb_nd(nb, m));
-  std::vector<float> hf(cheb_nf(nb, m));
-  cheb_plan(nb, m, bd, lam, S, hd.data(), hf.data());
-  cheb_issue(c, prec, X, ldx, nb, bd, S, hd.data(), hf.data(), Xo, ldo, s);
-  // keep host-side scalars alive until the async copies have been consumed
-  PAW_CUDA(cudaStreamSynchronize(s));
-  if (prec == PAW_TF32 || prec == PAW_BF16)
-    PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+  const size_t nd = cheb_nd(nb, m), nf = cheb_nf(nb, m);
+  HostSlot &sl = acquire_slot(c, sizeof(double) * nd + sizeof(float) * nf);
+  double *hd = static_cast<double *>(sl.host);
+  float *hf = reinterpret_cast<float *>(hd + nd);
+  cheb_plan(nb, m, bd, lam, S, hd, hf);
+  try {
+    cheb_issue(c, prec, X, ldx, nb, bd, S, hd, hf, Xo, ldo, s);
+  } catch (...) {
+    // copies from the slot may already be enqueued: keep it until the stream passes them
+    if (cudaEventRecord(sl.done, s) == cudaSuccess) sl.pending = true;
+    throw;
+  }
+  PAW_CUDA(cudaEventRecord(sl.done, s));
+  sl.pending = true;
 }
 
 // ============================================================== reductions
@@ -577,33 +617,6 @@ __global__ void __launch_bounds__(256) k_grad_V(int nc, int nq, const int *__res
   }
 }
 
-// Mixed-precision subspace rotation (Sec. 4.4): q32 = fl32(Q) with a zero
-// diagonal (column-major N x N), qd = diag(Q) in FP64.
-__global__ void k_split_q(int N, const double *__restrict__ Q, float *__restrict__ q32, double *__restrict__ qd) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)N * N) return;
-  const int r = (int)(i % N), col = (int)(i / N);
-  q32[i] = (r == col) ? 0.f : (float)Q[i];
-  if (r == col) qd[col] = Q[i];
-}
-
-// x32[r][j] = fl32(X[r][j]) for nr rows of N columns (X row pitch ld)
-__global__ void k_rows_to_f32(int nr, int N, const double *__restrict__ X, int ld, float *__restrict__ x32) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)nr * N) return;
-  const size_t r = i / N, j = i % N;
-  x32[i] = (float)X[r * ld + j];
-}
-
-// X[r][j] = X[r][j] Q[j][j] + t32[r][j]   (FP64 combination)
-__global__ void k_rot_combine(int nr, int N, const double *__restrict__ qd, const float *__restrict__ t32,
-                              double *__restrict__ X, int ld) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)nr * N) return;
-  const size_t r = i / N, j = i % N;
-  X[r * ld + j] = fma(X[r * ld + j], qd[j], (double)t32[i]);
-}
-
 // dD[a][ext(al)][ext(be)] = sum_v f[v] U[a][al][v] U[a][be][v]  (ext: internal -> caller's
 // projector index; f NULL: 1)
 template <typename T>
@@ -714,6 +727,38 @@ static void apply_any(paw_context *c, paw_precision prec, int which, const void 
   }
 }
 
+namespace pawfe {
+void check_block_args(paw_context *c, const void *X, const void *Y, int ncols, int ldx, int ldy) {
+  PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+  PAW_REQUIRE(ncols >= 0, PAW_ERR_INVALID_ARG, "ncols < 0");
+  if (ncols == 0) return;
+  PAW_REQUIRE(X && Y, PAW_ERR_INVALID_ARG, "NULL X or Y");
+  PAW_REQUIRE(ldx >= ncols && ldy >= ncols, PAW_ERR_INVALID_ARG, "leading dimension smaller than ncols");
+}
+
+// Tensor-core precisions: wait for the stream and report a kernel that gave
+// up on a bounded wait (its output is incomplete).
+static void check_tc_status(paw_context *c, paw_precision prec) {
+  if (prec != PAW_TF32 && prec != PAW_BF16) return;
+  PAW_CUDA(cudaStreamSynchronize(c->last_stream));
+  PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
+}
+
+// Calls that synchronise report a bounded wait that expired in an earlier,
+// asynchronous call on the handle (paw_cheb_filter): its output is incomplete.
+static void report_earlier_timeout(paw_context *c) {
+  PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT,
+              "a tensor-core kernel of an earlier call on this handle gave up on a bounded wait");
+}
+
+void check_prec(paw_precision prec, bool pair_ok) {
+  PAW_REQUIRE(pair_ok || prec != PAW_F32X2, PAW_ERR_UNSUPPORTED,
+              "PAW_F32X2 applies to paw_apply_H and paw_apply_S (step 2 of the filter: options.y0_pair32)");
+  PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16 || prec == PAW_F32X2,
+              PAW_ERR_INVALID_ARG, "unknown precision");
+}
+}  // namespace pawfe
+
 extern "C" {
 
 const char *paw_last_error(void) { return g_last_error.c_str(); }
@@ -810,8 +855,8 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
                 "pair-of-FP32 step 2 (y0_pair32) is implemented for real vectors (k = 0)");
     c->npjr = c->kc ? 2 * npj : npj;
     if (npj == 0) c->natoms = 0;   // atoms without projectors carry no nonlocal term
-    c->status_dev.ensure(sizeof(int), &c->dev_bytes);
-    PAW_CUDA(cudaMemset(c->status_dev.ptr, 0, sizeof(int)));
+    c->status_dev.ensure(2 * sizeof(int), &c->dev_bytes);
+    PAW_CUDA(cudaMemset(c->status_dev.ptr, 0, 2 * sizeof(int)));
     if (npj > 0) {
       c->proj_ext_dev.ensure(sizeof(int) * npj, &c->dev_bytes);
       PAW_CUDA(cudaMemcpy(c->proj_ext_dev.ptr, c->proj_ext.data(), sizeof(int) * npj, cudaMemcpyHostToDevice));
@@ -819,7 +864,6 @@ paw_status paw_fe_create(const paw_mesh *mesh, int degree, const paw_atoms *atom
     build_tables(c);
     build_operators(c, vloc);
     build_couplings(c);
-    if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) throw Error{PAW_ERR_LIBRARY, "cublasCreate failed"};
     if (cusolverDnCreate(&c->cusolver) != CUSOLVER_STATUS_SUCCESS)
       throw Error{PAW_ERR_LIBRARY, "cusolverDnCreate failed"};
     PAW_CUDA(cudaDeviceSynchronize());
@@ -842,14 +886,14 @@ paw_status paw_destroy(paw_handle c) {
                     &c->DH64, &c->DS64, &c->DSinv64, &c->ws_partial, &c->ws_W, &c->ws_W2, &c->ws_Y0, &c->ws_RX,
                     &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
-                    &c->ws_rot, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
+                    &c->ws_rot, &c->ws_gram, &c->ws_cg, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
                     &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
                     &c->own_lg, &c->own_sidx, &c->own_cnt, &c->Bk64, &c->Bk32, &c->tc_bk_tf32.He,
                     &c->tc_bk_bf16.He, &c->ws_cx, &c->ws_cy,
                     &c->nltc.eoff, &c->ownPx2, &c->ws_Wx2, &c->wVx2};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-  if (c->cublas) cublasDestroy(c->cublas);
+  release_ring(c);
   if (c->cusolver) cusolverDnDestroy(c->cusolver);
   delete c;
   return PAW_OK;
@@ -894,29 +938,6 @@ paw_status paw_set_dij(paw_handle c, const double *D_ij) {
   PAW_TRY_END
 }
 
-static void check_block_args(paw_context *c, const void *X, const void *Y, int ncols, int ldx, int ldy) {
-  PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
-  PAW_REQUIRE(ncols >= 0, PAW_ERR_INVALID_ARG, "ncols < 0");
-  if (ncols == 0) return;
-  PAW_REQUIRE(X && Y, PAW_ERR_INVALID_ARG, "NULL X or Y");
-  PAW_REQUIRE(ldx >= ncols && ldy >= ncols, PAW_ERR_INVALID_ARG, "leading dimension smaller than ncols");
-}
-
-// Tensor-core precisions: wait for the stream and report a kernel that gave
-// up on a bounded wait (its output is incomplete).
-static void check_tc_status(paw_context *c, paw_precision prec) {
-  if (prec != PAW_TF32 && prec != PAW_BF16) return;
-  PAW_CUDA(cudaStreamSynchronize(c->last_stream));
-  PAW_REQUIRE(read_status(c) == 0, PAW_ERR_TIMEOUT, "a tensor-core kernel gave up on a bounded wait");
-}
-
-// pair_ok: the call takes PAW_F32X2 (paw_apply_H, paw_apply_S)
-static void check_prec(paw_precision prec, bool pair_ok = false) {
-  PAW_REQUIRE(pair_ok || prec != PAW_F32X2, PAW_ERR_UNSUPPORTED,
-              "PAW_F32X2 applies to paw_apply_H and paw_apply_S (step 2 of the filter: options.y0_pair32)");
-  PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16 || prec == PAW_F32X2,
-              PAW_ERR_INVALID_ARG, "unknown precision");
-}
 
 paw_status paw_apply_H(paw_handle c, paw_precision prec, const void *X, void *Y, int ncols, int ldx, int ldy,
                        void *stream) {
@@ -996,43 +1017,41 @@ paw_status paw_cheb_filter(paw_handle c, paw_precision prec, const double *X_in,
   PAW_TRY_END
 }
 
-// Rayleigh-Ritz at k != 0 (complex X, interleaved, ld complex entries).  In the
-// column-major view Xc = X^T (N x M), C = (H X)^T Xc^H = conj(H^p) and
-// D = conj(S^p); zhegvd on (C, D) gives the Ritz values and Y = conj(Q), and
-// X <- X Q is Xc <- Y^H Xc.
+// Rayleigh-Ritz at k != 0 (complex X, interleaved, ld complex entries).  The
+// complex blocks are read as real blocks of 2N interleaved columns: the real
+// Gram matrix of X with H X (S X) holds the four real products of
+// H^p = X^H H X (S^p), zhegvd solves H^p Q = S^p Q Lambda, and X <- X Q is the
+// real rotation of the interleaved rows by the 2N x 2N real form of Q.
 static void rr_complex(paw_context *c, double *X, int ld, int N, double *lambda_out, cudaStream_t s) {
-  const int M = (int)c->ndof;
+  const int64_t M = c->ndof;
   const int Bc = std::min(N, c->opts.block);
   c->ws_HX.ensure(sizeof(double) * 2 * (size_t)M * N, &c->dev_bytes);
   c->ws_SX.ensure(sizeof(double) * 2 * (size_t)M * N, &c->dev_bytes);
   c->ws_Hp.ensure(sizeof(double) * 2 * (size_t)N * N, &c->dev_bytes);
   c->ws_Sp.ensure(sizeof(double) * 2 * (size_t)N * N, &c->dev_bytes);
-  double *HX = c->ws_HX.as<double>(), *SX = c->ws_SX.as<double>();
+  c->ws_cg.ensure(sizeof(double) * 4 * (size_t)N * N, &c->dev_bytes);
+  double *HX = c->ws_HX.as<double>(), *SX = c->ws_SX.as<double>(), *G = c->ws_cg.as<double>();
   for (int j0 = 0; j0 < N; j0 += Bc) {
     const int nb = std::min(Bc, N - j0);
     apply_cplx<double>(c, PAW_FP64, 0, X + 2 * (size_t)j0, ld, HX + 2 * (size_t)j0, N, nb, s);
     apply_cplx<double>(c, PAW_FP64, 1, X + 2 * (size_t)j0, ld, SX + 2 * (size_t)j0, N, nb, s);
   }
-  cublasSetStream(c->cublas, s);
   cusolverDnSetStream(c->cusolver, s);
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-  auto *Xc = reinterpret_cast<cuDoubleComplex *>(X);
-  auto *Cm = reinterpret_cast<cuDoubleComplex *>(c->ws_Hp.ptr);
-  auto *Dm = reinterpret_cast<cuDoubleComplex *>(c->ws_Sp.ptr);
-  if (cublasZgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_C, N, N, M, &one, reinterpret_cast<cuDoubleComplex *>(HX), N,
-                  Xc, ld, &zero, Cm, N) != CUBLAS_STATUS_SUCCESS ||
-      cublasZgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_C, N, N, M, &one, reinterpret_cast<cuDoubleComplex *>(SX), N,
-                  Xc, ld, &zero, Dm, N) != CUBLAS_STATUS_SUCCESS)
-    throw Error{PAW_ERR_LIBRARY, "cublasZgemm (projection) failed"};
+  rr_gram(c, X, 2 * ld, 2 * N, HX, 2 * N, 2 * N, M, false, G, 2 * N, s);
+  rr_gram_to_hermitian(N, G, c->ws_Hp.ptr, s);
+  rr_gram(c, X, 2 * ld, 2 * N, SX, 2 * N, 2 * N, M, false, G, 2 * N, s);
+  rr_gram_to_hermitian(N, G, c->ws_Sp.ptr, s);
+  auto *Am = reinterpret_cast<cuDoubleComplex *>(c->ws_Hp.ptr);
+  auto *Bm = reinterpret_cast<cuDoubleComplex *>(c->ws_Sp.ptr);
   int lwork = 0;
   c->ws_eig.ensure(sizeof(double) * N, &c->dev_bytes);
   c->ws_info.ensure(sizeof(int), &c->dev_bytes);
   if (cusolverDnZhegvd_bufferSize(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                  N, Cm, N, Dm, N, c->ws_eig.as<double>(), &lwork) != CUSOLVER_STATUS_SUCCESS)
+                                  N, Am, N, Bm, N, c->ws_eig.as<double>(), &lwork) != CUSOLVER_STATUS_SUCCESS)
     throw Error{PAW_ERR_LIBRARY, "cusolverDnZhegvd_bufferSize failed"};
   c->ws_solver.ensure(sizeof(cuDoubleComplex) * std::max(1, lwork), &c->dev_bytes);
-  if (cusolverDnZhegvd(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, Cm, N,
-                       Dm, N, c->ws_eig.as<double>(), reinterpret_cast<cuDoubleComplex *>(c->ws_solver.ptr), lwork,
+  if (cusolverDnZhegvd(c->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, N, Am, N,
+                       Bm, N, c->ws_eig.as<double>(), reinterpret_cast<cuDoubleComplex *>(c->ws_solver.ptr), lwork,
                        c->ws_info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
     throw Error{PAW_ERR_LIBRARY, "cusolverDnZhegvd failed"};
   int info = 0;
@@ -1040,17 +1059,8 @@ static void rr_complex(paw_context *c, double *X, int ld, int N, double *lambda_
   PAW_CUDA(cudaStreamSynchronize(s));
   PAW_REQUIRE(info <= N, PAW_ERR_NOT_SPD, "projected overlap S^p is not positive definite");
   PAW_REQUIRE(info == 0, PAW_ERR_LIBRARY, "zhegvd did not converge");
-  const int rows = std::min(M, std::max(1024, (1 << 26) / N));
-  c->ws_rot.ensure(sizeof(cuDoubleComplex) * (size_t)rows * N, &c->dev_bytes);
-  auto *tmp = reinterpret_cast<cuDoubleComplex *>(c->ws_rot.ptr);
-  for (int r0 = 0; r0 < M; r0 += rows) {
-    const int nr = std::min(rows, M - r0);
-    if (cublasZgemm(c->cublas, CUBLAS_OP_C, CUBLAS_OP_N, N, nr, N, &one, Cm, N, Xc + (size_t)r0 * ld, ld, &zero,
-                    tmp, N) != CUBLAS_STATUS_SUCCESS)
-      throw Error{PAW_ERR_LIBRARY, "cublasZgemm (rotation) failed"};
-    PAW_CUDA(cudaMemcpy2DAsync(Xc + (size_t)r0 * ld, sizeof(cuDoubleComplex) * ld, tmp, sizeof(cuDoubleComplex) * N,
-                               sizeof(cuDoubleComplex) * N, nr, cudaMemcpyDeviceToDevice, s));
-  }
+  rr_complex_to_real(N, c->ws_Hp.ptr, G, s);
+  rr_rotate(c, X, 2 * ld, M, 2 * N, G, false, s);
   PAW_CUDA(cudaMemcpyAsync(lambda_out, c->ws_eig.ptr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   PAW_CUDA(cudaStreamSynchronize(s));
 }
@@ -1064,28 +1074,24 @@ paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lam
   c->last_stream = s;
   if (c->kc) {
     rr_complex(c, X, ld, N, lambda_out, s);
+    report_earlier_timeout(c);
     return PAW_OK;
   }
-  const int M = (int)c->ndof;
+  const int64_t M = c->ndof;
   const int Bc = std::min(N, c->opts.block);
   c->ws_HX.ensure(sizeof(double) * (size_t)M * Bc, &c->dev_bytes);
   c->ws_Hp.ensure(sizeof(double) * (size_t)N * N, &c->dev_bytes);
   c->ws_Sp.ensure(sizeof(double) * (size_t)N * N, &c->dev_bytes);
   double *HX = c->ws_HX.as<double>(), *Hp = c->ws_Hp.as<double>(), *Sp = c->ws_Sp.as<double>();
-  cublasSetStream(c->cublas, s);
   cusolverDnSetStream(c->cusolver, s);
-  const double one = 1.0, zero = 0.0;
-  // lower triangle only (dsygvd reads the lower part): column block j0..j0+nb gets rows j0..N-1
+  // RR-Projection, lower triangle only (dsygvd reads the lower part): column
+  // block j0..j0+nb of H^p and S^p gets rows j0..N-1
   for (int j0 = 0; j0 < N; j0 += Bc) {
     const int nb = std::min(Bc, N - j0), nr = N - j0;
     op_H<double>(c, PAW_FP64, X + j0, ld, HX, nb, nb, s);
-    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, nr, nb, M, &one, X + j0, ld, HX, nb, &zero,
-                    Hp + (size_t)j0 * N + j0, N) != CUBLAS_STATUS_SUCCESS)
-      throw Error{PAW_ERR_LIBRARY, "cublasDgemm (H^p) failed"};
+    rr_gram(c, X + j0, ld, nr, HX, nb, nb, M, true, Hp + (size_t)j0 * N + j0, N, s);
     op_S<double>(c, X + j0, ld, HX, nb, nb, s);
-    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, nr, nb, M, &one, X + j0, ld, HX, nb, &zero,
-                    Sp + (size_t)j0 * N + j0, N) != CUBLAS_STATUS_SUCCESS)
-      throw Error{PAW_ERR_LIBRARY, "cublasDgemm (S^p) failed"};
+    rr_gram(c, X + j0, ld, nr, HX, nb, nb, M, true, Sp + (size_t)j0 * N + j0, N, s);
   }
   int lwork = 0;
   c->ws_eig.ensure(sizeof(double) * N, &c->dev_bytes);
@@ -1103,42 +1109,11 @@ paw_status paw_rayleigh_ritz(paw_handle c, double *X, int ld, int N, double *lam
   PAW_CUDA(cudaStreamSynchronize(s));
   PAW_REQUIRE(info <= N, PAW_ERR_NOT_SPD, "projected overlap S^p is not positive definite");
   PAW_REQUIRE(info == 0, PAW_ERR_LIBRARY, "dsygvd did not converge");
-  // rotation X <- X Q in row chunks
-  const int rows = std::min(M, std::max(1024, (1 << 27) / N));   // temp <= 1 GiB
-  if (c->opts.rr_mixed) {
-    // X <- X diag(Q) (FP64) + fl32(X) fl32(Q - diag(Q)) (FP32 GEMM, FP32 accumulation)
-    c->ws_rot.ensure(sizeof(float) * ((size_t)N * N + 2 * (size_t)rows * N) + sizeof(double) * N, &c->dev_bytes);
-    double *qd = c->ws_rot.as<double>();
-    float *q32 = reinterpret_cast<float *>(qd + N);
-    float *x32 = q32 + (size_t)N * N, *t32 = x32 + (size_t)rows * N;
-    k_split_q<<<(unsigned)(((size_t)N * N + 255) / 256), 256, 0, s>>>(N, Hp, q32, qd);
-    PAW_LAUNCH_CHECK("k_split_q");
-    const float onef = 1.f, zerof = 0.f;
-    for (int r0 = 0; r0 < M; r0 += rows) {
-      const int nr = std::min(rows, M - r0);
-      const size_t n = (size_t)nr * N;
-      k_rows_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nr, N, X + (size_t)r0 * ld, ld, x32);
-      PAW_LAUNCH_CHECK("k_rows_to_f32");
-      if (cublasSgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, N, nr, N, &onef, q32, N, x32, N, &zerof, t32, N) !=
-          CUBLAS_STATUS_SUCCESS)
-        throw Error{PAW_ERR_LIBRARY, "cublasSgemm (off-diagonal rotation) failed"};
-      k_rot_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nr, N, qd, t32, X + (size_t)r0 * ld, ld);
-      PAW_LAUNCH_CHECK("k_rot_combine");
-    }
-  } else {
-    c->ws_rot.ensure(sizeof(double) * (size_t)rows * N, &c->dev_bytes);
-    double *tmp = c->ws_rot.as<double>();
-    for (int r0 = 0; r0 < M; r0 += rows) {
-      const int nr = std::min(rows, M - r0);
-      if (cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, N, nr, N, &one, Hp, N, X + (size_t)r0 * ld, ld, &zero,
-                      tmp, N) != CUBLAS_STATUS_SUCCESS)
-        throw Error{PAW_ERR_LIBRARY, "cublasDgemm (rotation) failed"};
-      PAW_CUDA(cudaMemcpy2DAsync(X + (size_t)r0 * ld, sizeof(double) * ld, tmp, sizeof(double) * N,
-                                 sizeof(double) * N, nr, cudaMemcpyDeviceToDevice, s));
-    }
-  }
+  // RR-SR: X <- X Q in FP64, or (rr_mixed) X diag(Q) in FP64 + fl32(X) fl32(Q - diag(Q)) in FP32
+  rr_rotate(c, X, ld, M, N, Hp, c->opts.rr_mixed != 0, s);
   PAW_CUDA(cudaMemcpyAsync(lambda_out, c->ws_eig.ptr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   PAW_CUDA(cudaStreamSynchronize(s));
+  report_earlier_timeout(c);
   return PAW_OK;
   PAW_TRY_END
 }
@@ -1169,6 +1144,7 @@ paw_status paw_residuals(paw_handle c, const double *X, int ld, const double *la
                                             c->ws_colscale.as<double>(), 2 * nb, s);
       for (int j = 0; j < nb; ++j) rnorm_out[j0 + j] = std::sqrt(r[j] + r[nb + j]);
     }
+    report_earlier_timeout(c);
     return PAW_OK;
   }
   c->ws_HX.ensure(sizeof(double) * (size_t)c->ndof * Bc, &c->dev_bytes);
@@ -1185,6 +1161,7 @@ paw_status paw_residuals(paw_handle c, const double *X, int ld, const double *la
                                           c->ws_colscale.as<double>(), nb, s);
     for (int j = 0; j < nb; ++j) rnorm_out[j0 + j] = std::sqrt(r[j]);
   }
+  report_earlier_timeout(c);
   return PAW_OK;
   PAW_TRY_END
 }
@@ -1365,6 +1342,17 @@ paw_status paw_profile_read(paw_handle c, paw_profile *out) {
   }
   for (int i = 0; i < PAW_NPHASES; ++i) out->launches[i] = c->prof.launches[i];
   out->total_launches = g_launch_count - c->prof.launch0;
+  return PAW_OK;
+  PAW_TRY_END
+}
+
+paw_status paw_set_wait_limit(paw_handle c, double seconds, int probe) {
+  PAW_TRY_BEGIN
+  PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+  PAW_REQUIRE(std::isfinite(seconds) && seconds >= 1e-3 && seconds <= 60.0, PAW_ERR_INVALID_ARG,
+              "wait limit must be between 1 ms and 60 s");
+  c->wait_ns = (uint64_t)(seconds * 1e9);
+  c->wait_probe = probe ? 1 : 0;
   return PAW_OK;
   PAW_TRY_END
 }

@@ -389,7 +389,8 @@ static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx
   PAW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int cap = c->grid_cap > 0 ? std::min(c->grid_cap, nsm) : nsm;
   const int grid = std::max(1, std::min(p.ntiles, cap));
-  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>());
+  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>(), c->wait_ns,
+                                                                     c->wait_probe);
   PAW_LAUNCH_CHECK("k_tc_stream<cell>");
 }
 

@@ -3,7 +3,6 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
-#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <cstdint>
@@ -13,6 +12,10 @@
 #include "paw_fe.h"
 
 namespace pawfe {
+
+// Atoms whose projectors reach the owned nodes of one cell: the owner-cell
+// kernels stage the atom list of a cell in shared memory (checked at set-up).
+constexpr int PAIRS_PER_CELL_MAX = 192;
 
 // ---------------------------------------------------------------- errors
 struct Error {
@@ -96,6 +99,21 @@ struct NlTcMats {
   int ntile = 0;    // owned nodes per expansion N tile (multiple of 16, <= 128)
   int nh = 0;       // expansion N tiles per cell
   int64_t exp_chunks = 0;
+};
+
+// Pinned host slots for the scalar images of paw_cheb_filter's blocks.  A
+// slot is rewritten only once the GPU has passed the copies that read it
+// (its event), so the filter enqueues block after block without waiting for
+// the stream; the host blocks only when it runs a whole ring ahead.
+struct HostSlot {
+  void *host = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+struct HostRing {
+  std::vector<HostSlot> slots;
+  size_t next = 0;
 };
 
 // Phase timing (paw_profile_enable / paw_profile_read)
@@ -202,15 +220,20 @@ struct paw_context {
   pawfe::DevBuf ws_lam, ws_colscale, ws_red, ws_vec;
   pawfe::DevBuf ws_pp;                        // per-pair projection partials
   pawfe::DevBuf ws_HX, ws_SX, ws_Hp, ws_Sp, ws_eig, ws_solver, ws_info, ws_rot;
+  pawfe::DevBuf ws_gram;                      // split partial tiles of the RR projection
+  pawfe::DevBuf ws_cg;                        // real 2N x 2N Gram / rotation matrix (k != 0)
   pawfe::DevBuf ws_cx, ws_cy;                 // split [Re | Im] copies of complex arguments (k != 0)
 
   // tensor-core kernel family: 0 persistent warp-specialised where the layout
   // allows it, 1 one-CTA-per-tile kernels; grid_cap > 0 limits the CTAs of a
   // persistent launch (instances sharing the GPU)
   int tc_variant = 0, grid_cap = 0;
-  pawfe::DevBuf status_dev;                   // int: set by a kernel whose bounded wait expired
+  pawfe::DevBuf status_dev;                   // int[2]: [0] set by a kernel whose bounded wait expired,
+                                              // [1] a word nothing sets (wait probe, paw_set_wait_limit)
+  uint64_t wait_ns = 2000000000ull;           // give-up bound of the pipeline waits of tensor-core kernels
+  int wait_probe = 0;                         // 1: persistent tensor-core launches first wait on status[1]
+  pawfe::HostRing scal_ring;                  // pinned scalar images of paw_cheb_filter blocks
 
-  cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t cusolver = nullptr;
   cudaStream_t last_stream = nullptr;
   pawfe::Profiler prof;
@@ -320,6 +343,10 @@ void cell_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
 // the same with the one Bloch cell matrix B^e shared by every cell (k != 0)
 void bloch_apply_tc(paw_context *c, paw_precision prec, const float *X, int ldx,
                     float *Y, int ldy, int ncols, float alpha, cudaStream_t s);
+// argument checks shared by the entry points (api.cu).  pair_ok: the call
+// takes PAW_F32X2 (paw_apply_H, paw_apply_S)
+void check_prec(paw_precision prec, bool pair_ok = false);
+void check_block_args(paw_context *c, const void *X, const void *Y, int ncols, int ldx, int ldy);
 // device status word of the instance: 0 when no bounded wait of a tensor-core
 // kernel expired since the last read, 1 when one did (read on the last stream,
 // then cleared); -1 when it cannot be read
@@ -351,6 +378,20 @@ struct PhaseScope {
   PhaseScope(paw_context *ctx, int phase, cudaStream_t st);
   ~PhaseScope();
 };
+
+// Rayleigh-Ritz contractions (rr.cu).  rr_gram: G[c * ldg + r] =
+// sum_{i < K} A[i][r] B[i][c] for r < R, c < C (column-major G; lower: only
+// tiles that reach the lower triangle, r >= c, are computed and written).
+// rr_rotate: X <- X Q for M rows of N columns (Q column-major N x N), in FP64
+// or mixed (diagonal of Q in FP64, the rest in FP32).  At k != 0:
+// rr_gram_to_hermitian turns the real Gram matrix (2N x 2N) of interleaved
+// complex columns into X^H Y (complex column-major), rr_complex_to_real the
+// complex Q into its real 2N x 2N form.
+void rr_gram(paw_context *c, const double *A, int lda, int R, const double *B, int ldb, int C, int64_t K, bool lower,
+             double *G, int ldg, cudaStream_t s);
+void rr_rotate(paw_context *c, double *X, int ld, int64_t M, int N, const double *Q, bool mixed, cudaStream_t s);
+void rr_gram_to_hermitian(int N, const double *G, void *Ap, cudaStream_t s);
+void rr_complex_to_real(int N, const void *Q, double *Qr, cudaStream_t s);
 
 // small host linear algebra (setup.cu)
 void jacobi_eigh(int n, std::vector<double> &A, std::vector<double> &evals,

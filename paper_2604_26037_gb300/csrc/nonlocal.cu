@@ -37,7 +37,7 @@ template <typename T>
 struct ExpCfg;
 template <>
 struct ExpCfg<float> {
-  static constexpr int VT = 32;
+  static constexpr int VT = 32;       // vectors per CTA; 4 when the W of a cell's pairs would not fit
 };
 
 constexpr int OWN_MAX = 512;   // p <= 8
@@ -391,17 +391,16 @@ __global__ void __launch_bounds__(NPAD / 2 * 32) k_couple_h_c(int np, const int 
 // ------------------------------------------------------------------ expansion
 // FP32 SIMT form (the FP64 form is k_own_expand64 below).
 // Expansion with a fused output stage.  W of every pair of the cell is staged
-// in shared memory (at most 48 pairs); a thread owns 4 vectors of one node row
-// at a time.
+// in shared memory (VT vectors of each: 32, or 4 for cells with many pairs);
+// a thread owns 4 vectors of one node row at a time.
 //   EXP_ADD        Y += cs[v] * S1
 //   EXP_SINV       Y  = md_inv * (X - S1)                                         (Eq. Sinvapprox)
 //   EXP_RECURRENCE T  = md_inv * (R_Y - S1)
 //                  R_X = [-beta R_Y - gamma R_X + S2] + alpha Y Lambda_Y   (S2: nonlocal part of alpha H T)
 // with S1 = sum_k P[k][o] . W1[a_k], S2 = sum_k P[k][o] . W2[a_k].
-template <typename T, int NPAD, int MODE>
+template <typename T, int NPAD, int MODE, int VT>
 __global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__restrict__ oP, const T *__restrict__ W1,
                                                     const T *__restrict__ W2) {
-  constexpr int VT = ExpCfg<T>::VT;
   constexpr int G = VT / 4;               // groups of 4 vectors
   constexpr int OR = 256 / G;             // node rows per pass
   constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
@@ -689,7 +688,7 @@ __global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const R *__rest
   constexpr int NG = NPAD / 4, NWARP = 8;
   constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
   __shared__ int ooff[OWN_MAX];
-  __shared__ int patom[64];
+  __shared__ int patom[PAIRS_PER_CELL_MAX];
   const int e = blockIdx.y, v0 = blockIdx.x * 32;
   const int k0 = A.own_off[e], k1 = A.own_off[e + 1];
   if (MODE == EXP_ADD && k0 == k1) return;
@@ -882,7 +881,7 @@ void nl_residual_pair(paw_context *c, const double *X, int ldx, int ncols, const
                       const double *cs, double *Y, int ldy, cudaStream_t s) {
   if (c->nown_pairs == 0 || ncols <= 0) return;
   PAW_REQUIRE(!c->kc, PAW_ERR_UNSUPPORTED, "pair-of-FP32 arithmetic is implemented for real vectors (k = 0)");
-  PAW_REQUIRE(c->max_own_pairs <= 64 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+  PAW_REQUIRE(c->max_own_pairs <= PAIRS_PER_CELL_MAX && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
               "too many atoms on one cell for the expansion kernel");
   const int64_t ntab = (int64_t)c->nown_pairs * c->own * c->npad;
   if (!c->ownPx2.ptr) {   // built on first use from the FP64 table
@@ -971,7 +970,7 @@ static void own_expand(paw_context *c, paw_precision prec, ExpArgs A, const T *W
     }
   }
   if constexpr (sizeof(T) == 8) {
-    PAW_REQUIRE(c->max_own_pairs <= 64 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+    PAW_REQUIRE(c->max_own_pairs <= PAIRS_PER_CELL_MAX && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
                 "too many atoms on one cell for the expansion kernel");
     dim3 g((A.ncols + 31) / 32, c->ncells);
     if (c->npad == 16)
@@ -980,24 +979,27 @@ static void own_expand(paw_context *c, paw_precision prec, ExpArgs A, const T *W
       k_own_expand64<32, MODE, double><<<g, 256, 0, s>>>(A, c->ownP64.as<double>(), c->own_lg.as<int8_t>(), W1, W2);
     PAW_LAUNCH_CHECK("k_own_expand64");
   } else {
-    constexpr int VT = ExpCfg<T>::VT;
     A.vec_ok = aligned16(A.Y, A.ldy * sizeof(T)) && aligned16(A.Xin, A.ldx * sizeof(T)) &&
                aligned16(A.RX, A.ldx * sizeof(T)) && aligned16(A.Y0, A.ldy0 * sizeof(float)) &&
                aligned16(A.Y0lo, A.ldy0 * sizeof(float));
     constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
-    const size_t shm = sizeof(T) * (size_t)NW * std::max(1, c->max_own_pairs) * c->npad * VT;
-    PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
+    constexpr size_t SHM_MAX = 200 * 1024;
+    // W of every pair of a cell for VT vectors: 32 vectors per CTA, or 4 when that exceeds the budget
+    const size_t per_vec = sizeof(T) * (size_t)NW * std::max(1, c->max_own_pairs) * c->npad;
+    const bool wide = per_vec * ExpCfg<T>::VT <= SHM_MAX;
+    const int VT = wide ? ExpCfg<T>::VT : 4;
+    const size_t shm = per_vec * VT;
+    PAW_REQUIRE(shm <= SHM_MAX && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
                 "too many atoms on one cell for the expansion kernel");
     dim3 g((A.ncols + VT - 1) / VT, c->ncells);
-    if (c->npad == 16) {
-      auto kern = k_own_expand<T, 16, MODE>;
+    auto launch = [&](auto kern) {
       PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
       kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
-    } else {
-      auto kern = k_own_expand<T, 32, MODE>;
-      PAW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      kern<<<g, 256, shm, s>>>(A, ownP<T>(c), W1, W2);
-    }
+    };
+    if (c->npad == 16)
+      wide ? launch(k_own_expand<T, 16, MODE, ExpCfg<T>::VT>) : launch(k_own_expand<T, 16, MODE, 4>);
+    else
+      wide ? launch(k_own_expand<T, 32, MODE, ExpCfg<T>::VT>) : launch(k_own_expand<T, 32, MODE, 4>);
     PAW_LAUNCH_CHECK("k_own_expand");
   }
 }
@@ -1107,21 +1109,41 @@ namespace pawfe {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PAW_NOALLOC_SCRATCH_BYTES];
 
+// The driver context current on the calling thread (NULL if the driver entry
+// point cannot be found: then only the device ordinal keys the cache).
+static CUcontext current_context() {
+  typedef CUresult (*GetCurrent)(CUcontext *);
+  static GetCurrent fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+    return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<GetCurrent>(f) : nullptr;
+  }();
+  CUcontext ctx = nullptr;
+  if (fn && fn(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  return ctx;
+}
+
 // Device address of g_noalloc_scratch on the current device, looked up once per
-// device.  In host code the symbol itself is only a host-side handle.
+// device and context (a device reset makes a new primary context, and the
+// address is looked up again).  In host code the symbol itself is only a
+// host-side handle.
 static void *noalloc_scratch() {
   static std::mutex mu;
   static void *addr[128] = {};
+  static CUcontext ctx_of[128] = {};
   int dev = 0;
   PAW_CUDA(cudaGetDevice(&dev));
   PAW_REQUIRE(dev >= 0 && dev < 128, PAW_ERR_UNSUPPORTED, "device ordinal above 127");
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  if (!addr[dev] || ctx == nullptr || ctx_of[dev] != ctx) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // binds the primary context
     PAW_REQUIRE(e == cudaSuccess && p != nullptr, PAW_ERR_CUDA,
                 std::string("cudaGetSymbolAddress(no-allocation scratch): ") + cudaGetErrorString(e));
     addr[dev] = p;
+    ctx_of[dev] = current_context();
   }
   return addr[dev];
 }
@@ -1163,14 +1185,11 @@ extern "C" paw_status paw_apply_Sinv_approx_noalloc(paw_handle c, paw_precision 
                                                     int ncols, int ldx, int ldy, void *stream) {
   using namespace pawfe;
   try {
-    PAW_REQUIRE(c != nullptr, PAW_ERR_INVALID_ARG, "NULL handle");
+    // the same checks, in the same order and with the same codes, as paw_apply_Sinv_approx
+    check_prec(prec);
+    check_block_args(c, X, Y, ncols, ldx, ldy);
     PAW_REQUIRE(!c->kc, PAW_ERR_UNSUPPORTED, "the allocation-free entry point has no Bloch-wavevector form");
-    PAW_REQUIRE(prec == PAW_FP64 || prec == PAW_FP32 || prec == PAW_TF32 || prec == PAW_BF16, PAW_ERR_INVALID_ARG,
-                "unknown precision");
-    PAW_REQUIRE(ncols >= 0, PAW_ERR_INVALID_ARG, "ncols < 0");
     if (ncols == 0) return PAW_OK;
-    PAW_REQUIRE(X && Y, PAW_ERR_INVALID_ARG, "NULL X or Y");
-    PAW_REQUIRE(ldx >= ncols && ldy >= ncols, PAW_ERR_INVALID_ARG, "leading dimension smaller than ncols");
     auto s = (cudaStream_t)stream;
     c->last_stream = s;
     if (prec == PAW_FP64)

@@ -40,7 +40,7 @@ constexpr int THREADS = 256;             // two gather threads per A row
 constexpr uint32_t A_BYTES = MT * 128;   // one K-chunk of A (128 rows x 32 TF32)
 constexpr uint32_t TMEM_COLS = 256;
 constexpr int OWN_MAX_TC = 512;          // p <= 8
-constexpr int PAIR_MAX = 48;             // pairs of one cell (checked at set-up)
+constexpr int PAIR_MAX = PAIRS_PER_CELL_MAX;   // pairs of one cell (checked at set-up)
 constexpr uint32_t PROJ_STAGE = A_BYTES + 256u * 128u;
 
 __host__ __device__ constexpr uint32_t exp_stage_bytes(int nw) { return (uint32_t)nw * A_BYTES + 128u * 128u; }
@@ -1025,7 +1025,8 @@ static void launch_stream(const paw_context *c, const P &p, cudaStream_t s, cons
   const size_t shm = tcs::Geo<P>::SMEM;
   PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const int grid = std::max(1, std::min(p.ntiles, persistent_grid(c)));
-  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>());
+  tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>(), c->wait_ns,
+                                                                     c->wait_probe);
   PAW_LAUNCH_CHECK(what);
 }
 

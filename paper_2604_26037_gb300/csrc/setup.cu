@@ -592,8 +592,9 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
       c->max_own_pairs = std::max(c->max_own_pairs, off[e + 1]);
       off[e + 1] += off[e];
     }
-    PAW_REQUIRE(c->max_own_pairs <= 48, PAW_ERR_UNSUPPORTED,
-                "more than 48 atoms have projector support on the nodes of one cell");
+    PAW_REQUIRE(c->max_own_pairs <= PAIRS_PER_CELL_MAX, PAW_ERR_UNSUPPORTED,
+                "more than " + std::to_string(PAIRS_PER_CELL_MAX) +
+                    " atoms have projector support on the nodes of one cell");
     const size_t blk = (size_t)c->own * c->npad;
     std::vector<double> oP(keys.size() * blk, 0.0);
     for (int a = 0; a < natoms; ++a)

@@ -35,9 +35,14 @@
 // transposer threads), empty[s] (MMAs done, tcgen05.commit); per
 // accumulator b: accf[b] (commit) and acce[b] (one arrival per epilogue warp).
 //
-// Every wait is bounded (2 s) and gives up early once another role has given
-// up (a shared abort word).  The CTA then lets its bulk copies land, drains
-// its MMAs, frees the tensor memory and records the failure in *status.
+// Every pipeline wait is bounded (wait_ns, 2 s unless paw_set_wait_limit
+// changed it) and gives up early once another role has given up (a shared
+// abort word).  The CTA then lets its bulk copies land and drains its MMAs
+// (those two waits keep the fixed 2 s bound: they end as soon as the copies
+// and MMAs already issued complete), frees the tensor memory and records the
+// failure in status[0].  With probe set, thread 0 first waits on status[1], a
+// word nothing writes, so the launch gives up before it issues any copy or MMA:
+// the failure path, exercised without a fault.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -61,6 +66,7 @@ constexpr int SMAX = 6;                       // stages at most
 
 struct Shared {
   uint64_t full[SMAX], afull[SMAX], empty[SMAX], accf[2], acce[2], drain;
+  uint64_t wait_ns;                           // give-up bound of the pipeline waits of this launch
   uint32_t taddr;
   int abort;
 };
@@ -85,12 +91,13 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 // Bounded wait that also returns false as soon as another role has given up.
 // Warps that go on to warp-collective instructions call warp_wait instead,
 // so that all 32 lanes take the same decision.
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort) {
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort,
+                                              uint64_t limit = WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if (gtimer() - t0 > WAIT_NS) {
+    if (gtimer() - t0 > limit) {
       *abort = 1;
       return false;
     }
@@ -99,9 +106,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 }
 
 // lane 0 waits, the warp follows its result
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort, int lane) {
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort, int lane,
+                                          uint64_t limit = WAIT_NS) {
   int ok = 0;
-  if (lane == 0) ok = wait_or_abort(bar, parity, abort) ? 1 : 0;
+  if (lane == 0) ok = wait_or_abort(bar, parity, abort, limit) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
@@ -178,7 +186,7 @@ __device__ void role_loader(const P &p, uint8_t *base, Shared *sh, int lane) {
   for (; run && have; ++g) {
     const int s = (int)(g % S);
     const uint32_t u = g / S;
-    if (g >= (uint32_t)S && !warp_wait(smem_u32(&sh->empty[s]), (u - 1) & 1u, abort, lane)) {
+    if (g >= (uint32_t)S && !warp_wait(smem_u32(&sh->empty[s]), (u - 1) & 1u, abort, lane, sh->wait_ns)) {
       run = false;
       break;
     }
@@ -238,7 +246,7 @@ __device__ void role_transpose(const P &p, uint8_t *base, Shared *sh, int r) {
       for (int kc = 0; kc < nk; ++kc, ++g) {
         const int s = (int)(g % S);
         const uint32_t u = g / S;
-        if (!wait_or_abort(smem_u32(&sh->full[s]), u & 1u, abort)) {
+        if (!wait_or_abort(smem_u32(&sh->full[s]), u & 1u, abort, sh->wait_ns)) {
           run = false;
           break;
         }
@@ -289,7 +297,7 @@ __device__ void role_mma(const P &p, uint8_t *base, Shared *sh, uint32_t tmem) {
     for (int sub = 0; run && sub < ns; ++sub, ++tc) {
       const int b = (int)(tc & 1u);
       const uint32_t ub = tc >> 1;
-      if (tc >= 2 && !wait_or_abort(smem_u32(&sh->acce[b]), (ub - 1) & 1u, abort)) {
+      if (tc >= 2 && !wait_or_abort(smem_u32(&sh->acce[b]), (ub - 1) & 1u, abort, sh->wait_ns)) {
         run = false;
         break;
       }
@@ -299,7 +307,7 @@ __device__ void role_mma(const P &p, uint8_t *base, Shared *sh, uint32_t tmem) {
       for (int kc = 0; kc < nk; ++kc, ++g) {
         const int s = (int)(g % S);
         const uint32_t u = g / S;
-        if (!wait_or_abort(smem_u32(&sh->afull[s]), u & 1u, abort)) {
+        if (!wait_or_abort(smem_u32(&sh->afull[s]), u & 1u, abort, sh->wait_ns)) {
           run = false;
           break;
         }
@@ -336,7 +344,7 @@ __device__ void role_epilogue(const P &p, Shared *sh, uint32_t tmem, int warp, i
     for (int sub = 0; sub < ns; ++sub, ++tc) {
       const int b = (int)(tc & 1u);
       const uint32_t ub = tc >> 1;
-      if (!warp_wait(smem_u32(&sh->accf[b]), ub & 1u, abort, lane)) {
+      if (!warp_wait(smem_u32(&sh->accf[b]), ub & 1u, abort, lane, sh->wait_ns)) {
         run = false;
         break;
       }
@@ -351,7 +359,8 @@ __device__ void role_epilogue(const P &p, Shared *sh, uint32_t tmem, int warp, i
 }
 
 template <class P>
-__global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const __grid_constant__ P p, int *status) {
+__global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const __grid_constant__ P p, int *status, uint64_t wait_ns,
+                                                                     int probe) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = align1024(smem_raw);
   Shared *sh = reinterpret_cast<Shared *>(base + (size_t)P::S * Geo<P>::STAGE);
@@ -367,7 +376,20 @@ __global__ void __launch_bounds__(threads_for(P::NEPI), 1) k_tc_stream(const __g
       mbar_init(smem_u32(&sh->acce[b]), P::NEPI);
     }
     mbar_init(smem_u32(&sh->drain), 1);
+    sh->wait_ns = wait_ns;
     sh->abort = (*reinterpret_cast<volatile int *>(status) != 0) ? 1 : 0;   // an earlier CTA gave up
+    if (probe && !sh->abort) {
+      // failure-path probe: wait on status[1], a word nothing sets, before any copy or
+      // MMA is issued; the bounded wait runs out and every role of the CTA gives up
+      const volatile int *gate = status + 1;
+      const uint64_t t0 = gtimer();
+      while (*gate == 0) {
+        if (gtimer() - t0 > wait_ns) {
+          sh->abort = 1;
+          break;
+        }
+      }
+    }
     fence_barrier_init();
     fence_proxy_async();
   }

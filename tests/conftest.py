@@ -25,3 +25,16 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    try:
+        from tests.gpu_util import MEASURED
+    except Exception:  # pragma: no cover
+        return
+    if not MEASURED:
+        return
+    terminalreporter.write_sep("-", "measured errors (GPU parity)")
+    for test, quantity, value, bound in MEASURED:
+        b = "" if bound is None else f"   (bound {bound:.1e})"
+        terminalreporter.write_line(f"{test}: {quantity} = {value:.3e}{b}")

@@ -48,3 +48,22 @@ def rel_err(a, b):
     a = np.asarray(a, float)
     b = np.asarray(b, float)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# measured errors of the parity tests, printed in the terminal summary (tests/conftest.py)
+MEASURED = []
+
+
+def report(test, quantity, value, bound=None):
+    MEASURED.append((test, quantity, float(value), None if bound is None else float(bound)))
+
+
+def gap_index(lam, k0, gap_min=1e-4):
+    """State count nearest to k0 with lam[k] - lam[k-1] > gap_min (Ha): compared sets of the
+    lowest states never split a (near-)degenerate level (gap-aware choice of k)."""
+    n = len(lam)
+    for d in range(n):
+        for k in (k0 - d, k0 + d):
+            if 1 <= k < n and lam[k] - lam[k - 1] > gap_min:
+                return k
+    return n

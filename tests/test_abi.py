@@ -96,6 +96,7 @@ def test_rejects_bad_kpoint_arguments_before_device_work(lib):
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.paw_apply_H(None, 0, None, None, 4, 4, 4, None) == 1
     assert lib.paw_sync_status(None) == 1
+    assert lib.paw_set_wait_limit(None, 1.0, 0) == 1
     assert lib.paw_destroy(None) == 0
     b = L._Bounds(1.0, 0.5, 2.0)
     lam = np.zeros(1)
@@ -122,3 +123,15 @@ def test_options_struct_matches_header():
 def test_precision_enum_matches_header():
     vals = dict((k, int(v)) for k, v in re.findall(r"PAW_(FP64|FP32|TF32|BF16|F32X2) = (\d+)", _header()))
     assert vals == {k: getattr(L.Precision, k) for k in vals} and len(vals) == 5
+
+
+def test_sinv_entry_points_reject_the_same_requests(lib):
+    """paw_apply_Sinv_approx and its allocation-free variant share their argument checks:
+    the same request gets the same status code from both (checked before the handle)."""
+    for prec, code in ((L.Precision.F32X2, 2), (17, 1)):
+        a = lib.paw_apply_Sinv_approx(None, prec, None, None, 4, 4, 4, None)
+        b = lib.paw_apply_Sinv_approx_noalloc(None, prec, None, None, 4, 4, 4, None)
+        assert a == b == code, (prec, a, b)
+    for args in ((4, 4, 4), (-1, 4, 4)):   # NULL handle, then a bad column count
+        assert lib.paw_apply_Sinv_approx(None, 0, None, None, *args, None) == \
+            lib.paw_apply_Sinv_approx_noalloc(None, 0, None, None, *args, None) == 1

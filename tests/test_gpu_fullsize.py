@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import inputs
-from tests.gpu_util import rel_err, to_dev
+from tests.gpu_util import rel_err, report, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,8 @@ def test_operators_full_size(prec, tol):
     if prec != "f32x2":
         Si = fe.apply_Sinv_approx(Xin, prec=prec)[:, list(COLS)].double().cpu().numpy()
         errs["Sinv"] = rel_err(Si, op.apply_Sinv_approx(Xs))
-    print(f"full-size operators {prec}: " + ", ".join(f"{k} {v:.3e}" for k, v in errs.items()))
+    for k, v in errs.items():
+        report(f"mid operators {prec}", f"{k} relative error", v, tol)
     assert max(errs.values()) < tol
     del H, S
     torch.cuda.empty_cache()
@@ -97,5 +98,29 @@ def test_filter_full_size(prec, pair32, tol):
     del out
     torch.cuda.empty_cache()
     err = rel_err(got, _oracle_filter(bounds))
-    print(f"full-size filter {prec} pair32={pair32}: relative error {err:.3e} (tolerance {tol:g})")
+    report(f"mid filter {prec}{' pair32 step 2' if pair32 else ''}", "relative error", err, tol)
     assert err < tol
+
+
+def test_filter_calls_are_stream_ordered():
+    """Two TF32 filter calls on one stream, no host wait between them: each returns once its
+    work is enqueued (the stream is still busy when the second returns), and both outputs
+    match the oracle's columns."""
+    import torch
+    fe = _fe()
+    bounds = _bounds()
+    m = inputs.CONFIGS[NAME]["degree"]
+    X = _X()
+    torch.cuda.synchronize()
+    out1 = fe.cheb_filter(X, _lam(), m, bounds, prec="tf32")
+    out2 = fe.cheb_filter(X, _lam(), m, bounds, prec="tf32")
+    busy = not torch.cuda.current_stream().query()
+    fe.sync_status()
+    ref = _oracle_filter(bounds)
+    e1 = rel_err(out1[:, list(COLS)].cpu().numpy(), ref)
+    e2 = rel_err(out2[:, list(COLS)].cpu().numpy(), ref)
+    del out1, out2
+    torch.cuda.empty_cache()
+    report("mid filter tf32, two calls without a host wait", "relative error (first, second)", max(e1, e2), 5e-2)
+    assert busy, "the second call returned after the GPU had finished both"
+    assert e1 < 5e-2 and e2 < 5e-2

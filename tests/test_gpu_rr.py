@@ -5,7 +5,7 @@ import pytest
 
 import inputs
 from oracle import rr
-from tests.gpu_util import gpu_fe, oracle_ops, rel_err, to_dev
+from tests.gpu_util import gap_index, gpu_fe, oracle_ops, rel_err, report, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -75,21 +75,29 @@ def _rchfsi_gpu(fe, X0, m, iters, prec, nwanted):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32-y32", "tf32-rrmix", "tf32-pair"])
 def test_rchfsi_converges_to_dense(prec):
-    """tiny workload: 10 iterations, degree 20; 8 lowest eigenvalues within 1e-6 Ha of
-    the dense FP64 generalised eigensolve of the oracle's matrices ("-y32": the
-    residual block Y kept in FP32 only; "-rrmix": mixed-precision subspace rotation;
-    "-pair": step 2 in pair-of-FP32 arithmetic)."""
+    """tiny workload, degree 20 ("-y32": the residual block Y kept in FP32 only; "-rrmix":
+    mixed-precision subspace rotation; "-pair": step 2 in pair-of-FP32 arithmetic):
+    after the configured 10 iterations the 8 lowest eigenvalues are within 1e-6 Ha of the
+    dense FP64 generalised eigensolve of the oracle's matrices; after 13 iterations the
+    span of the lowest states (k = 8 moved to a gap above 1e-4 Ha) is within principal
+    angles of 1e-5 of the dense eigenvectors in the S inner product (the FP64 oracle's own
+    R-ChFSI reaches 8e-5 after 10 and 2.6e-6 after 13 iterations: angles converge at half
+    the rate of the eigenvalue errors)."""
     op = oracle_ops("tiny")
-    lam_ex, V_ex = rr.dense_eigs(op, 8)
+    lam_ex, V_ex = rr.dense_eigs(op, 12)
     y32 = prec.endswith("-y32")
     rrmix = prec.endswith("-rrmix")
     pair = prec.endswith("-pair")
-    prec = prec.split("-")[0]
+    p = prec.split("-")[0]
     fe = gpu_fe("tiny", block=16, y0_fp32=y32, rr_mixed=rrmix, y0_pair32=pair)
     X0 = inputs.start_columns("tiny", range(16))
-    X, lam, hist = _rchfsi_gpu(fe, X0, 20, 10, prec, 8)
-    err = np.abs(lam[:8] - lam_ex).max()
-    assert err < 1e-6, (prec, err, [h[0][:8] - lam_ex for h in hist[-2:]])
-    # subspace of the 8 lowest states: principal angles in the S inner product
-    ang = rr.subspace_angles_S(op.apply_S, X.cpu().numpy()[:, :8], V_ex)
-    assert ang.max() < 1e-3
+    X, lam, hist = _rchfsi_gpu(fe, X0, 20, 13, p, 8)
+    err10 = np.abs(hist[9][0][:8] - lam_ex[:8]).max()
+    assert err10 < 1e-6, (prec, err10)
+    k = gap_index(lam_ex, 8)
+    ang = rr.subspace_angles_S(op.apply_S, X.cpu().numpy()[:, :k], V_ex[:, :k])
+    err = np.abs(lam[:k] - lam_ex[:k]).max()
+    report(f"tiny R-ChFSI {prec}", "eigenvalue error after 10 iterations (Ha)", err10, 1e-6)
+    report(f"tiny R-ChFSI {prec}", f"max S-angle of the lowest {k} after 13 iterations", ang.max(), 1e-5)
+    assert err < 1e-6, (prec, err)
+    assert ang.max() < 1e-5, (prec, ang)

@@ -19,7 +19,10 @@ from tests.gpu_util import gpu_fe, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-11, "fp32": 2e-5}
+# fp64 / fp32: the same SIMT arithmetic as the allocating call.  tf32 / bf16: the allocating call
+# runs the projector contractions on the tensor cores (TF32 operands), this one in FP32 FMA, so
+# the two differ by TF32 operand rounding (the operator tests' TF32 bound).
+TOL = {"fp64": 1e-11, "fp32": 2e-5, "tf32": 4e-3, "bf16": 4e-3}
 
 
 def _noalloc(fe, prec, X, Y):
@@ -32,7 +35,7 @@ def _noalloc(fe, prec, X, Y):
 
 
 @pytest.mark.parametrize("name", ["tiny", "p6"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_noalloc_matches_allocating_entry_point(name, prec):
     import torch
     fe = gpu_fe(name)
@@ -45,6 +48,26 @@ def test_noalloc_matches_allocating_entry_point(name, prec):
         assert _noalloc(fe, prec, X, Y) == 0, fe._lib.paw_last_error()
         torch.cuda.synchronize()
         assert rel_err(Y.double().cpu().numpy(), ref) < TOL[prec]
+    fe.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_strided_blocks(prec):
+    """X and Y as column blocks of wider arrays (ld > ncols): only their own columns are
+    read and written."""
+    import torch
+    fe = gpu_fe("p6")
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rng = np.random.default_rng(32)
+    Xw = to_dev(rng.standard_normal((fe.ndof, 40)), dt)
+    Yw = torch.full((fe.ndof, 48), 7.0, dtype=dt, device="cuda")
+    X, Y = Xw[:, 5:25], Yw[:, 11:31]
+    ref = fe.apply_Sinv_approx(X.contiguous(), prec=prec).double().cpu().numpy()
+    assert _noalloc(fe, prec, X, Y) == 0, fe._lib.paw_last_error()
+    torch.cuda.synchronize()
+    assert rel_err(Y.double().cpu().numpy(), ref) < TOL[prec]
+    untouched = torch.cat([Yw[:, :11], Yw[:, 31:]], 1)
+    assert bool((untouched == 7.0).all())
     fe.close()
 
 
