@@ -336,8 +336,10 @@ def run_ours(args, ws, rank, local):
     sysd = inputs.make_system(args.workload)
     kp = tuple(args.kpoint) if args.kpoint else None
     fe = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, kpoint=kp,
-                             y0_pair32=args.y0_pair32)
+                             y0_pair32=args.y0_pair32, overlap=not args.no_overlap)
     M, N, m = fe.ndof, cfg["nvec"], cfg["degree"]
+    # the library overlaps the blocks of a call for real vectors in a reduced precision
+    overlapped = (not args.no_overlap and not kp and args.prec != "fp64" and N > cfg["block"])
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     # at a Bloch wavevector k the vectors are complex (one complex vector = one vector of the metric)
     X = torch.randn((M, N), dtype=torch.complex128 if fe.complex else torch.float64, device="cuda", generator=g)
@@ -401,7 +403,8 @@ def run_ours(args, ws, rank, local):
     # the same filter with step 2 in pair-of-FP32 arithmetic (FP64-class accuracy on the FP32 pipes)
     pair = None
     if args.pair_steps > 0 and not kp and not args.y0_pair32:
-        fe_p = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, y0_pair32=True)
+        fe_p = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, y0_pair32=True,
+                                   overlap=not args.no_overlap)
         out_p = torch.empty_like(out)
         ms_p, prof_p, clk_p = timed(args.prec, args.pair_steps, 1, profile=True, h=fe_p, dst=out_p)
         # both handles filter the same input with the FP64 bracket: the outputs differ
@@ -423,56 +426,61 @@ def run_ours(args, ws, rank, local):
         fe_p.close()
 
     # end to end through the public API with host buffers (pinned), copies inside the timed
-    # region.  The filter is independent per column, so the block goes through in column
-    # chunks: chunk c + 1 is copied in (one copy stream) and chunk c - 1 copied out (another)
-    # while chunk c is filtered on the compute stream.
+    # region: every step copies the whole block in, filters it with one call and copies the
+    # result out.  Consecutive steps are pipelined with two device buffer pairs: the input of
+    # step i + 1 is copied in (one copy stream) and the output of step i - 1 copied out
+    # (another) while step i filters.
     e2e = None
     if not args.no_e2e:
         del out
         torch.cuda.empty_cache()
-        cw = max(1, min(N, args.e2e_chunk))
-        cols = [(j, min(j + cw, N)) for j in range(0, N, cw)]
-        Xc = X.cpu()
-        Xh = [Xc[:, a:b].contiguous().pin_memory() for a, b in cols]   # chunk-major host arrays
-        Oh = [torch.empty_like(t).pin_memory() for t in Xh]
-        del Xc
-        Xd = [torch.empty_like(t, device="cuda") for t in Xh]
-        Od = [torch.empty_like(t, device="cuda") for t in Xh]
+        Xh = X.cpu().pin_memory()
+        Oh = torch.empty_like(Xh).pin_memory()
+        Xd = [torch.empty_like(X) for _ in range(2)]
+        Od = [torch.empty_like(X) for _ in range(2)]
+        del X
+        torch.cuda.empty_cache()
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
         comp = torch.cuda.current_stream()
+        nsteps = args.steps + 1   # one untimed step first
 
-        def e2e_step():
-            ev_in = []
-            for i in range(len(cols)):
+        def e2e_run(n):
+            ev_f, ev_o = [None] * n, [None] * n
+            for i in range(n):
+                b = i % 2
                 with torch.cuda.stream(s_in):
-                    Xd[i].copy_(Xh[i], non_blocking=True)
-                    ev = torch.cuda.Event()
-                    ev.record(s_in)
-                ev_in.append(ev)
-            for i, (a, b) in enumerate(cols):
-                comp.wait_event(ev_in[i])
-                fe.cheb_filter(Xd[i], lam[a:b], m, bounds, prec=args.prec, out=Od[i])
-                ev = torch.cuda.Event()
-                ev.record(comp)
+                    if i >= 2:
+                        s_in.wait_event(ev_f[i - 2])          # filter of step i - 2 has read Xd[b]
+                    Xd[b].copy_(Xh, non_blocking=True)
+                    ev_in = torch.cuda.Event()
+                    ev_in.record(s_in)
+                comp.wait_event(ev_in)
+                if i >= 2:
+                    comp.wait_event(ev_o[i - 2])              # Od[b] of step i - 2 copied out
+                fe.cheb_filter(Xd[b], lam, m, bounds, prec=args.prec, out=Od[b])
+                ev_f[i] = torch.cuda.Event()
+                ev_f[i].record(comp)
                 with torch.cuda.stream(s_out):
-                    s_out.wait_event(ev)
-                    Oh[i].copy_(Od[i], non_blocking=True)
+                    s_out.wait_event(ev_f[i])
+                    Oh.copy_(Od[b], non_blocking=True)
+                    ev_o[i] = torch.cuda.Event()
+                    ev_o[i].record(s_out)
             torch.cuda.synchronize()
 
-        e2e_step()
+        e2e_run(1)
         _barrier(ws)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_run(args.steps)
         t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
+        fe.sync_status()
         e2e = {"value": whole_job_rate(units_per_step, ws, t_e2e * 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in Xh) + N * 8),
-               "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in Oh)),
-               "chunks": len(cols), "chunk_columns": cw,
-               "overlap": "H2D of chunk c+1 and D2H of chunk c-1 on two copy streams while chunk c filters"}
+               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + N * 8),
+               "d2h_bytes_per_step": int(Oh.numel() * Oh.element_size()),
+               "overlap": "the H2D copy of step i+1 and the D2H copy of step i-1 on two copy streams while "
+                          "step i filters (two device buffer pairs)"}
+        out = Od[(args.steps - 1) % 2] if (args.rr or args.grad) else None   # a filtered block
         del Xd, Xh, Oh
-        out = torch.cat(Od, dim=1) if (args.rr or args.grad) else None   # the filtered block
-        del Od
+        X = None
 
     # Rayleigh-Ritz on the filtered block: FP64 rotation vs the mixed-precision one (rr_mixed)
     rrm = None
@@ -541,6 +549,32 @@ def run_ours(args, ws, rank, local):
     dom = max(phases, key=lambda k: phases[k]["ms"])
     roof = roofline(dom, phases[dom], fe, sysd, cfg, args.prec, peaks, clocks, args.workload)
     all_roof = {k: roofline(k, v, fe, sysd, cfg, args.prec, peaks, clocks, args.workload) for k, v in phases.items()}
+    # With the overlapped block schedule a phase's wall time includes the SMs it shares with
+    # the other stream.  The same kernels timed with the blocks one after another (a second
+    # handle, a few calls right after the timed region) give each kernel's own rate.
+    iso = None
+    if overlapped and args.iso_steps > 0:
+        fe_s = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, y0_pair32=args.y0_pair32,
+                                   overlap=False)
+        ms_s, prof_s, clk_s = timed(args.prec, args.iso_steps, 1, profile=True, h=fe_s)
+        fe_s.close()
+        ph_s = {k: v for k, v in prof_s.items() if isinstance(v, dict)}
+        iso = {k: roofline(k, v, fe, sysd, cfg, args.prec, peaks, clk_s, args.workload) for k, v in ph_s.items()}
+        src = (f"the same kernels with the blocks one after another (options.no_overlap = 1), {args.iso_steps} "
+               f"calls after the timed region: {ms_s:.1f} ms per call")
+        roof["isolated"] = {kk: iso[dom][kk] for kk in ("achieved", "frac", "ms_per_launch") if kk in iso[dom]}
+        roof["isolated"]["source"] = src
+        if "peak_alt" in iso[dom]:
+            roof["isolated"]["frac_alt"] = iso[dom]["peak_alt"]["frac"]
+        roof["schedule"] = ("timed region: step 2 of block 0 alone, step 2 of block 1 beside the loop of block 0, "
+                            "so the average launch duration includes the SMs shared with the loop")
+        for k in all_roof:
+            if k in iso:
+                all_roof[k]["isolated_frac"] = iso[k]["frac"]
+                all_roof[k]["isolated_ms_per_launch"] = iso[k]["ms_per_launch"]
+        iso = {"ms_per_step": round(ms_s, 3), "steps": args.iso_steps, "warmup": 1, "clocks": clk_s,
+               "phases_ms_per_step": {k: round(v["ms"] / args.iso_steps, 3) for k, v in ph_s.items()},
+               "value": round(whole_job_rate(units_per_step, ws, ms_s), 4)}
     launches = prof["total_launches"] // args.steps
 
     res = {
@@ -554,13 +588,17 @@ def run_ours(args, ws, rank, local):
                    **({"kpoint_per_bohr": list(kp), "vectors": "complex (real blocks of 2 B columns inside)"}
                       if kp else {}),
                    "start": args.start,
+                   "block_schedule": ("step 2 of block j+1 overlaps the loop of block j (two internal streams)"
+                                      if overlapped else "blocks one after another"),
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in phases.items()},
-        "phase_roofline": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "ms_per_launch", "traffic")
+        "phase_roofline": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "ms_per_launch", "traffic",
+                                                   "isolated_frac", "isolated_ms_per_launch")
                                if kk in v} for k, v in all_roof.items()},
+        "serial_schedule": iso,
         "fp64_form": fp64,
         "speedup_vs_fp64": (round(value / fp64["value"], 3) if fp64 else None),
         "e2e": e2e,
@@ -873,8 +911,11 @@ def main():
                     help="timed calls of the filter with a pair-of-FP32 step 2, reported beside the FP64 one "
                          "(0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunk", type=int, default=128,
-                    help="columns per chunk of the end-to-end leg (copies overlap the filter of other chunks)")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="filter the blocks one after another (no overlap of step 2 with the previous block's loop)")
+    ap.add_argument("--iso-steps", type=int, default=2,
+                    help="calls timed with the blocks one after another after the (overlapped) timed region, "
+                         "for each kernel's own roofline (0: skip)")
     ap.add_argument("--kpoint", type=float, nargs=3, default=None,
                     help="Bloch wavevector k (1/bohr): complex vectors, throughput per complex vector")
     ap.add_argument("--no-cpu-baseline", action="store_true")

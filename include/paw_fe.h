@@ -144,6 +144,12 @@ typedef struct {
                           2) in PAW_F32X2 arithmetic instead of FP64; Y keeps
                           FP64 storage.  k = 0 only (else paw_fe_create returns
                           PAW_ERR_UNSUPPORTED).  Default 0: FP64, as Algorithm 2 */
+  int32_t no_overlap;  /* 1: paw_cheb_filter runs its blocks one after another.
+                          Default 0: with two or more blocks of real vectors in
+                          PAW_FP32/TF32/BF16, step 2 (FP64) of block j + 1 runs
+                          on an internal stream while the loop of block j runs
+                          on another (the results are the same up to the order
+                          of FP32 additions)                                    */
 } paw_options;
 
 /* Filter bounds (Algorithm 2 inputs): a0 lower end of the wanted spectrum,
@@ -254,7 +260,10 @@ paw_status paw_apply_Sinv_approx_noalloc(paw_handle h, paw_precision prec, const
  * the call enqueues every copy and kernel on `stream` and returns without
  * waiting for them (the per-block scalars travel through pinned host memory
  * owned by the handle; the host only waits when it is eight blocks ahead of
- * the GPU).  Read failures with paw_sync_status.
+ * the GPU).  Read failures with paw_sync_status.  With two or more blocks of
+ * real vectors in a reduced precision (and options.no_overlap = 0), the call
+ * runs on two internal streams of the handle that wait for `stream` and that
+ * `stream` waits for: step 2 of block j + 1 runs beside the loop of block j.
  *   X_in      : device FP64 ndof x ncols (ld ldx), the block Psi_in
  *   lambda_in : host FP64 ncols, the eigenvalue estimates Lambda
  *   degree    : m >= 1 (H applied m times, Shat^-1 applied m times)

@@ -59,7 +59,8 @@ class _Vloc(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("block", C.c_int32), ("pp_overlap", C.c_int32), ("y0_fp32", C.c_int32),
-                ("rr_mixed", C.c_int32), ("kpoint", C.c_double * 3), ("y0_pair32", C.c_int32)]
+                ("rr_mixed", C.c_int32), ("kpoint", C.c_double * 3), ("y0_pair32", C.c_int32),
+                ("no_overlap", C.c_int32)]
 
 
 class _Bounds(C.Structure):
@@ -190,7 +191,7 @@ class PawFE:
 
     def __init__(self, L, ncell, degree, positions=(), shells=(), D=None, dS=None,
                  vloc=None, block=256, pp_overlap=False, y0_fp32=False, rr_mixed=False, kpoint=None,
-                 y0_pair32=False):
+                 y0_pair32=False, overlap=True):
         self._lib = load_library()
         pos = np.ascontiguousarray(np.asarray(positions, float).reshape(-1, 3))
         na = pos.shape[0]
@@ -214,7 +215,7 @@ class PawFE:
             vp = C.pointer(_Vloc(cen.shape[0], _dptr(cen), _dptr(dep), _dptr(wid)))
         kp = (0.0, 0.0, 0.0) if kpoint is None else tuple(float(x) for x in kpoint)
         opts = _Opts(int(block), int(bool(pp_overlap)), int(bool(y0_fp32)), int(bool(rr_mixed)),
-                     (C.c_double * 3)(*kp), int(bool(y0_pair32)))
+                     (C.c_double * 3)(*kp), int(bool(y0_pair32)), int(not overlap))
         h = C.c_void_p()
         _check(self._lib.paw_fe_create(C.byref(mesh), int(degree), C.byref(atoms), C.byref(proj),
                                        _dptr(Dh), _dptr(dSh), vp, C.byref(opts), C.byref(h)))

@@ -254,8 +254,8 @@ static void residual_block(paw_context *c, const double *X, int ldx, const doubl
   } else if (c->nown_pairs > 0) {
     PhaseScope ps(c, 4, s);
     // sum_a P^a (D_H^a - lambda_j dS^a) P^a^T x_j: one projection, one expansion
-    c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
-    double *W = c->ws_W2.as<double>();
+    c->scr->W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
+    double *W = c->scr->W2.as<double>();
     nl_project_residual<double>(c, X, ldx, ncols, negLam_dev, W, s);
     nl_expand<double>(c, PAW_FP64, W, ncols, Y, ldy, nullptr, s);
   }
@@ -318,45 +318,50 @@ void cheb_plan(int nb, int m, paw_bounds bd, const double *lam, ChebScalars &S, 
   hf[2 * ncf] = hf[2 * ncf + 1] = 0.f;
 }
 
-// Algorithm 2 for one block of nb columns: stream-ordered copies of the
-// scalar images (hd, hf: host memory that stays valid until the stream has
-// consumed it) and kernel launches only, no host synchronisation, so that the
-// sequence can also be captured into a CUDA graph.
+// Algorithm 2 for one block of nb columns, in two parts that only enqueue
+// copies and kernels (no host synchronisation, capturable into a CUDA graph):
+// block_step2 copies the block's scalar images (hd, hf: host memory valid
+// until the stream has consumed it) into the parity-par device images and
+// forms Y = H X - S X Lambda (step 2) into the parity-par Y buffer;
+// block_loop runs steps 3-5 from them.  Both parts of a block use the same
+// parity; two blocks of different parity can be in flight at once.
+static void block_step2(paw_context *c, const double *X, int ldx, int nb, const ChebScalars &S, const double *hd,
+                        const float *hf, int par, cudaStream_t s) {
+  c->ws_lamp[par].ensure(sizeof(double) * S.nd, &c->dev_bytes);
+  c->ws_cfp[par].ensure(sizeof(float) * S.nf, &c->dev_bytes);
+  PAW_CUDA(cudaMemcpyAsync(c->ws_lamp[par].ptr, hd, sizeof(double) * S.nd, cudaMemcpyHostToDevice, s));
+  PAW_CUDA(cudaMemcpyAsync(c->ws_cfp[par].ptr, hf, sizeof(float) * S.nf, cudaMemcpyHostToDevice, s));
+  c->ws_Y0p[par].ensure(sizeof(double) * c->ndof * nb, &c->dev_bytes);
+  // step 2: Y = H X - S X Lambda (FP64; phases 0 and 4)
+  residual_block(c, X, ldx, c->ws_lamp[par].as<double>(), c->ws_Y0p[par].as<double>(), nb, nb, s);
+}
+
 template <typename TR>
-static void cheb_block_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, double a0,
-                             double cc, const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo,
-                             cudaStream_t s) {
+static void block_loop(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, double a0, double cc,
+                       const ChebScalars &S, int par, double *Xo, int ldo, cudaStream_t s) {
   const int64_t M = c->ndof;
   const int nsteps = S.nsteps;
-  c->ws_lam.ensure(sizeof(double) * S.nd, &c->dev_bytes);
-  c->ws_cf.ensure(sizeof(float) * S.nf, &c->dev_bytes);
-  double *d_neglam = c->ws_lam.as<double>();
+  const double *d_neglam = c->ws_lamp[par].as<double>();
   const double *d_lyfin = d_neglam + nb, *d_cf = d_neglam + 2 * nb;
   const size_t ncf = (size_t)nsteps * nb;
-  const float *d_chi = c->ws_cf.as<float>(), *d_clo = d_chi + ncf;
-  PAW_CUDA(cudaMemcpyAsync(d_neglam, hd, sizeof(double) * S.nd, cudaMemcpyHostToDevice, s));
-  PAW_CUDA(cudaMemcpyAsync(c->ws_cf.ptr, hf, sizeof(float) * S.nf, cudaMemcpyHostToDevice, s));
+  const float *d_chi = c->ws_cfp[par].as<float>(), *d_clo = d_chi + ncf;
 
   const int ldr = nb;
   constexpr bool f32 = sizeof(TR) == 4;
-  c->ws_Y0.ensure(sizeof(double) * M * nb, &c->dev_bytes);
   c->ws_RX.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
   c->ws_RY.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
   c->ws_T.ensure(sizeof(TR) * M * nb, &c->dev_bytes);
   const bool lo = f32 && !c->opts.y0_fp32;
   if (f32) c->ws_Y0f.ensure(sizeof(float) * M * nb, &c->dev_bytes);
   if (lo) c->ws_Y0lo.ensure(sizeof(float) * M * nb, &c->dev_bytes);
-  double *Y0 = c->ws_Y0.as<double>();
+  const double *Y0 = c->ws_Y0p[par].as<double>();
   float *Yhi = f32 ? c->ws_Y0f.as<float>() : nullptr;
   float *Ylo = lo ? c->ws_Y0lo.as<float>() : nullptr;
   TR *RX = c->ws_RX.as<TR>(), *RY = c->ws_RY.as<TR>(), *T = c->ws_T.as<TR>();
   const size_t wbytes = sizeof(TR) * (size_t)std::max(1, c->natoms * c->npad) * nb;
   c->ws_W.ensure(wbytes, &c->dev_bytes);
-  c->ws_W2.ensure(sizeof(double) * (size_t)std::max(1, c->natoms * c->npad) * nb, &c->dev_bytes);
-
-  // step 2: Y = H X - S X Lambda (FP64; phases 0 and 4)
-  residual_block(c, X, ldx, d_neglam, Y0, nb, nb, s);
-  TR *WS = c->ws_W.as<TR>(), *WH = c->ws_W2.as<TR>();
+  c->scr->W2.ensure(sizeof(double) * (size_t)std::max(1, c->natoms * c->npad) * nb, &c->dev_bytes);
+  TR *WS = c->ws_W.as<TR>(), *WH = c->scr->W2.as<TR>();
   // step 3
   const dim3 blk(32, 8);
   {
@@ -410,10 +415,11 @@ static void cheb_block_issue(paw_context *c, paw_precision prec, const double *X
 void cheb_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, paw_bounds bd,
                 const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s) {
   const double cc = (bd.bU + bd.bW) / 2.0;
+  block_step2(c, X, ldx, nb, S, hd, hf, 0, s);
   if (prec == PAW_FP64)
-    cheb_block_issue<double>(c, prec, X, ldx, nb, bd.a0, cc, S, hd, hf, Xo, ldo, s);
+    block_loop<double>(c, prec, X, ldx, nb, bd.a0, cc, S, 0, Xo, ldo, s);
   else
-    cheb_block_issue<float>(c, prec, X, ldx, nb, bd.a0, cc, S, hd, hf, Xo, ldo, s);
+    block_loop<float>(c, prec, X, ldx, nb, bd.a0, cc, S, 0, Xo, ldo, s);
 }
 
 // Next slot of the handle's pinned ring, large enough for `bytes`.  Waits only
@@ -468,6 +474,105 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   }
   PAW_CUDA(cudaEventRecord(sl.done, s));
   sl.pending = true;
+}
+
+// ============================================================== overlapped blocks
+// Step 2 (FP64, bound by the FP64 pipe) of block j + 1 runs on a low-priority
+// side stream while the loop of block j (bound by copy bandwidth and the
+// tensor cores) runs on a high-priority stream: the blocks are independent
+// (Sec. 4.4 filters blocks independently), so this reorders nothing but the
+// schedule.  While a step 2 shares the SMs, the loop's persistent
+// cell-product and projection kernels take their half-shared-memory form and
+// the FP64 local kernel its 4-vector form, so that one CTA of each fits on
+// an SM; the high priority hands freed SM slots to the persistent kernels
+// first.  Blocks of parity j & 1 use the parity's Y buffer and scalar
+// images; the side stream reuses them for block j + 2 only after the loop of
+// block j has finished.
+static cudaEvent_t next_event(paw_context *c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    PAW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+static void ensure_streams(paw_context *c) {
+  if (c->s_loop) return;
+  int least = 0, greatest = 0;
+  PAW_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  PAW_CUDA(cudaStreamCreateWithPriority(&c->s_loop, cudaStreamNonBlocking, greatest));
+  PAW_CUDA(cudaStreamCreateWithPriority(&c->s_side, cudaStreamNonBlocking, least));
+}
+
+// work issued while this is alive uses the side scratch set and the lean FP64 kernel
+struct SideIssue {
+  paw_context *c;
+  SideIssue(paw_context *ctx, bool lean) : c(ctx) {
+    c->scr = &c->scr_side;
+    c->sf_lean = lean ? 1 : 0;
+  }
+  ~SideIssue() {
+    c->scr = &c->scr_main;
+    c->sf_lean = 0;
+  }
+};
+
+struct LeanLoop {
+  paw_context *c;
+  LeanLoop(paw_context *ctx, bool lean) : c(ctx) { c->lean = lean ? 1 : 0; }
+  ~LeanLoop() { c->lean = 0; }
+};
+
+static void cheb_filter_overlapped(paw_context *c, paw_precision prec, const double *X, int ldx, const double *lam,
+                                   int ncols, int m, paw_bounds bd, double *Xo, int ldo, cudaStream_t s) {
+  ensure_streams(c);
+  c->ev_used = 0;
+  const int B = c->opts.block, nbk = (ncols + B - 1) / B;
+  const double cc = (bd.bU + bd.bW) / 2.0;
+  cudaEvent_t ev0 = next_event(c);
+  PAW_CUDA(cudaEventRecord(ev0, s));   // the caller's earlier work on s (X, for one) is done
+  PAW_CUDA(cudaStreamWaitEvent(c->s_loop, ev0, 0));
+  PAW_CUDA(cudaStreamWaitEvent(c->s_side, ev0, 0));
+  std::vector<ChebScalars> S(nbk);
+  std::vector<cudaEvent_t> evY(nbk), evFree(nbk);
+  auto issue_step2 = [&](int j) {
+    const int j0 = j * B, nb = std::min(B, ncols - j0);
+    const size_t nd = cheb_nd(nb, m), nf = cheb_nf(nb, m);
+    HostSlot &sl = acquire_slot(c, sizeof(double) * nd + sizeof(float) * nf);
+    double *hd = static_cast<double *>(sl.host);
+    float *hf = reinterpret_cast<float *>(hd + nd);
+    cheb_plan(nb, m, bd, lam + j0, S[j], hd, hf);
+    if (j >= 2) PAW_CUDA(cudaStreamWaitEvent(c->s_side, evFree[j - 2], 0));   // parity buffers free again
+    try {
+      SideIssue side(c, j > 0);
+      block_step2(c, X + j0, ldx, nb, S[j], hd, hf, j & 1, c->s_side);
+    } catch (...) {
+      if (cudaEventRecord(sl.done, c->s_side) == cudaSuccess) sl.pending = true;
+      throw;
+    }
+    PAW_CUDA(cudaEventRecord(sl.done, c->s_side));
+    sl.pending = true;
+    evY[j] = next_event(c);
+    PAW_CUDA(cudaEventRecord(evY[j], c->s_side));
+  };
+  issue_step2(0);
+  for (int j = 0; j < nbk; ++j) {
+    if (j + 1 < nbk) issue_step2(j + 1);
+    const int j0 = j * B, nb = std::min(B, ncols - j0);
+    PAW_CUDA(cudaStreamWaitEvent(c->s_loop, evY[j], 0));
+    {
+      LeanLoop lean(c, j + 1 < nbk);   // a step 2 shares the SMs with this loop
+      block_loop<float>(c, prec, X + j0, ldx, nb, bd.a0, cc, S[j], j & 1, Xo + j0, ldo, c->s_loop);
+    }
+    evFree[j] = next_event(c);
+    PAW_CUDA(cudaEventRecord(evFree[j], c->s_loop));
+  }
+  cudaEvent_t e1 = next_event(c), e2 = next_event(c);
+  PAW_CUDA(cudaEventRecord(e1, c->s_loop));
+  PAW_CUDA(cudaEventRecord(e2, c->s_side));
+  PAW_CUDA(cudaStreamWaitEvent(s, e1, 0));   // later work on s follows every part of the call
+  PAW_CUDA(cudaStreamWaitEvent(s, e2, 0));
 }
 
 // ============================================================== reductions
@@ -883,16 +988,22 @@ paw_status paw_destroy(paw_handle c) {
                     &c->K64, &c->Nq64, &c->wq64, &c->Vq, &c->tc_tf32.He, &c->tc_tf32.Me, &c->tc_bf16.He,
                     &c->tc_bf16.Me, &c->ent_dof, &c->P64, &c->P32, &c->own_off, &c->own_atom, &c->ownP64,
                     &c->ownP32,
-                    &c->DH64, &c->DS64, &c->DSinv64, &c->ws_partial, &c->ws_W, &c->ws_W2, &c->ws_Y0, &c->ws_RX,
-                    &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_lam, &c->ws_colscale, &c->ws_red, &c->ws_vec,
+                    &c->DH64, &c->DS64, &c->DSinv64, &c->ws_W, &c->ws_RX,
+                    &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
-                    &c->ws_rot, &c->ws_gram, &c->ws_cg, &c->wV, &c->ws_Y0lo, &c->ws_cf, &c->gnb_off, &c->gnb_atom, &c->Gfull,
-                    &c->Gfull32, &c->apair_off, &c->apair, &c->ws_pp, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
+                    &c->ws_rot, &c->ws_gram, &c->ws_cg, &c->wV, &c->ws_Y0lo, &c->gnb_off, &c->gnb_atom, &c->Gfull,
+                    &c->Gfull32, &c->apair_off, &c->apair, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
                     &c->own_lg, &c->own_sidx, &c->own_cnt, &c->Bk64, &c->Bk32, &c->tc_bk_tf32.He,
                     &c->tc_bk_bf16.He, &c->ws_cx, &c->ws_cy,
-                    &c->nltc.eoff, &c->ownPx2, &c->ws_Wx2, &c->wVx2};
+                    &c->nltc.eoff, &c->ownPx2, &c->wVx2,
+                    &c->scr_main.partial, &c->scr_main.pp, &c->scr_main.W2, &c->scr_main.Wx2,
+                    &c->scr_side.partial, &c->scr_side.pp, &c->scr_side.W2, &c->scr_side.Wx2,
+                    &c->ws_Y0p[0], &c->ws_Y0p[1], &c->ws_lamp[0], &c->ws_lamp[1], &c->ws_cfp[0], &c->ws_cfp[1]};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->s_loop) cudaStreamDestroy(c->s_loop);
+  if (c->s_side) cudaStreamDestroy(c->s_side);
   release_ring(c);
   if (c->cusolver) cusolverDnDestroy(c->cusolver);
   delete c;
@@ -996,6 +1107,12 @@ paw_status paw_cheb_filter(paw_handle c, paw_precision prec, const double *X_in,
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
   const int B = c->opts.block;
+  // reduced-precision filter of real vectors over two or more blocks: step 2 of
+  // the next block overlaps the loop of the current one
+  if (!c->kc && prec != PAW_FP64 && ncols > B && c->opts.no_overlap == 0) {
+    cheb_filter_overlapped(c, prec, X_in, ldx, lambda_in, ncols, degree, b, X_out, ldo, s);
+    return PAW_OK;
+  }
   for (int j0 = 0; j0 < ncols; j0 += B) {
     const int nb = std::min(B, ncols - j0);
     if (c->kc) {
@@ -1265,15 +1382,15 @@ static void density_like(paw_context *c, paw_precision prec, const void *X, int 
   PAW_LAUNCH_CHECK("k_grad_V");
   if (c->nown_pairs > 0 && outD) {
     if (prec == PAW_FP64) {
-      c->ws_W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
-      nl_project<double>(c, PAW_FP64, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<double>(), s);
-      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<double>(), N, N,
+      c->scr->W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
+      nl_project<double>(c, PAW_FP64, (const double *)X, ld, N, nullptr, nullptr, 1.0, c->scr->W2.as<double>(), s);
+      k_grad_D<double><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->scr->W2.as<double>(), N, N,
                                                  c->proj_ext_dev.as<int>(), f, outD);
     } else {
-      c->ws_W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
+      c->scr->W2.ensure(sizeof(float) * (size_t)c->natoms * c->npad * N, &c->dev_bytes);
       // projector coefficients stay in FP32 arithmetic
-      nl_project<float>(c, PAW_FP32, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->ws_W2.as<float>(), s);
-      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->ws_W2.as<float>(), N, N,
+      nl_project<float>(c, PAW_FP32, (const float *)X, ld, N, nullptr, nullptr, 1.0, c->scr->W2.as<float>(), s);
+      k_grad_D<float><<<c->natoms, 256, 0, s>>>(c->npj, c->npad, c->scr->W2.as<float>(), N, N,
                                                 c->proj_ext_dev.as<int>(), f, outD);
     }
     PAW_LAUNCH_CHECK("k_grad_D");

@@ -253,11 +253,12 @@ __global__ void k_tile_mats(const float *__restrict__ He, long long stride, int 
 // Persistent warp-specialised form (tc_stream.cuh) for 16-byte-aligned rows:
 // tile = (cell, 128 vectors), one accumulation round per N tile of H^e.
 // SMALL: N tiles of at most 176 rows (degree <= 6), which leaves room for one
-// more pipeline stage.
-template <bool BF, bool SMALL>
+// more pipeline stage.  LEAN: two stages (about half the shared memory), the
+// form used while an FP64 step 2 shares the SMs (paw_cheb_filter).
+template <bool BF, bool SMALL, bool LEAN = false>
 struct CellStream {
   static constexpr int NW = 1, NEPI = 8;
-  static constexpr int S = (BF ? 2 : 3) + (SMALL ? 1 : 0);
+  static constexpr int S = LEAN ? 2 : (BF ? 2 : 3) + (SMALL ? 1 : 0);
   static constexpr bool BF16 = BF;
   static constexpr uint32_t B_MAX = (SMALL ? 176u : 256u) * 128u;
   static constexpr int KR = BF ? 64 : 32;
@@ -359,10 +360,10 @@ size_t tc_smem_bytes(int ntile, int kchunks, bool bf16) {
   return b < 80 * 1024 ? 80 * 1024 : b;
 }
 
-template <bool BF, bool SMALL>
+template <bool BF, bool SMALL, bool LEAN>
 static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx, float *Y, int ldy, int ncols,
                         float alpha, cudaStream_t s) {
-  CellStream<BF, SMALL> p;
+  CellStream<BF, SMALL, LEAN> p;
   p.vtiles = (ncols + MT - 1) / MT;
   const int64_t nt = (int64_t)c->ncells * p.vtiles;
   PAW_REQUIRE(nt < (1ll << 31), PAW_ERR_UNSUPPORTED, "too many cell tiles");
@@ -381,9 +382,12 @@ static void cell_stream(paw_context *c, const TcMats &T, const float *X, int ldx
   p.Y = Y;
   p.alpha = alpha;
   encode_row_map(&p.tm[0], X, c->ndof, ncols, ldx);
-  using P = CellStream<BF, SMALL>;
+  using P = CellStream<BF, SMALL, LEAN>;
   const size_t shm = tcs::Geo<P>::SMEM;
   PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (LEAN)   // the whole shared memory configured, so that an FP64 CTA fits beside this one
+    PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
   int dev = 0, nsm = 0;
   PAW_CUDA(cudaGetDevice(&dev));
   PAW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -405,16 +409,25 @@ static void cell_apply_tc_mats(paw_context *c, paw_precision prec, const TcMats 
   if (c->tc_variant == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 && ldx % 4 == 0 && ncols % 4 == 0 &&
       Tm.ntile <= 256) {
     const bool small = Tm.ntile <= 176;
+    if (c->lean) {   // an FP64 step 2 shares the SMs: half the shared memory
+      if (bf16)
+        small ? cell_stream<true, true, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s)
+              : cell_stream<true, false, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
+      else
+        small ? cell_stream<false, true, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s)
+              : cell_stream<false, false, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
+      return;
+    }
     if (bf16) {
       if (small)
-        cell_stream<true, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<true, true, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
       else
-        cell_stream<true, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<true, false, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
     } else {
       if (small)
-        cell_stream<false, true>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<false, true, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
       else
-        cell_stream<false, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
+        cell_stream<false, false, false>(c, Tm, X, ldx, Y, ldy, ncols, alpha, s);
     }
     return;
   }

@@ -101,6 +101,13 @@ struct NlTcMats {
   int64_t exp_chunks = 0;
 };
 
+// Scratch of the nonlocal helpers (per-atom sums, per-pair partials,
+// coefficients).  A context has two sets: step 2 of the next block, issued on
+// a side stream while the current block's loop runs, uses the second.
+struct NlScratch {
+  DevBuf partial, pp, W2, Wx2;
+};
+
 // Pinned host slots for the scalar images of paw_cheb_filter's blocks.  A
 // slot is rewritten only once the GPU has passed the copies that read it
 // (its event), so the filter enqueues block after block without waiting for
@@ -195,7 +202,6 @@ struct paw_context {
   pawfe::DevBuf own_atom;                     // int32 nown_pairs
   pawfe::DevBuf ownP64, ownP32;               // nown_pairs * own * npad
   pawfe::DevBuf ownPx2;                       // the same as pairs of FP32 numbers (built on first use)
-  pawfe::DevBuf ws_Wx2;                       // pair-of-FP32 coefficients of the nonlocal step-2 part
   pawfe::DevBuf own_ngrp;                     // int32 per pair: projector groups of 4 with a nonzero value
   // per pair and owned node o: index of the last projector group of 4 with a
   // nonzero value at o (-1: none); the owned nodes sorted by that index
@@ -216,9 +222,20 @@ struct paw_context {
   pawfe::DevBuf DH64, DS64, DSinv64;
 
   // workspaces
-  pawfe::DevBuf ws_partial, ws_W, ws_W2, ws_Y0, ws_RX, ws_RY, ws_T, ws_Y0f, ws_Y0lo, ws_cf;
-  pawfe::DevBuf ws_lam, ws_colscale, ws_red, ws_vec;
-  pawfe::DevBuf ws_pp;                        // per-pair projection partials
+  pawfe::DevBuf ws_W, ws_RX, ws_RY, ws_T, ws_Y0f, ws_Y0lo;
+  pawfe::DevBuf ws_colscale, ws_red, ws_vec;
+  pawfe::NlScratch scr_main, scr_side;       // nonlocal scratch sets (partial = U, pp, W2, Wx2)
+  pawfe::NlScratch *scr = &scr_main;         // the set the helpers use while work is issued
+  // per-block buffers, by block parity (two blocks in flight when step 2 of the
+  // next block overlaps the loop of the current one): Y = HX - SX Lambda (FP64)
+  // and the scalar images of the block (FP64 -Lambda, Lambda_Y, alpha Lambda_Y;
+  // FP32 hi/lo words)
+  pawfe::DevBuf ws_Y0p[2], ws_lamp[2], ws_cfp[2];
+  int lean = 0;      // 1: persistent cell/projection kernels in their half-shared-memory form
+  int sf_lean = 0;   // 1: FP64 sum-factorised kernel in its 4-vector form
+  cudaStream_t s_loop = nullptr, s_side = nullptr;   // internal streams of the overlapped filter
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
   pawfe::DevBuf ws_HX, ws_SX, ws_Hp, ws_Sp, ws_eig, ws_solver, ws_info, ws_rot;
   pawfe::DevBuf ws_gram;                      // split partial tiles of the RR projection
   pawfe::DevBuf ws_cg;                        // real 2N x 2N Gram / rotation matrix (k != 0)

@@ -767,6 +767,9 @@ static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T
                 "projection tile exceeds shared memory (degree too high)");
     PAW_CUDA(cudaFuncSetAttribute(k_own_project64<NPAD, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)shm));
+    if (c->sf_lean)   // step 2 sharing the SMs with a lean loop kernel: whole shared memory configured
+      PAW_CUDA(cudaFuncSetAttribute(k_own_project64<NPAD, double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    cudaSharedmemCarveoutMaxShared));
     dim3 g((ncols + 31) / 32, c->ncells);
     k_own_project64<NPAD, double><<<g, 256, shm, s>>>(c->n, c->p, c->N1, c->own_off.as<int>(), c->own_cnt.as<int>(),
                                              c->own_sidx.as<int16_t>(), c->ownP64.as<double>(), X, ldx, ncols,
@@ -788,7 +791,7 @@ static void project_impl(paw_context *c, const T *X, int ldx, int ncols, const T
   }
 }
 
-// U = P^T (rowscale .* X) into c->ws_partial (natoms x npad x ncols): per-pair
+// U = P^T (rowscale .* X) into c->scr->partial (natoms x npad x ncols): per-pair
 // partials, then a fixed-order sum per atom (deterministic, no atomics)
 // tensor-core form: FP32 data, TF32 or BF16 filter precision, supported layout
 template <typename T>
@@ -800,9 +803,9 @@ template <typename T>
 static T *project_U(paw_context *c, paw_precision prec, const T *X, int ldx, int ncols, const T *rowscale,
                     cudaStream_t s) {
   const size_t ub = sizeof(T) * (size_t)c->natoms * c->npad * ncols;
-  c->ws_partial.ensure(ub, &c->dev_bytes);
-  c->ws_pp.ensure(sizeof(T) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
-  T *U = c->ws_partial.as<T>(), *PP = c->ws_pp.as<T>();
+  c->scr->partial.ensure(ub, &c->dev_bytes);
+  c->scr->pp.ensure(sizeof(T) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
+  T *U = c->scr->partial.as<T>(), *PP = c->scr->pp.as<T>();
   if constexpr (sizeof(T) == 4) {
     if (use_tc<T>(c, prec)) {
       if (nltc_project(c, X, ldx, ncols, rowscale, PP, U, s)) return U;   // reduced in the epilogue
@@ -890,9 +893,9 @@ void nl_residual_pair(paw_context *c, const double *X, int ldx, int ncols, const
   }
   const f32x2 *oP = c->ownPx2.as<f32x2>();
   const size_t ub = sizeof(double) * (size_t)c->natoms * c->npad * ncols;
-  c->ws_partial.ensure(ub, &c->dev_bytes);
-  c->ws_pp.ensure(sizeof(double) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
-  double *U = c->ws_partial.as<double>(), *PP = c->ws_pp.as<double>();
+  c->scr->partial.ensure(ub, &c->dev_bytes);
+  c->scr->pp.ensure(sizeof(double) * (size_t)c->nown_pairs * c->npad * ncols, &c->dev_bytes);
+  double *U = c->scr->partial.as<double>(), *PP = c->scr->pp.as<double>();
   const size_t shm = sizeof(f32x2) * ((size_t)c->own * 32 + (size_t)8 * c->npad * 32);
   PAW_REQUIRE(shm <= 200 * 1024 && c->own <= OWN_MAX, PAW_ERR_UNSUPPORTED,
               "projection tile exceeds shared memory (degree too high)");
@@ -906,18 +909,18 @@ void nl_residual_pair(paw_context *c, const double *X, int ldx, int ncols, const
   k_pair_reduce<double><<<gr, 32, 0, s>>>(c->apair_off.as<int>(), c->apair.as<int>(), PP, c->npad, ncols, U);
   PAW_LAUNCH_CHECK("k_pair_reduce");
   const int64_t nw = (int64_t)c->natoms * c->npad * ncols;
-  c->ws_W2.ensure(sizeof(double) * std::max<int64_t>(1, nw), &c->dev_bytes);
-  c->ws_Wx2.ensure(sizeof(f32x2) * std::max<int64_t>(1, nw), &c->dev_bytes);
-  double *W = c->ws_W2.as<double>();
+  c->scr->W2.ensure(sizeof(double) * std::max<int64_t>(1, nw), &c->dev_bytes);
+  c->scr->Wx2.ensure(sizeof(f32x2) * std::max<int64_t>(1, nw), &c->dev_bytes);
+  double *W = c->scr->W2.as<double>();
   couple<double>(c, U, C, C2, cs, 1.0, W, ncols, s);
-  to_pair(W, nw, c->ws_Wx2.as<f32x2>(), s);
+  to_pair(W, nw, c->scr->Wx2.as<f32x2>(), s);
   ExpArgs A = exp_args(c, ncols);
   A.Y = Y;
   A.ldy = ldy;
   A.ldx = ldy;
   A.ldy0 = 4;
   dim3 ge((ncols + 31) / 32, c->ncells);
-  const f32x2 *Wx = c->ws_Wx2.as<f32x2>();
+  const f32x2 *Wx = c->scr->Wx2.as<f32x2>();
   if (c->npad == 16)
     k_own_expand64<16, EXP_ADD, f32x2><<<ge, 256, 0, s>>>(A, oP, c->own_lg.as<int8_t>(), Wx, nullptr);
   else

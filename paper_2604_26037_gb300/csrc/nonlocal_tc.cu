@@ -489,8 +489,10 @@ __global__ void k_build_expB(const float *__restrict__ oP, const int *__restrict
 
 // ------------------------------------------------------------------ streaming forms
 // Persistent warp-specialised forms (tc_stream.cuh) for 16-byte-aligned rows.
+// LEAN: two stages, the form used while an FP64 step 2 shares the SMs.
+template <bool LEAN = false>
 struct ProjStream {
-  static constexpr int NW = 1, S = 4, NEPI = 4;
+  static constexpr int NW = 1, S = LEAN ? 2 : 4, NEPI = 4;
   static constexpr bool BF16 = false;
   static constexpr uint32_t B_MAX = 192u * 128u;
   CUtensorMap tm[NW];   // rows of X (gathered with TMA)
@@ -1024,6 +1026,9 @@ template <class P>
 static void launch_stream(const paw_context *c, const P &p, cudaStream_t s, const char *what) {
   const size_t shm = tcs::Geo<P>::SMEM;
   PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (c->lean)   // the whole shared memory configured, so that an FP64 CTA fits beside this one
+    PAW_CUDA(cudaFuncSetAttribute(tcs::k_tc_stream<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
   const int grid = std::max(1, std::min(p.ntiles, persistent_grid(c)));
   tcs::k_tc_stream<P><<<grid, tcs::threads_for(P::NEPI), shm, s>>>(p, c->status_dev.as<int>(), c->wait_ns,
                                                                      c->wait_probe);
@@ -1034,6 +1039,32 @@ static bool rows16(const void *p, int ld) {
   return reinterpret_cast<uintptr_t>(p) % 16 == 0 && ld % 4 == 0;
 }
 
+template <bool LEAN>
+static void proj_stream(paw_context *c, const float *X, int ldx, int ncols, bool scaled, float *U, int vtiles,
+                        cudaStream_t s) {
+  const NlTcMats &N = c->nltc;
+  ProjStream<LEAN> p;
+  p.ntiles = c->ncells * vtiles;
+  p.ncols = ncols;
+  p.n = c->n;
+  p.p = c->p;
+  p.N1 = c->N1;
+  p.own = c->own;
+  p.npad = c->npad;
+  p.kc_own = N.kc_own;
+  p.ppt = N.ppt;
+  p.vtiles = vtiles;
+  p.ldx = ldx;
+  p.own_off = c->own_off.as<int>();
+  p.own_atom = c->own_atom.as<int>();
+  p.B = scaled ? N.projBs.as<uint8_t>() : N.projB.as<uint8_t>();
+  p.X = X;
+  p.U = U;
+  PAW_CUDA(cudaMemsetAsync(U, 0, sizeof(float) * (size_t)c->natoms * c->npad * ncols, s));
+  encode_row_map(&p.tm[0], X, c->ndof, ncols, ldx);
+  launch_stream(c, p, s, LEAN ? "k_tc_stream<projection, lean>" : "k_tc_stream<projection>");
+}
+
 bool nltc_project(paw_context *c, const float *X, int ldx, int ncols, const float *rowscale, float *PP,
                   float *U, cudaStream_t s) {
   if (ncols <= 0) return false;
@@ -1042,26 +1073,10 @@ bool nltc_project(paw_context *c, const float *X, int ldx, int ncols, const floa
   const int vtiles = (ncols + MT - 1) / MT;
   const bool scaled = rowscale != nullptr && rowscale == c->md_inv32.as<float>();
   if (c->tc_variant == 0 && (rowscale == nullptr || scaled) && rows16(X, ldx) && ncols % 4 == 0) {
-    ProjStream p;
-    p.ntiles = c->ncells * vtiles;
-    p.ncols = ncols;
-    p.n = c->n;
-    p.p = c->p;
-    p.N1 = c->N1;
-    p.own = c->own;
-    p.npad = c->npad;
-    p.kc_own = N.kc_own;
-    p.ppt = N.ppt;
-    p.vtiles = vtiles;
-    p.ldx = ldx;
-    p.own_off = c->own_off.as<int>();
-    p.own_atom = c->own_atom.as<int>();
-    p.B = scaled ? N.projBs.as<uint8_t>() : N.projB.as<uint8_t>();
-    p.X = X;
-    p.U = U;
-    PAW_CUDA(cudaMemsetAsync(U, 0, sizeof(float) * (size_t)c->natoms * c->npad * ncols, s));
-    encode_row_map(&p.tm[0], X, c->ndof, ncols, ldx);
-    launch_stream(c, p, s, "k_tc_stream<projection>");
+    if (c->lean)
+      proj_stream<true>(c, X, ldx, ncols, scaled, U, vtiles, s);
+    else
+      proj_stream<false>(c, X, ldx, ncols, scaled, U, vtiles, s);
     return true;   // U holds the per-atom sums
   }
   ProjTcArgs a;
@@ -1129,6 +1144,8 @@ static void expand_stream(paw_context *c, const ExpArgs &A, const float *W1, con
       encode_row_map(&p.tm[k], static_cast<const float *>(arr[k]), c->ndof, A.ncols, ld[k]);
       p.amask |= 1 << k;
     }
+  // (the expansion keeps its four staged groups while a step 2 shares the SMs: a two-group
+  // form, 160 KB, still leaves too little room for the FP64 kernel and slowed the loop)
   const size_t shm = xs::smem_bytes<MODE>();
   PAW_CUDA(cudaFuncSetAttribute(xs::k_exp_stream<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const int grid = std::max(1, std::min(p.ntiles, persistent_grid(c)));

@@ -134,15 +134,13 @@ struct Half {
 
 // cK reaches the kernel folded into tab.kD and tab.kM (the host scales the tables);
 // the parameter stays in the launch signature for the call sites.
-template <int NP, typename R>
-__global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<NP, R>()) k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs,
-                                                  const R *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
-                                                  const double *__restrict__ X, int ldx, double *__restrict__ Y,
-                                                  int ldy, int ncols, double alpha, double cK, double cV,
-                                                  double cM, const double *__restrict__ cMcol) {
+template <int NP, typename R, int VT, int NT>
+__device__ __forceinline__ void sf_body(const SfTablesT<R> &tab, int ncells, const int *__restrict__ cell_dofs,
+                                        const R *__restrict__ wV,   // ncells x NQ^3 (w_q V_q)
+                                        const double *__restrict__ X, int ldx, double *__restrict__ Y, int ldy,
+                                        int ncols, double alpha, double cK, double cV, double cM,
+                                        const double *__restrict__ cMcol) {
   constexpr int NQ = NP + 1;
-  constexpr int VT = sf_vt_r<NP, R>();
-  constexpr int NT = sf_threads<R>();
   constexpr int N3 = NP * NP * NP;
   constexpr int S1 = (NQ * NP * NP > N3) ? NQ * NP * NP : N3;
   constexpr int S2 = (NQ * NQ * NP > N3) ? NQ * NQ * NP : N3;
@@ -320,6 +318,31 @@ __global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<NP, R>()) k_loc
   }
 }
 
+template <int NP, typename R>
+__global__ void __launch_bounds__(sf_threads<R>(), sf_min_blocks<NP, R>())
+    k_local_sf(SfTablesT<R> tab, int ncells, const int *__restrict__ cell_dofs, const R *__restrict__ wV,
+               const double *__restrict__ X, int ldx, double *__restrict__ Y, int ldy, int ncols, double alpha,
+               double cK, double cV, double cM, const double *__restrict__ cMcol) {
+  sf_body<NP, R, sf_vt_r<NP, R>(), sf_threads<R>()>(tab, ncells, cell_dofs, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV,
+                                                    cM, cMcol);
+}
+
+// Lean FP64 form (4 vectors, 256 threads, at most 120 registers, about 69 KB of
+// shared memory at degree 6): small enough to share an SM with a persistent
+// cell-product or projection kernel in its lean form when step 2 of one block
+// overlaps the loop of another (paw_cheb_filter).  (A 2-vector form, several
+// per SM, measured slower: 305 against 291 ms per mid filter call.)
+constexpr int SF_LEAN_VT = 4, SF_LEAN_THREADS = 256;
+template <int NP>
+__global__ void __maxnreg__(120)
+    k_local_sf_lean(SfTablesT<double> tab, int ncells, const int *__restrict__ cell_dofs,
+                    const double *__restrict__ wV, const double *__restrict__ X, int ldx, double *__restrict__ Y,
+                    int ldy, int ncols, double alpha, double cK, double cV, double cM,
+                    const double *__restrict__ cMcol) {
+  sf_body<NP, double, SF_LEAN_VT, SF_LEAN_THREADS>(tab, ncells, cell_dofs, wV, X, ldx, Y, ldy, ncols, alpha, cK, cV,
+                                                   cM, cMcol);
+}
+
 // Bloch term at a wavevector k: y = (h/2)^2 [k_x C (x) M (x) M + k_y M (x) C (x) M
 // + k_z M (x) M (x) C] x per cell (C = the skew 1D matrix (C1 - C1^T)/2,
 // C1[a][b] = int l_a l_b' dxi; M the 1D reference mass), accumulated into
@@ -443,19 +466,32 @@ void launch_bloch(paw_context *c, const BlochTables &t, const double *X, int ldx
   PAW_LAUNCH_CHECK("k_bloch_sf");
 }
 
-template <int NP, typename R>
+template <int NP, typename R, int VT = sf_vt_r<NP, R>()>
 size_t sf_smem() {
   constexpr int NQ = NP + 1;
   constexpr int N3 = NP * NP * NP;
   constexpr int S1 = (NQ * NP * NP > N3) ? NQ * NP * NP : N3;
   constexpr int S2 = (NQ * NQ * NP > N3) ? NQ * NQ * NP : N3;
   constexpr int S3 = (NQ * NQ * NQ > N3) ? NQ * NQ * NQ : N3;
-  return sizeof(double) * ((size_t)(2 * N3 + S1 + S2 + S3) * sf_vt_r<NP, R>() + NQ * NQ * NQ);
+  return sizeof(double) * ((size_t)(2 * N3 + S1 + S2 + S3) * VT + NQ * NQ * NQ);
 }
 
 template <int NP, typename R>
 void launch_sf(paw_context *c, const SfTablesT<R> &t, const R *wV, const double *X, int ldx, double *Y, int ldy,
                int ncols, double alpha, double cK, double cV, double cM, const double *cMcol, cudaStream_t s) {
+  if constexpr (std::is_same<R, double>::value) {
+    if (c->sf_lean) {
+      const size_t shm = sf_smem<NP, double, SF_LEAN_VT>();
+      PAW_CUDA(cudaFuncSetAttribute(k_local_sf_lean<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      PAW_CUDA(cudaFuncSetAttribute(k_local_sf_lean<NP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    cudaSharedmemCarveoutMaxShared));
+      dim3 g(c->ncells, (ncols + SF_LEAN_VT - 1) / SF_LEAN_VT);
+      k_local_sf_lean<NP><<<g, SF_LEAN_THREADS, shm, s>>>(t, c->ncells, c->cell_dofs.as<int>(), wV, X, ldx, Y, ldy,
+                                                            ncols, alpha, cK, cV, cM, cMcol);
+      PAW_LAUNCH_CHECK("k_local_sf_lean");
+      return;
+    }
+  }
   const size_t shm = sf_smem<NP, R>();
   PAW_CUDA(cudaFuncSetAttribute(k_local_sf<NP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 g(c->ncells, (ncols + sf_vt_r<NP, R>() - 1) / sf_vt_r<NP, R>());

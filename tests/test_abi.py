@@ -57,7 +57,7 @@ def _create(lib, **kw):
     h = C.c_void_p()
     opts = None
     if "kpoint" in args:
-        opts = C.byref(L._Opts(0, 0, 0, 0, (C.c_double * 3)(*args["kpoint"]), int(args.get("y0_pair32", 0))))
+        opts = C.byref(L._Opts(0, 0, 0, 0, (C.c_double * 3)(*args["kpoint"]), int(args.get("y0_pair32", 0)), 0))
     code = lib.paw_fe_create(C.byref(mesh), args["degree"], C.byref(atoms), C.byref(proj),
                              D.ctypes.data_as(L._DP), dS.ctypes.data_as(L._DP), None, opts, C.byref(h))
     return code, lib.paw_last_error().decode()

@@ -65,3 +65,22 @@ def test_filter_rejects_bad_bounds():
     with pytest.raises(P.PawError) as ei:
         fe.cheb_filter(to_dev(Psi), lam, 5, (1.0, 0.5, 3.0))
     assert ei.value.status == "PAW_ERR_INVALID_ARG"
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_overlapped_blocks_match_serial_schedule(prec):
+    """Three blocks (32 + 32 + 16 columns): step 2 of each next block overlaps the loop of the
+    current one on two internal streams (the default), or the blocks run one after another.
+    Both schedules do the same arithmetic on each column, apart from the order of FP32
+    additions, and both match the oracle."""
+    op, Psi, lam, bounds = _inputs("p6", 80)
+    fe_o = gpu_fe("p6", block=32)
+    fe_s = gpu_fe("p6", block=32, overlap=False)
+    X = to_dev(Psi)
+    out_o = fe_o.cheb_filter(X, lam, 8, bounds, prec=prec)
+    out_s = fe_s.cheb_filter(X, lam, 8, bounds, prec=prec)
+    fe_o.sync_status()
+    ref = cheb.rchfsi_filter(op.apply_H, op.apply_S, op.apply_Sinv_approx, Psi, lam, 8, *bounds)
+    o, s_ = out_o.cpu().numpy(), out_s.cpu().numpy()
+    assert rel_err(o, ref) < TOL[prec] and rel_err(s_, ref) < TOL[prec]
+    assert rel_err(o, s_) < (1e-5 if prec == "fp32" else 4e-3)
