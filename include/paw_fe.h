@@ -406,8 +406,11 @@ paw_status paw_density(paw_handle h, paw_precision prec, const void *X, int ld, 
 
 /* Phase timing of paw_cheb_filter (tracing, not part of the method).  When
  * enabled, every phase of Algorithm 2 is bracketed by CUDA events recorded on
- * the caller's stream; paw_profile_read synchronises and returns the summed
- * device time per phase and the number of kernels the library launched.
+ * the stream that runs it (the caller's stream, or the handle's internal
+ * streams when paw_cheb_filter overlaps its blocks: a phase's time then
+ * includes the SMs it shares with the other stream); paw_profile_read
+ * synchronises and returns the summed device time per phase and the number of
+ * kernels the library launched.
  * Phases: 0 local part of Y = H X - S X Lambda (step 2, FP64 cell kernel),
  * 1 recurrence update fused with T = Shat^-1 R_Y and the nonlocal part of
  * alpha H T, 2 projector contraction P^T M_D^-1 R_Y and couplings, 3 cell

@@ -237,9 +237,27 @@ static void merge_cplx(paw_context *c, const T *Xs, int n, T *Z, int ldz, cudaSt
 static void residual_block(paw_context *c, const double *X, int ldx, const double *negLam_dev,
                            double *Y, int ldy, int ncols, cudaStream_t s) {
   zero_block<double>(Y, c->ndof, ncols, ldy, s);
+  const bool pair = c->opts.y0_pair32 != 0;   // pair-of-FP32 arithmetic (k = 0 only, checked at create)
+  // Both parts add into Y.  Beside a loop (the lean FP64 form) the nonlocal part goes
+  // first: its small blocks share the SMs with the loop better than the local kernel
+  // does, and the local kernel then runs alone once the loop has finished.
+  const bool nl_first = c->sf_lean != 0;
+  auto nonlocal = [&]() {
+    if (c->nown_pairs > 0 && pair) {
+      PhaseScope ps(c, 4, s);
+      nl_residual_pair(c, X, ldx, ncols, c->DH64.as<double>(), c->DS64.as<double>(), negLam_dev, Y, ldy, s);
+    } else if (c->nown_pairs > 0) {
+      PhaseScope ps(c, 4, s);
+      // sum_a P^a (D_H^a - lambda_j dS^a) P^a^T x_j: one projection, one expansion
+      c->scr->W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
+      double *W = c->scr->W2.as<double>();
+      nl_project_residual<double>(c, X, ldx, ncols, negLam_dev, W, s);
+      nl_expand<double>(c, PAW_FP64, W, ncols, Y, ldy, nullptr, s);
+    }
+  };
+  if (nl_first) nonlocal();
   // (1/2 K^e + V^e + (1/2 |k|^2 - lambda_j) M^e) X_e in one sum-factorised pass;
   // at k != 0 the Bloch term -i B of Eq. hij on the split block [Re | Im]
-  const bool pair = c->opts.y0_pair32 != 0;   // pair-of-FP32 arithmetic (k = 0 only, checked at create)
   {
     PhaseScope ps(c, 0, s);
     local_sf(c, X, ldx, Y, ldy, ncols, 1.0, 1.0, 1.0, c->kmass, negLam_dev, s, pair);
@@ -248,17 +266,7 @@ static void residual_block(paw_context *c, const double *X, int ldx, const doubl
       bloch_sf(c, X, ldx, Y + ncols / 2, ldy, ncols / 2, -1.0, s);
     }
   }
-  if (c->nown_pairs > 0 && pair) {
-    PhaseScope ps(c, 4, s);
-    nl_residual_pair(c, X, ldx, ncols, c->DH64.as<double>(), c->DS64.as<double>(), negLam_dev, Y, ldy, s);
-  } else if (c->nown_pairs > 0) {
-    PhaseScope ps(c, 4, s);
-    // sum_a P^a (D_H^a - lambda_j dS^a) P^a^T x_j: one projection, one expansion
-    c->scr->W2.ensure(sizeof(double) * (size_t)c->natoms * c->npad * ncols, &c->dev_bytes);
-    double *W = c->scr->W2.as<double>();
-    nl_project_residual<double>(c, X, ldx, ncols, negLam_dev, W, s);
-    nl_expand<double>(c, PAW_FP64, W, ncols, Y, ldy, nullptr, s);
-  }
+  if (!nl_first) nonlocal();
 }
 
 template <typename T>
@@ -991,7 +999,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->DH64, &c->DS64, &c->DSinv64, &c->ws_W, &c->ws_RX,
                     &c->ws_RY, &c->ws_T, &c->ws_Y0f, &c->ws_colscale, &c->ws_red, &c->ws_vec,
                     &c->ws_HX, &c->ws_SX, &c->ws_Hp, &c->ws_Sp, &c->ws_eig, &c->ws_solver, &c->ws_info,
-                    &c->ws_rot, &c->ws_gram, &c->ws_cg, &c->wV, &c->ws_Y0lo, &c->gnb_off, &c->gnb_atom, &c->Gfull,
+                    &c->ws_rot, &c->ws_gram, &c->ws_cg, &c->wV, &c->ws_Y0lo, &c->gnb_off, &c->gnb_atom, &c->Gfull, &c->Fsh32, &c->DSinv32,
                     &c->Gfull32, &c->apair_off, &c->apair, &c->nltc.projB, &c->nltc.projBs, &c->nltc.expB, &c->nltc.mdo, &c->nltc.odof, &c->status_dev, &c->proj_ext_dev, &c->own_ngrp,
                     &c->own_lg, &c->own_sidx, &c->own_cnt, &c->Bk64, &c->Bk32, &c->tc_bk_tf32.He,
                     &c->tc_bk_bf16.He, &c->ws_cx, &c->ws_cy,
@@ -1045,6 +1053,7 @@ paw_status paw_set_dij(paw_handle c, const double *D_ij) {
   c->D = to_internal(c, D_ij);
   PAW_CUDA(cudaDeviceSynchronize());
   PAW_CUDA(cudaMemcpy(c->DH64.ptr, c->D.data(), sizeof(double) * c->D.size(), cudaMemcpyHostToDevice));
+  build_couple_f(c);   // the fused FP32 coupling carries D_H
   return PAW_OK;
   PAW_TRY_END
 }

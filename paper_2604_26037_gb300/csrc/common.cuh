@@ -216,6 +216,9 @@ struct paw_context {
   // nodes (CSR over atoms, a included); lets P^T Shat^-1 R follow from P^T M_D^-1 R
   pawfe::DevBuf gnb_off, gnb_atom;            // int32 natoms+1, ngpairs
   pawfe::DevBuf Gfull, Gfull32;               // FP64 / FP32 ngpairs * npad * npad
+  // FP32 coupling of the filter loop (k = 0): per Gram slot s (atoms a, b) the block
+  // F_s = D_H,a (delta_ab I - G_ab DeltaSinv_b), and DeltaSinv per atom, npad x npad each
+  pawfe::DevBuf Fsh32, DSinv32;
   int64_t ngpairs = 0;
   std::vector<double> mdinv_h;                // 1 / M_D on the host
   // couplings (FP64, natoms*npj*npj)
@@ -263,6 +266,9 @@ void build_tables(paw_context *c);
 void build_operators(paw_context *c, const paw_vloc *vloc);
 void rebuild_hamiltonian(paw_context *c);
 void build_couplings(paw_context *c);
+// F_s and DeltaSinv in FP32 for the fused coupling of the filter loop (after
+// build_couplings and after every change of D_H); synchronises the device
+void build_couple_f(paw_context *c);
 
 // ---------------------------------------------------------------- ops.cu
 // Y += alpha * colscale[j] * (sum_e Q_e^T A_e Q_e X)  with A_e = mats + e*stride

@@ -256,6 +256,105 @@ __global__ void __launch_bounds__(NPAD * 32) k_own_couple_h(int npj, const int *
   if (v < ncols) WH[((size_t)a * NPAD + al) * ncols + v] = (T)(scale * (double)w);
 }
 
+// Fused coupling of the FP32 filter loop.  Both outputs follow from U alone:
+//   W_S[a] = DeltaSinv_a U[a],
+//   W_H[a] = alpha D_H,a (U[a] - sum_b G_ab W_S[b]) = alpha sum_s F_s U[b_s],
+//   F_s    = D_H,a (delta_{a b_s} I - G_{a b_s} DeltaSinv_{b_s})
+// over the Gram slots s of atom a (its list holds a itself).  The blocks F_s are
+// formed once in FP64 (k_couple_f) and rounded to FP32, so one launch replaces
+// the chain W_S -> sum_b G_ab W_S[b] -> D_H (.), whose steps each waited on
+// global-memory latency.
+//
+// k_couple_f: block = atom a, thread (r, col) of an npad x npad tile.
+template <int NPAD>
+__global__ void __launch_bounds__(NPAD * NPAD) k_couple_f(int npj, const int *__restrict__ goff,
+                                                          const int *__restrict__ gatom, const double *__restrict__ G,
+                                                          const double *__restrict__ Dsinv,
+                                                          const double *__restrict__ DH, float *__restrict__ F,
+                                                          float *__restrict__ Ds32) {
+  __shared__ double M[NPAD][NPAD + 1];
+  const int a = blockIdx.x;
+  const int r = threadIdx.x / NPAD, col = threadIdx.x % NPAD;
+  const bool in = r < npj && col < npj;
+  const double *Da = DH + (size_t)a * npj * npj;
+  Ds32[((size_t)a * NPAD + r) * NPAD + col] = in ? (float)Dsinv[(size_t)a * npj * npj + r * npj + col] : 0.f;
+  for (int s = goff[a]; s < goff[a + 1]; ++s) {
+    const int b = gatom[s];
+    const double *Gs = G + (size_t)s * NPAD * NPAD;
+    const double *Db = Dsinv + (size_t)b * npj * npj;
+    double m = 0.0;   // (G_ab DeltaSinv_b)[r][col]
+    if (in)
+      for (int ga = 0; ga < npj; ++ga) m = fma(Gs[r * NPAD + ga], Db[ga * npj + col], m);
+    __syncthreads();   // the previous slot's readers of M are done
+    M[r][col] = m;
+    __syncthreads();
+    double f = 0.0;
+    if (in) {
+      f = (b == a) ? Da[r * npj + col] : 0.0;
+      for (int be = 0; be < npj; ++be) f = fma(-Da[r * npj + be], M[be][col], f);
+    }
+    F[((size_t)s * NPAD + r) * NPAD + col] = (float)f;
+  }
+}
+
+// k_own_couple_sh: block = (atom a, 32 vectors), lane = vector; warp w sums the
+// slots s = goff[a] + w, + NW, ... into all npj rows, the NW partial sums meet in
+// shared memory.  F rows are warp-uniform float4 loads (padded columns are zero),
+// U columns coalesced 128-byte loads.  Rows al >= npj of W_S and W_H are zero.
+template <int NPAD, int NW>
+__global__ void __launch_bounds__(NW * 32) k_own_couple_sh(int npj, const int *__restrict__ goff,
+                                                           const int *__restrict__ gatom, const float *__restrict__ F,
+                                                           const float *__restrict__ Ds, const float *__restrict__ U,
+                                                           float alpha, float *__restrict__ WS,
+                                                           float *__restrict__ WH, int ncols) {
+  __shared__ float red[NW][NPAD][32];
+  const int a = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int v = blockIdx.y * 32 + lane;
+  const int vc = v < ncols ? v : ncols - 1;   // in-range column for the loads of idle lanes
+  float acc[NPAD];
+#pragma unroll
+  for (int al = 0; al < NPAD; ++al) acc[al] = 0.f;
+  for (int s = goff[a] + w; s < goff[a + 1]; s += NW) {
+    const float *Ub = U + (size_t)gatom[s] * NPAD * ncols + vc;
+    float u[NPAD];
+#pragma unroll
+    for (int g = 0; g < NPAD; ++g) u[g] = g < npj ? Ub[(size_t)g * ncols] : 0.f;
+    const float4 *Fs = reinterpret_cast<const float4 *>(F + (size_t)s * NPAD * NPAD);
+#pragma unroll
+    for (int al = 0; al < NPAD; ++al) {
+      if (al < npj) {
+        float t = acc[al];
+#pragma unroll
+        for (int q = 0; q < NPAD / 4; ++q) {
+          const float4 f = __ldg(Fs + al * (NPAD / 4) + q);
+          t = fmaf(f.x, u[4 * q], t);
+          t = fmaf(f.y, u[4 * q + 1], t);
+          t = fmaf(f.z, u[4 * q + 2], t);
+          t = fmaf(f.w, u[4 * q + 3], t);
+        }
+        acc[al] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int al = 0; al < NPAD; ++al) red[w][al][lane] = acc[al];
+  __syncthreads();
+  const float *Ua = U + (size_t)a * NPAD * ncols + vc;
+  for (int al = w; al < NPAD; al += NW) {
+    float h = 0.f, sv = 0.f;
+    if (al < npj) {
+#pragma unroll
+      for (int k = 0; k < NW; ++k) h += red[k][al][lane];
+      const float *Dr = Ds + ((size_t)a * NPAD + al) * NPAD;
+      for (int g = 0; g < npj; ++g) sv = fmaf(Dr[g], Ua[(size_t)g * ncols], sv);
+    }
+    if (v < ncols) {
+      WS[((size_t)a * NPAD + al) * ncols + v] = sv;
+      WH[((size_t)a * NPAD + al) * ncols + v] = alpha * h;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ Bloch wavevector (k != 0)
 // Complex multivectors are split blocks [Re X | Im X] (nb = ncols / 2 columns
 // each) and the projectors C^{a,k} are stored as 2 np real projectors,
@@ -928,6 +1027,22 @@ void nl_residual_pair(paw_context *c, const double *X, int ldx, int ncols, const
   PAW_LAUNCH_CHECK("k_own_expand64");
 }
 
+void build_couple_f(paw_context *c) {
+  if (c->kc || c->natoms == 0 || c->ngpairs == 0) return;
+  PAW_REQUIRE(c->npad == 16 || c->npad == 32, PAW_ERR_UNSUPPORTED, "projector padding must be 16 or 32");
+  c->Fsh32.ensure(sizeof(float) * (size_t)c->ngpairs * c->npad * c->npad, &c->dev_bytes);
+  c->DSinv32.ensure(sizeof(float) * (size_t)c->natoms * c->npad * c->npad, &c->dev_bytes);
+  const int *go = c->gnb_off.as<int>(), *ga = c->gnb_atom.as<int>();
+  if (c->npad == 16)
+    k_couple_f<16><<<c->natoms, 16 * 16>>>(c->npj, go, ga, c->Gfull.as<double>(), c->DSinv64.as<double>(),
+                                           c->DH64.as<double>(), c->Fsh32.as<float>(), c->DSinv32.as<float>());
+  else
+    k_couple_f<32><<<c->natoms, 32 * 32>>>(c->npj, go, ga, c->Gfull.as<double>(), c->DSinv64.as<double>(),
+                                           c->DH64.as<double>(), c->Fsh32.as<float>(), c->DSinv32.as<float>());
+  PAW_LAUNCH_CHECK("k_couple_f");
+  PAW_CUDA(cudaDeviceSynchronize());
+}
+
 // atom-pair Gram blocks in the element type of the filter
 template <typename T>
 static const T *gram(paw_context *c);
@@ -941,6 +1056,20 @@ void nl_project_filter(paw_context *c, paw_precision prec, const T *RY, int ldr,
                        double alpha, T *WS, T *WH, cudaStream_t s) {
   if (c->nown_pairs == 0 || ncols <= 0) return;
   const T *U = project_U<T>(c, prec, RY, ldr, ncols, mdinv, s);
+  if constexpr (sizeof(T) == 4) {
+    if (!c->kc && c->Fsh32.ptr) {   // W_S and W_H in one launch
+      dim3 g(c->natoms, (ncols + 31) / 32);
+      const int *go = c->gnb_off.as<int>(), *ga = c->gnb_atom.as<int>();
+      if (c->npad == 16)
+        k_own_couple_sh<16, 8><<<g, 8 * 32, 0, s>>>(c->npj, go, ga, c->Fsh32.as<float>(), c->DSinv32.as<float>(), U,
+                                                    (float)alpha, WS, WH, ncols);
+      else
+        k_own_couple_sh<32, 4><<<g, 4 * 32, 0, s>>>(c->npj, go, ga, c->Fsh32.as<float>(), c->DSinv32.as<float>(), U,
+                                                    (float)alpha, WS, WH, ncols);
+      PAW_LAUNCH_CHECK("k_own_couple_sh");
+      return;
+    }
+  }
   couple<T>(c, U, c->DSinv64.as<double>(), nullptr, nullptr, 1.0, WS, ncols, s);
   if (c->kc) {
     dim3 gc(c->natoms, (ncols / 2 + 31) / 32);

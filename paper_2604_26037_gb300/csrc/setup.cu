@@ -857,6 +857,7 @@ void build_couplings(paw_context *c) {
     PAW_CUDA(cudaMemcpy(c->DS64.ptr, c->dS.data(), sizeof(double) * c->dS.size(), cudaMemcpyHostToDevice));
     PAW_CUDA(cudaMemcpy(c->DSinv64.ptr, c->Dsinv.data(), sizeof(double) * c->Dsinv.size(), cudaMemcpyHostToDevice));
   }
+  build_couple_f(c);
 }
 
 // ============================================================== small host linear algebra
