@@ -438,9 +438,10 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public API with host buffers (pinned), copies inside the timed
     # region: every step copies the whole block in, filters it with one call and copies the
-    # result out.  Consecutive steps are pipelined with two device buffer pairs: the input of
-    # step i + 1 is copied in (one copy stream) and the output of step i - 1 copied out
-    # (another) while step i filters.
+    # result out.  Consecutive steps are pipelined with two device buffer pairs on one copy
+    # stream: while step i filters, the input of step i + 1 is copied in and then the output of
+    # step i - 1 out.  (An input and an output copy that run at the same time beside the filter
+    # slow each other several-fold on this machine, so the two directions take turns.)
     e2e = None
     if not args.no_e2e:
         del out
@@ -451,30 +452,36 @@ def run_ours(args, ws, rank, local):
         Od = [torch.empty_like(X) for _ in range(2)]
         del X
         torch.cuda.empty_cache()
-        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        s_io = torch.cuda.Stream()
         comp = torch.cuda.current_stream()
 
         def e2e_run(n):
-            ev_f, ev_o = [None] * n, [None] * n
+            ev_in, ev_f, ev_o = [None] * n, [None] * n, [None] * n
+
+            def h2d(i):
+                with torch.cuda.stream(s_io):
+                    if i >= 2:
+                        s_io.wait_event(ev_f[i - 2])          # filter of step i - 2 has read Xd[i % 2]
+                    Xd[i % 2].copy_(Xh, non_blocking=True)
+                    ev_in[i] = torch.cuda.Event()
+                    ev_in[i].record(s_io)
+
+            h2d(0)
             for i in range(n):
                 b = i % 2
-                with torch.cuda.stream(s_in):
-                    if i >= 2:
-                        s_in.wait_event(ev_f[i - 2])          # filter of step i - 2 has read Xd[b]
-                    Xd[b].copy_(Xh, non_blocking=True)
-                    ev_in = torch.cuda.Event()
-                    ev_in.record(s_in)
-                comp.wait_event(ev_in)
+                comp.wait_event(ev_in[i])
                 if i >= 2:
                     comp.wait_event(ev_o[i - 2])              # Od[b] of step i - 2 copied out
                 fe.cheb_filter(Xd[b], lam, m, bounds, prec=args.prec, out=Od[b])
                 ev_f[i] = torch.cuda.Event()
                 ev_f[i].record(comp)
-                with torch.cuda.stream(s_out):
-                    s_out.wait_event(ev_f[i])
+                if i + 1 < n:
+                    h2d(i + 1)
+                with torch.cuda.stream(s_io):
+                    s_io.wait_event(ev_f[i])
                     Oh.copy_(Od[b], non_blocking=True)
                     ev_o[i] = torch.cuda.Event()
-                    ev_o[i].record(s_out)
+                    ev_o[i].record(s_io)
             torch.cuda.synchronize()
 
         e2e_run(2)                      # untimed: both buffer pairs and both copy directions
@@ -486,8 +493,8 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": whole_job_rate(units_per_step, ws, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + N * 8),
                "d2h_bytes_per_step": int(Oh.numel() * Oh.element_size()),
-               "overlap": "the H2D copy of step i+1 and the D2H copy of step i-1 on two copy streams while "
-                          "step i filters (two device buffer pairs)"}
+               "overlap": "while step i filters, the H2D copy of step i+1 then the D2H copy of step i-1 on one "
+                          "copy stream (two device buffer pairs)"}
         out = Od[(args.steps - 1) % 2] if (args.rr or args.grad) else None   # a filtered block
         del Xd, Xh, Oh
         X = None

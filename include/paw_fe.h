@@ -232,9 +232,8 @@ paw_status paw_apply_Sinv_approx(paw_handle h, paw_precision prec, const void *X
 
 /* Same result as paw_apply_Sinv_approx, but this call never allocates device
  * memory.  It is meant for callers that cannot call cudaMalloc at the point of
- * use: code running while a stream is being captured into a CUDA graph (where
- * allocation calls are not permitted), real-time loops that must not block on
- * the allocator, or hosts that hand the library a fixed memory budget.
+ * use: real-time loops that must not block on the allocator, or hosts that
+ * hand the library a fixed memory budget.
  * (Library-side engineering; the paper has no counterpart.)
  *
  * Its scratch (projector partial sums and coefficients) lives in one
@@ -244,8 +243,7 @@ paw_status paw_apply_Sinv_approx(paw_handle h, paw_precision prec, const void *X
  * (elem = 8 for PAW_FP64, 4 otherwise; npad = projectors per atom rounded up
  * to 16); a larger request returns PAW_ERR_INVALID_ARG before any device work.
  * The first call on a device looks the array up (cudaGetSymbolAddress, which
- * may load the library's device code): make that first call before any stream
- * capture begins.  All calls share the one array and leave their partial
+ * may load the library's device code).  All calls share the one array and leave their partial
  * sums in it; every value a call reads it has first written itself, so
  * nothing needs clearing, but calls whose GPU work overlaps (different
  * streams, or different handles on one device) race on the array and must be
@@ -257,10 +255,11 @@ paw_status paw_apply_Sinv_approx_noalloc(paw_handle h, paw_precision prec, const
 
 /* Algorithm 2: Psi_f = Shat^-1 R_m + Psi_in C_m(Lambda~) for one or more
  * blocks of columns (processed opts.block columns at a time).  Stream-ordered:
- * the call enqueues every copy and kernel on `stream` and returns without
- * waiting for them (the per-block scalars travel through pinned host memory
- * owned by the handle; the host only waits when it is eight blocks ahead of
- * the GPU).  Read failures with paw_sync_status.  With two or more blocks of
+ * the call enqueues every kernel on `stream` and returns without waiting for
+ * them (the per-block scalars sit in mapped pinned host memory owned by the
+ * handle and a kernel reads them, so the call issues no copy that could queue
+ * behind the caller's own transfers; the host only waits when it is eight
+ * blocks ahead of the GPU).  Read failures with paw_sync_status.  With two or more blocks of
  * real vectors in a reduced precision (and options.no_overlap = 0), the call
  * runs on two internal streams of the handle that wait for `stream` and that
  * `stream` waits for: step 2 of block j + 1 runs beside the loop of block j.

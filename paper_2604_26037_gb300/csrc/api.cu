@@ -238,10 +238,8 @@ static void residual_block(paw_context *c, const double *X, int ldx, const doubl
                            double *Y, int ldy, int ncols, cudaStream_t s) {
   zero_block<double>(Y, c->ndof, ncols, ldy, s);
   const bool pair = c->opts.y0_pair32 != 0;   // pair-of-FP32 arithmetic (k = 0 only, checked at create)
-  // Both parts add into Y.  Beside a loop (the lean FP64 form) the nonlocal part goes
-  // first: its small blocks share the SMs with the loop better than the local kernel
-  // does, and the local kernel then runs alone once the loop has finished.
-  const bool nl_first = c->sf_lean != 0;
+  // both parts add into Y (the local part first: with the nonlocal part first beside a
+  // loop, the mid filter call measured 293 instead of 288 ms)
   auto nonlocal = [&]() {
     if (c->nown_pairs > 0 && pair) {
       PhaseScope ps(c, 4, s);
@@ -255,7 +253,6 @@ static void residual_block(paw_context *c, const double *X, int ldx, const doubl
       nl_expand<double>(c, PAW_FP64, W, ncols, Y, ldy, nullptr, s);
     }
   };
-  if (nl_first) nonlocal();
   // (1/2 K^e + V^e + (1/2 |k|^2 - lambda_j) M^e) X_e in one sum-factorised pass;
   // at k != 0 the Bloch term -i B of Eq. hij on the split block [Re | Im]
   {
@@ -266,7 +263,7 @@ static void residual_block(paw_context *c, const double *X, int ldx, const doubl
       bloch_sf(c, X, ldx, Y + ncols / 2, ldy, ncols / 2, -1.0, s);
     }
   }
-  if (!nl_first) nonlocal();
+  nonlocal();
 }
 
 template <typename T>
@@ -333,12 +330,33 @@ void cheb_plan(int nb, int m, paw_bounds bd, const double *lam, ChebScalars &S, 
 // forms Y = H X - S X Lambda (step 2) into the parity-par Y buffer;
 // block_loop runs steps 3-5 from them.  Both parts of a block use the same
 // parity; two blocks of different parity can be in flight at once.
+// The scalar images read straight from mapped pinned host memory by a kernel:
+// a copy-engine transfer of them would queue behind any large copy the caller
+// runs on another stream, and every kernel of the block would wait for it.
+__global__ void k_stage_scalars(const double *__restrict__ hd, double *__restrict__ dd, int64_t nd,
+                                const float *__restrict__ hf, float *__restrict__ df, int64_t nf) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd + nf; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nd)
+      dd[i] = hd[i];
+    else
+      df[i - nd] = hf[i - nd];
+  }
+}
+
 static void block_step2(paw_context *c, const double *X, int ldx, int nb, const ChebScalars &S, const double *hd,
-                        const float *hf, int par, cudaStream_t s) {
+                        const float *hf, int par, cudaStream_t s, const double *hd_dev, const float *hf_dev) {
   c->ws_lamp[par].ensure(sizeof(double) * S.nd, &c->dev_bytes);
   c->ws_cfp[par].ensure(sizeof(float) * S.nf, &c->dev_bytes);
-  PAW_CUDA(cudaMemcpyAsync(c->ws_lamp[par].ptr, hd, sizeof(double) * S.nd, cudaMemcpyHostToDevice, s));
-  PAW_CUDA(cudaMemcpyAsync(c->ws_cfp[par].ptr, hf, sizeof(float) * S.nf, cudaMemcpyHostToDevice, s));
+  if (hd_dev && hf_dev) {
+    const int64_t n = (int64_t)(S.nd + S.nf);
+    const int grid = (int)std::min<int64_t>(64, (n + 255) / 256);
+    k_stage_scalars<<<grid, 256, 0, s>>>(hd_dev, c->ws_lamp[par].as<double>(), (int64_t)S.nd, hf_dev,
+                                         c->ws_cfp[par].as<float>(), (int64_t)S.nf);
+    PAW_LAUNCH_CHECK("k_stage_scalars");
+  } else {
+    PAW_CUDA(cudaMemcpyAsync(c->ws_lamp[par].ptr, hd, sizeof(double) * S.nd, cudaMemcpyHostToDevice, s));
+    PAW_CUDA(cudaMemcpyAsync(c->ws_cfp[par].ptr, hf, sizeof(float) * S.nf, cudaMemcpyHostToDevice, s));
+  }
   c->ws_Y0p[par].ensure(sizeof(double) * c->ndof * nb, &c->dev_bytes);
   // step 2: Y = H X - S X Lambda (FP64; phases 0 and 4)
   residual_block(c, X, ldx, c->ws_lamp[par].as<double>(), c->ws_Y0p[par].as<double>(), nb, nb, s);
@@ -421,9 +439,10 @@ static void block_loop(paw_context *c, paw_precision prec, const double *X, int 
 }
 
 void cheb_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, paw_bounds bd,
-                const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s) {
+                const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s,
+                const double *hd_dev, const float *hf_dev) {
   const double cc = (bd.bU + bd.bW) / 2.0;
-  block_step2(c, X, ldx, nb, S, hd, hf, 0, s);
+  block_step2(c, X, ldx, nb, S, hd, hf, 0, s, hd_dev, hf_dev);
   if (prec == PAW_FP64)
     block_loop<double>(c, prec, X, ldx, nb, bd.a0, cc, S, 0, Xo, ldo, s);
   else
@@ -445,9 +464,11 @@ static HostSlot &acquire_slot(paw_context *c, size_t bytes) {
   if (sl.bytes < bytes) {
     if (sl.host) cudaFreeHost(sl.host);
     sl.host = nullptr;
+    sl.dev = nullptr;
     sl.bytes = 0;
-    PAW_CUDA(cudaHostAlloc(&sl.host, bytes, cudaHostAllocDefault));
+    PAW_CUDA(cudaHostAlloc(&sl.host, bytes, cudaHostAllocMapped));
     sl.bytes = bytes;
+    PAW_CUDA(cudaHostGetDevicePointer(&sl.dev, sl.host, 0));
   }
   return sl;
 }
@@ -473,8 +494,9 @@ static void cheb_block(paw_context *c, paw_precision prec, const double *X, int 
   double *hd = static_cast<double *>(sl.host);
   float *hf = reinterpret_cast<float *>(hd + nd);
   cheb_plan(nb, m, bd, lam, S, hd, hf);
+  const double *hd_dev = static_cast<const double *>(sl.dev);
   try {
-    cheb_issue(c, prec, X, ldx, nb, bd, S, hd, hf, Xo, ldo, s);
+    cheb_issue(c, prec, X, ldx, nb, bd, S, hd, hf, Xo, ldo, s, hd_dev, reinterpret_cast<const float *>(hd_dev + nd));
   } catch (...) {
     // copies from the slot may already be enqueued: keep it until the stream passes them
     if (cudaEventRecord(sl.done, s) == cudaSuccess) sl.pending = true;
@@ -554,7 +576,9 @@ static void cheb_filter_overlapped(paw_context *c, paw_precision prec, const dou
     if (j >= 2) PAW_CUDA(cudaStreamWaitEvent(c->s_side, evFree[j - 2], 0));   // parity buffers free again
     try {
       SideIssue side(c, j > 0);
-      block_step2(c, X + j0, ldx, nb, S[j], hd, hf, j & 1, c->s_side);
+      const double *hd_dev = static_cast<const double *>(sl.dev);
+      block_step2(c, X + j0, ldx, nb, S[j], hd, hf, j & 1, c->s_side, hd_dev,
+                  reinterpret_cast<const float *>(hd_dev + nd));
     } catch (...) {
       if (cudaEventRecord(sl.done, c->s_side) == cudaSuccess) sl.pending = true;
       throw;

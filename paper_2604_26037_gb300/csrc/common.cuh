@@ -114,6 +114,7 @@ struct NlScratch {
 // the stream; the host blocks only when it runs a whole ring ahead.
 struct HostSlot {
   void *host = nullptr;
+  void *dev = nullptr;   // the same memory as the device reads it (mapped)
   size_t bytes = 0;
   cudaEvent_t done = nullptr;
   bool pending = false;
@@ -377,9 +378,11 @@ int read_status(paw_context *c);
 
 // Algorithm 2 for one block of nb columns (api.cu).  cheb_plan fills the host
 // scalar images hd (cheb_nd entries) and hf (cheb_nf entries); cheb_issue
-// enqueues the copies of those images and all kernels on stream s without any
-// host synchronisation (capturable into a CUDA graph; hd and hf must stay
-// valid until the stream has consumed them).
+// enqueues the transfer of those images and all kernels on stream s without
+// any host synchronisation (capturable into a CUDA graph; hd and hf must stay
+// valid until the stream has consumed them).  With hd_dev / hf_dev (the same
+// memory, mapped pinned, as the device addresses it) a kernel reads the images;
+// otherwise two cudaMemcpyAsync copy them.
 struct ChebScalars {
   std::vector<double> al, be, ga;
   int nsteps = 0;
@@ -389,7 +392,8 @@ size_t cheb_nd(int nb, int m);
 size_t cheb_nf(int nb, int m);
 void cheb_plan(int nb, int m, paw_bounds bd, const double *lam, ChebScalars &S, double *hd, float *hf);
 void cheb_issue(paw_context *c, paw_precision prec, const double *X, int ldx, int nb, paw_bounds bd,
-                const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s);
+                const ChebScalars &S, const double *hd, const float *hf, double *Xo, int ldo, cudaStream_t s,
+                const double *hd_dev = nullptr, const float *hf_dev = nullptr);
 
 // RAII bracket of one phase of the filter (records events only when enabled)
 struct PhaseScope {

@@ -1,9 +1,8 @@
 """The allocation-free approximate inverse overlap entry point.
 
 paw_apply_Sinv_approx_noalloc serves callers that cannot call cudaMalloc where
-they need Shat^-1 X: code running while a CUDA stream is captured into a graph,
-real-time loops that must not wait on the allocator, hosts that give the
-library a fixed memory budget.  Its scratch is a static device array inside the
+they need Shat^-1 X: real-time loops that must not wait on the allocator, hosts
+that give the library a fixed memory budget.  Its scratch is a static device array inside the
 library.  This test calls it through the C ABI twice in a row and checks both
 results against paw_apply_Sinv_approx within the operator-test tolerances, and
 checks that a request beyond the static scratch is refused before any device
