@@ -339,7 +339,7 @@ def run_ours(args, ws, rank, local):
                              y0_pair32=args.y0_pair32, overlap=not args.no_overlap)
     M, N, m = fe.ndof, cfg["nvec"], cfg["degree"]
     # the library overlaps the blocks of a call for real vectors in a reduced precision
-    overlapped = (not args.no_overlap and not kp and args.prec != "fp64" and N > cfg["block"])
+    overlapped = (not args.no_overlap and args.prec != "fp64" and N > cfg["block"])
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
     # at a Bloch wavevector k the vectors are complex (one complex vector = one vector of the metric)
     X = torch.randn((M, N), dtype=torch.complex128 if fe.complex else torch.float64, device="cuda", generator=g)
@@ -389,7 +389,7 @@ def run_ours(args, ws, rank, local):
     iso_run = None
     if overlapped and args.iso_steps > 0:
         fe_s = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, y0_pair32=args.y0_pair32,
-                                   overlap=False)
+                                   kpoint=kp, overlap=False)
         iso_run = timed(args.prec, args.iso_steps, 1, profile=True, h=fe_s)
         fe_s.close()
         del fe_s
@@ -440,8 +440,9 @@ def run_ours(args, ws, rank, local):
     # region: every step copies the whole block in, filters it with one call and copies the
     # result out.  Consecutive steps are pipelined with two device buffer pairs on one copy
     # stream: while step i filters, the input of step i + 1 is copied in and then the output of
-    # step i - 1 out.  (An input and an output copy that run at the same time beside the filter
-    # slow each other several-fold on this machine, so the two directions take turns.)
+    # step i - 1 out, each in 8 row chunks.  (An input and an output copy running at the same
+    # time beside the filter slow each other several-fold; chunks interleave better with the
+    # filter's traffic.)  Events around every copy and filter call give the per-step times.
     e2e = None
     if not args.no_e2e:
         del out
@@ -454,17 +455,25 @@ def run_ours(args, ws, rank, local):
         torch.cuda.empty_cache()
         s_io = torch.cuda.Stream()
         comp = torch.cuda.current_stream()
+        nchunk = 8
+        rows = (M + nchunk - 1) // nchunk
+        tev = lambda: torch.cuda.Event(enable_timing=True)
 
         def e2e_run(n):
             ev_in, ev_f, ev_o = [None] * n, [None] * n, [None] * n
+            spans = {"h2d": [], "filter": [], "d2h": []}
 
             def h2d(i):
                 with torch.cuda.stream(s_io):
                     if i >= 2:
                         s_io.wait_event(ev_f[i - 2])          # filter of step i - 2 has read Xd[i % 2]
-                    Xd[i % 2].copy_(Xh, non_blocking=True)
-                    ev_in[i] = torch.cuda.Event()
+                    a = tev()
+                    a.record(s_io)
+                    for r in range(0, M, rows):
+                        Xd[i % 2][r:r + rows].copy_(Xh[r:r + rows], non_blocking=True)
+                    ev_in[i] = tev()
                     ev_in[i].record(s_io)
+                    spans["h2d"].append((a, ev_in[i]))
 
             h2d(0)
             for i in range(n):
@@ -472,29 +481,40 @@ def run_ours(args, ws, rank, local):
                 comp.wait_event(ev_in[i])
                 if i >= 2:
                     comp.wait_event(ev_o[i - 2])              # Od[b] of step i - 2 copied out
+                f0 = tev()
+                f0.record(comp)
                 fe.cheb_filter(Xd[b], lam, m, bounds, prec=args.prec, out=Od[b])
-                ev_f[i] = torch.cuda.Event()
+                ev_f[i] = tev()
                 ev_f[i].record(comp)
+                spans["filter"].append((f0, ev_f[i]))
                 if i + 1 < n:
                     h2d(i + 1)
                 with torch.cuda.stream(s_io):
                     s_io.wait_event(ev_f[i])
-                    Oh.copy_(Od[b], non_blocking=True)
-                    ev_o[i] = torch.cuda.Event()
+                    o0 = tev()
+                    o0.record(s_io)
+                    for r in range(0, M, rows):
+                        Oh[r:r + rows].copy_(Od[b][r:r + rows], non_blocking=True)
+                    ev_o[i] = tev()
                     ev_o[i].record(s_io)
+                    spans["d2h"].append((o0, ev_o[i]))
             torch.cuda.synchronize()
+            return {k: [a.elapsed_time(e) for a, e in v] for k, v in spans.items()}
 
         e2e_run(2)                      # untimed: both buffer pairs and both copy directions
         _barrier(ws)
         t0 = time.perf_counter()
-        e2e_run(args.steps)
+        spans = e2e_run(args.steps)
         t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
         fe.sync_status()
         e2e = {"value": whole_job_rate(units_per_step, ws, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + N * 8),
                "d2h_bytes_per_step": int(Oh.numel() * Oh.element_size()),
+               "ms_per_step": round(t_e2e * 1e3, 3),
+               "step_ms": {k: [round(x, 2) for x in v] for k, v in spans.items()},
                "overlap": "while step i filters, the H2D copy of step i+1 then the D2H copy of step i-1 on one "
-                          "copy stream (two device buffer pairs)"}
+                          "copy stream, 8 row chunks each (two device buffer pairs); the first input and the "
+                          "last output copy are not overlapped"}
         out = Od[(args.steps - 1) % 2] if (args.rr or args.grad) else None   # a filtered block
         del Xd, Xh, Oh
         X = None

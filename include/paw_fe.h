@@ -145,8 +145,8 @@ typedef struct {
                           FP64 storage.  k = 0 only (else paw_fe_create returns
                           PAW_ERR_UNSUPPORTED).  Default 0: FP64, as Algorithm 2 */
   int32_t no_overlap;  /* 1: paw_cheb_filter runs its blocks one after another.
-                          Default 0: with two or more blocks of real vectors in
-                          PAW_FP32/TF32/BF16, step 2 (FP64) of block j + 1 runs
+                          Default 0: with two or more blocks (real, or complex
+                          at k != 0) in PAW_FP32/TF32/BF16, step 2 of block j + 1 runs
                           on an internal stream while the loop of block j runs
                           on another (the results are the same up to the order
                           of FP32 additions)                                    */
@@ -259,8 +259,8 @@ paw_status paw_apply_Sinv_approx_noalloc(paw_handle h, paw_precision prec, const
  * them (the per-block scalars sit in mapped pinned host memory owned by the
  * handle and a kernel reads them, so the call issues no copy that could queue
  * behind the caller's own transfers; the host only waits when it is eight
- * blocks ahead of the GPU).  Read failures with paw_sync_status.  With two or more blocks of
- * real vectors in a reduced precision (and options.no_overlap = 0), the call
+ * blocks ahead of the GPU).  Read failures with paw_sync_status.  With two or
+ * more blocks in a reduced precision (and options.no_overlap = 0), the call
  * runs on two internal streams of the handle that wait for `stream` and that
  * `stream` waits for: step 2 of block j + 1 runs beside the loop of block j.
  *   X_in      : device FP64 ndof x ncols (ld ldx), the block Psi_in

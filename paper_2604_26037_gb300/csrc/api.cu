@@ -566,18 +566,37 @@ static void cheb_filter_overlapped(paw_context *c, paw_precision prec, const dou
   PAW_CUDA(cudaStreamWaitEvent(c->s_side, ev0, 0));
   std::vector<ChebScalars> S(nbk);
   std::vector<cudaEvent_t> evY(nbk), evFree(nbk);
+  // At k != 0 a block of nb complex columns is filtered as the split real block
+  // [Re | Im] of 2 nb columns (every eigenvalue estimate applying to both halves):
+  // split on the side stream before step 2, merged on the loop stream after it.
+  const int cw = c->kc ? 2 : 1;
+  if (c->kc)
+    for (int p = 0; p < std::min(nbk, 2); ++p) {
+      c->ws_cxp[p].ensure(sizeof(double) * (size_t)c->ndof * 2 * B, &c->dev_bytes);
+      c->ws_cyp[p].ensure(sizeof(double) * (size_t)c->ndof * 2 * B, &c->dev_bytes);
+    }
+  auto block_in = [&](int j) -> const double * {
+    return c->kc ? c->ws_cxp[j & 1].as<double>() : X + (size_t)j * B;
+  };
   auto issue_step2 = [&](int j) {
-    const int j0 = j * B, nb = std::min(B, ncols - j0);
-    const size_t nd = cheb_nd(nb, m), nf = cheb_nf(nb, m);
+    const int j0 = j * B, nb = std::min(B, ncols - j0), nr = cw * nb;
+    const size_t nd = cheb_nd(nr, m), nf = cheb_nf(nr, m);
     HostSlot &sl = acquire_slot(c, sizeof(double) * nd + sizeof(float) * nf);
     double *hd = static_cast<double *>(sl.host);
     float *hf = reinterpret_cast<float *>(hd + nd);
-    cheb_plan(nb, m, bd, lam + j0, S[j], hd, hf);
+    if (c->kc) {
+      std::vector<double> lam2(2 * (size_t)nb);
+      for (int i = 0; i < nb; ++i) lam2[i] = lam2[nb + i] = lam[j0 + i];
+      cheb_plan(nr, m, bd, lam2.data(), S[j], hd, hf);
+    } else {
+      cheb_plan(nr, m, bd, lam + j0, S[j], hd, hf);
+    }
     if (j >= 2) PAW_CUDA(cudaStreamWaitEvent(c->s_side, evFree[j - 2], 0));   // parity buffers free again
     try {
       SideIssue side(c, j > 0);
       const double *hd_dev = static_cast<const double *>(sl.dev);
-      block_step2(c, X + j0, ldx, nb, S[j], hd, hf, j & 1, c->s_side, hd_dev,
+      if (c->kc) split_cplx<double>(c, X + 2 * (size_t)j0, ldx, nb, c->ws_cxp[j & 1].as<double>(), c->s_side);
+      block_step2(c, block_in(j), c->kc ? nr : ldx, nr, S[j], hd, hf, j & 1, c->s_side, hd_dev,
                   reinterpret_cast<const float *>(hd_dev + nd));
     } catch (...) {
       if (cudaEventRecord(sl.done, c->s_side) == cudaSuccess) sl.pending = true;
@@ -591,11 +610,17 @@ static void cheb_filter_overlapped(paw_context *c, paw_precision prec, const dou
   issue_step2(0);
   for (int j = 0; j < nbk; ++j) {
     if (j + 1 < nbk) issue_step2(j + 1);
-    const int j0 = j * B, nb = std::min(B, ncols - j0);
+    const int j0 = j * B, nb = std::min(B, ncols - j0), nr = cw * nb;
     PAW_CUDA(cudaStreamWaitEvent(c->s_loop, evY[j], 0));
     {
       LeanLoop lean(c, j + 1 < nbk);   // a step 2 shares the SMs with this loop
-      block_loop<float>(c, prec, X + j0, ldx, nb, bd.a0, cc, S[j], j & 1, Xo + j0, ldo, c->s_loop);
+      if (c->kc) {
+        double *Y = c->ws_cyp[j & 1].as<double>();
+        block_loop<float>(c, prec, block_in(j), nr, nr, bd.a0, cc, S[j], j & 1, Y, nr, c->s_loop);
+        merge_cplx<double>(c, Y, nb, Xo + 2 * (size_t)j0, ldo, c->s_loop);
+      } else {
+        block_loop<float>(c, prec, X + j0, ldx, nb, bd.a0, cc, S[j], j & 1, Xo + j0, ldo, c->s_loop);
+      }
     }
     evFree[j] = next_event(c);
     PAW_CUDA(cudaEventRecord(evFree[j], c->s_loop));
@@ -1030,7 +1055,7 @@ paw_status paw_destroy(paw_handle c) {
                     &c->nltc.eoff, &c->ownPx2, &c->wVx2,
                     &c->scr_main.partial, &c->scr_main.pp, &c->scr_main.W2, &c->scr_main.Wx2,
                     &c->scr_side.partial, &c->scr_side.pp, &c->scr_side.W2, &c->scr_side.Wx2,
-                    &c->ws_Y0p[0], &c->ws_Y0p[1], &c->ws_lamp[0], &c->ws_lamp[1], &c->ws_cfp[0], &c->ws_cfp[1]};
+                    &c->ws_Y0p[0], &c->ws_Y0p[1], &c->ws_cxp[0], &c->ws_cxp[1], &c->ws_cyp[0], &c->ws_cyp[1], &c->ws_lamp[0], &c->ws_lamp[1], &c->ws_cfp[0], &c->ws_cfp[1]};
   for (DevBuf *b : bufs) b->release(&c->dev_bytes);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -1140,9 +1165,9 @@ paw_status paw_cheb_filter(paw_handle c, paw_precision prec, const double *X_in,
   auto s = (cudaStream_t)stream;
   c->last_stream = s;
   const int B = c->opts.block;
-  // reduced-precision filter of real vectors over two or more blocks: step 2 of
-  // the next block overlaps the loop of the current one
-  if (!c->kc && prec != PAW_FP64 && ncols > B && c->opts.no_overlap == 0) {
+  // reduced-precision filter over two or more blocks: step 2 of the next block
+  // overlaps the loop of the current one
+  if (prec != PAW_FP64 && ncols > B && c->opts.no_overlap == 0) {
     cheb_filter_overlapped(c, prec, X_in, ldx, lambda_in, ncols, degree, b, X_out, ldo, s);
     return PAW_OK;
   }

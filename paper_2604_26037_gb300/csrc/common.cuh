@@ -244,6 +244,7 @@ struct paw_context {
   pawfe::DevBuf ws_gram;                      // split partial tiles of the RR projection
   pawfe::DevBuf ws_cg;                        // real 2N x 2N Gram / rotation matrix (k != 0)
   pawfe::DevBuf ws_cx, ws_cy;                 // split [Re | Im] copies of complex arguments (k != 0)
+  pawfe::DevBuf ws_cxp[2], ws_cyp[2];         // the same per block parity (overlapped filter at k != 0)
 
   // tensor-core kernel family: 0 persistent warp-specialised where the layout
   // allows it, 1 one-CTA-per-tile kernels; grid_cap > 0 limits the CTAs of a

@@ -24,6 +24,15 @@ def system(name):
                            shells=[(0, 0.7), (1, 0.7), (2, 0.7)],
                            D=sym_random(rng, 2, 9, 0.1), dS=sym_random(rng, 2, 9, 0.02),
                            vdepth=2.0, vwidth=1.0)
+    if name == "w18":
+        # 18 projectors per atom (two s, two p and two d shells): the projector arrays are
+        # padded to 32 instead of 16; the two supports overlap, so the atom-pair Gram blocks
+        # between different atoms are non-zero
+        rng = np.random.default_rng(23)
+        return mini_system(L=10.0, n=3, p=4, positions=[[2.5, 3.0, 4.0], [6.5, 6.0, 5.5]],
+                           shells=[(0, 0.6), (0, 0.8), (1, 0.6), (1, 0.8), (2, 0.7), (2, 0.5)],
+                           D=sym_random(rng, 2, 18, 0.1), dS=sym_random(rng, 2, 18, 0.02),
+                           vdepth=2.0, vwidth=1.0)
     raise KeyError(name)
 
 

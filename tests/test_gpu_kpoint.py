@@ -85,6 +85,29 @@ def test_filter_at_k_in_blocks_with_a_ragged_tail():
     fe.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("tf32", 2e-2)])
+def test_filter_at_k_overlapped_blocks(prec, tol):
+    """21 complex columns in blocks of 8 (8, 8, 5): by default step 2 of each next block runs
+    beside the loop of the current one on the handle's two streams; it matches the
+    one-after-another schedule and the oracle."""
+    import paper_2604_26037_gb300 as P
+    op = kops("tiny")
+    fe_o = P.PawFE.from_system(system("tiny"), kpoint=KVEC["tiny"], block=8)
+    fe_s = P.PawFE.from_system(system("tiny"), kpoint=KVEC["tiny"], block=8, overlap=False)
+    X = cvec(op.mesh.ndof, 21, 16)
+    lam = np.linspace(-0.4, 0.3, 21)
+    bounds = (-0.6, 0.35, 95.0)
+    ref = cheb.rchfsi_filter(op.apply_H, op.apply_S, op.apply_Sinv_approx, X, lam, 5, *bounds)
+    Xd = to_dev(X)
+    o = fe_o.cheb_filter(Xd, lam, 5, bounds, prec=prec).cpu().numpy()
+    s_ = fe_s.cheb_filter(Xd, lam, 5, bounds, prec=prec).cpu().numpy()
+    fe_o.sync_status()
+    assert crel(o, ref) < tol and crel(s_, ref) < tol
+    assert crel(o, s_) < (1e-5 if prec == "fp32" else 4e-3)
+    fe_o.close()
+    fe_s.close()
+
+
 def test_rayleigh_ritz_and_residuals_at_k():
     import torch
     op, fe = kops("tiny"), kfe("tiny")
