@@ -438,22 +438,24 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public API with host buffers (pinned), copies inside the timed
     # region: every step copies the whole block in, filters it with one call and copies the
-    # result out.  Consecutive steps are pipelined with two device buffer pairs on one copy
-    # stream: while step i filters, the input of step i + 1 is copied in and then the output of
-    # step i - 1 out, each in 8 row chunks.  (An input and an output copy running at the same
-    # time beside the filter slow each other several-fold; chunks interleave better with the
-    # filter's traffic.)  Events around every copy and filter call give the per-step times.
+    # result out.  Consecutive steps are pipelined with three device buffer sets: the input of
+    # step i + 2 is copied in (one copy stream, once step i - 1 has read its buffer) and the
+    # output of step i out (another) while the filter calls run, each copy in 8 row chunks.  The
+    # copy rate between pinned host memory and the GPU varies several-fold from run to run on
+    # this machine (17 to 260 ms for the same 3.6 GB), so the inputs run two steps ahead.
+    # Events around every copy and filter call give the per-step times.
     e2e = None
     if not args.no_e2e:
         del out
         torch.cuda.empty_cache()
         Xh = X.cpu().pin_memory()
         Oh = torch.empty_like(Xh).pin_memory()
-        Xd = [torch.empty_like(X) for _ in range(2)]
-        Od = [torch.empty_like(X) for _ in range(2)]
+        NB = 3
+        Xd = [torch.empty_like(X) for _ in range(NB)]
+        Od = [torch.empty_like(X) for _ in range(NB)]
         del X
         torch.cuda.empty_cache()
-        s_io = torch.cuda.Stream()
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
         comp = torch.cuda.current_stream()
         nchunk = 8
         rows = (M + nchunk - 1) // nchunk
@@ -464,39 +466,40 @@ def run_ours(args, ws, rank, local):
             spans = {"h2d": [], "filter": [], "d2h": []}
 
             def h2d(i):
-                with torch.cuda.stream(s_io):
-                    if i >= 2:
-                        s_io.wait_event(ev_f[i - 2])          # filter of step i - 2 has read Xd[i % 2]
+                with torch.cuda.stream(s_in):
+                    if i >= NB:
+                        s_in.wait_event(ev_f[i - NB])         # the filter of step i - NB has read the buffer
                     a = tev()
-                    a.record(s_io)
+                    a.record(s_in)
                     for r in range(0, M, rows):
-                        Xd[i % 2][r:r + rows].copy_(Xh[r:r + rows], non_blocking=True)
+                        Xd[i % NB][r:r + rows].copy_(Xh[r:r + rows], non_blocking=True)
                     ev_in[i] = tev()
-                    ev_in[i].record(s_io)
+                    ev_in[i].record(s_in)
                     spans["h2d"].append((a, ev_in[i]))
 
-            h2d(0)
+            for i in range(min(n, NB - 1)):
+                h2d(i)
             for i in range(n):
-                b = i % 2
+                b = i % NB
                 comp.wait_event(ev_in[i])
-                if i >= 2:
-                    comp.wait_event(ev_o[i - 2])              # Od[b] of step i - 2 copied out
+                if i >= NB:
+                    comp.wait_event(ev_o[i - NB])             # Od[b] of step i - NB copied out
                 f0 = tev()
                 f0.record(comp)
                 fe.cheb_filter(Xd[b], lam, m, bounds, prec=args.prec, out=Od[b])
                 ev_f[i] = tev()
                 ev_f[i].record(comp)
                 spans["filter"].append((f0, ev_f[i]))
-                if i + 1 < n:
-                    h2d(i + 1)
-                with torch.cuda.stream(s_io):
-                    s_io.wait_event(ev_f[i])
+                if i + NB - 1 < n:
+                    h2d(i + NB - 1)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_f[i])
                     o0 = tev()
-                    o0.record(s_io)
+                    o0.record(s_out)
                     for r in range(0, M, rows):
                         Oh[r:r + rows].copy_(Od[b][r:r + rows], non_blocking=True)
                     ev_o[i] = tev()
-                    ev_o[i].record(s_io)
+                    ev_o[i].record(s_out)
                     spans["d2h"].append((o0, ev_o[i]))
             torch.cuda.synchronize()
             return {k: [a.elapsed_time(e) for a, e in v] for k, v in spans.items()}
@@ -512,10 +515,10 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": int(Oh.numel() * Oh.element_size()),
                "ms_per_step": round(t_e2e * 1e3, 3),
                "step_ms": {k: [round(x, 2) for x in v] for k, v in spans.items()},
-               "overlap": "while step i filters, the H2D copy of step i+1 then the D2H copy of step i-1 on one "
-                          "copy stream, 8 row chunks each (two device buffer pairs); the first input and the "
-                          "last output copy are not overlapped"}
-        out = Od[(args.steps - 1) % 2] if (args.rr or args.grad) else None   # a filtered block
+               "overlap": "three device buffer sets: the H2D copy of step i+2 (one copy stream) and the D2H copy "
+                          "of step i (another) run beside the filter calls, 8 row chunks each; the first input "
+                          "and the last output copy are not overlapped"}
+        out = Od[(args.steps - 1) % NB] if (args.rr or args.grad) else None   # a filtered block
         del Xd, Xh, Oh
         X = None
 

@@ -77,3 +77,26 @@ def test_filter_overlapped_schedule():
     o, s_ = out_o.cpu().numpy(), out_s.cpu().numpy()
     assert rel_err(o, ref) < TOL_FILTER["tf32"] and rel_err(s_, ref) < TOL_FILTER["tf32"]
     assert rel_err(o, s_) < 4e-3
+
+
+@pytest.mark.parametrize("name", ["p6", "w18"])
+def test_filter_after_set_dij(name):
+    """paw_set_dij after creation: the fused FP32 coupling of the loop (which carries D_H) is
+    rebuilt, so the TF32 filter matches the oracle built with the new D_ij."""
+    from oracle import ops as O
+    from tests.oracle_systems import sym_random
+    sysd = dict(system(name))
+    D2 = sym_random(np.random.default_rng(31), sysd["natoms"], sysd["nproj"], 0.2)
+    sysd["D"] = D2
+    op = O.PawOperators(sysd)
+    X = np.random.default_rng(7).standard_normal((op.mesh.ndof, 24))
+    Psi, lam = rr.rayleigh_ritz(op, X)
+    tmin, up = rr.lanczos_bounds(lambda x: op.apply_Sinv_exact(op.apply_H(x)), op.apply_S, op.mesh.ndof)
+    bounds = (min(lam[0], tmin) - 0.1, lam[-1], up)
+    fe = gpu_fe(name, block=16)
+    fe.set_dij(D2)
+    ref = cheb.rchfsi_filter(op.apply_H, op.apply_S, op.apply_Sinv_approx, Psi, lam, 8, *bounds)
+    out = fe.cheb_filter(to_dev(Psi), lam, 8, bounds, prec="tf32")
+    fe.sync_status()
+    assert rel_err(out.cpu().numpy(), ref) < TOL_FILTER["tf32"]
+    fe.close()
