@@ -243,7 +243,8 @@ paw_status paw_apply_Sinv_approx(paw_handle h, paw_precision prec, const void *X
  * (elem = 8 for PAW_FP64, 4 otherwise; npad = projectors per atom rounded up
  * to 16); a larger request returns PAW_ERR_INVALID_ARG before any device work.
  * The first call on a device looks the array up (cudaGetSymbolAddress, which
- * may load the library's device code).  All calls share the one array and leave their partial
+ * may load the library's device code), so make that first call on each device
+ * before any stream capture begins.  All calls share the one array and leave their partial
  * sums in it; every value a call reads it has first written itself, so
  * nothing needs clearing, but calls whose GPU work overlaps (different
  * streams, or different handles on one device) race on the array and must be
