@@ -464,6 +464,8 @@ def run_ours(args, ws, rank, local):
         def e2e_run(n):
             ev_in, ev_f, ev_o = [None] * n, [None] * n, [None] * n
             spans = {"h2d": [], "filter": [], "d2h": []}
+            t_first = tev()
+            t_first.record(comp)
 
             def h2d(i):
                 with torch.cuda.stream(s_in):
@@ -502,12 +504,13 @@ def run_ours(args, ws, rank, local):
                     ev_o[i].record(s_out)
                     spans["d2h"].append((o0, ev_o[i]))
             torch.cuda.synchronize()
-            return {k: [a.elapsed_time(e) for a, e in v] for k, v in spans.items()}
+            return ({k: [a.elapsed_time(e) for a, e in v] for k, v in spans.items()},
+                    {k: [t_first.elapsed_time(a) for a, _ in v] for k, v in spans.items()})
 
         e2e_run(2)                      # untimed: both buffer pairs and both copy directions
         _barrier(ws)
         t0 = time.perf_counter()
-        spans = e2e_run(args.steps)
+        spans, starts = e2e_run(args.steps)
         t_e2e = _max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
         fe.sync_status()
         e2e = {"value": whole_job_rate(units_per_step, ws, t_e2e * 1e3), "unit": UNIT,
@@ -515,6 +518,7 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": int(Oh.numel() * Oh.element_size()),
                "ms_per_step": round(t_e2e * 1e3, 3),
                "step_ms": {k: [round(x, 2) for x in v] for k, v in spans.items()},
+               "start_ms": {k: [round(x, 2) for x in v] for k, v in starts.items()},
                "overlap": "three device buffer sets: the H2D copy of step i+2 (one copy stream) and the D2H copy "
                           "of step i (another) run beside the filter calls, 8 row chunks each; the first input "
                           "and the last output copy are not overlapped"}
