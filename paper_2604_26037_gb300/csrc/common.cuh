@@ -16,6 +16,10 @@ namespace pawfe {
 // Atoms whose projectors reach the owned nodes of one cell: the owner-cell
 // kernels stage the atom list of a cell in shared memory (checked at set-up).
 constexpr int PAIRS_PER_CELL_MAX = 192;
+// Projectors per group of the FP64 / pair-of-FP32 owner-cell nonlocal kernels: a
+// node's projectors (stored by decreasing width) are multiplied group by group up
+// to the last group with a nonzero value on the node (own_lg, own_cnt).
+constexpr int OWN_GROUP = 2;
 
 // ---------------------------------------------------------------- errors
 struct Error {
@@ -210,7 +214,7 @@ struct paw_context {
   // The FP64 kernels multiply only groups that can be nonzero on a node.
   pawfe::DevBuf own_lg;                       // int8  nown_pairs * own
   pawfe::DevBuf own_sidx;                     // int16 nown_pairs * own
-  pawfe::DevBuf own_cnt;                      // int32 nown_pairs * npad/4
+  pawfe::DevBuf own_cnt;                      // int32 nown_pairs * npad/OWN_GROUP
   int64_t proj_nnz = 0;                       // nonzero (owned node, projector) entries over all pairs
   pawfe::DevBuf apair_off, apair;             // atom-major list of the pairs (int32)
   // atom-pair Gram blocks G_ab = P^a^T M_D^-1 P^b for atoms with common support

@@ -660,8 +660,10 @@ __global__ void __launch_bounds__(256, 2) k_own_expand(ExpArgs A, const T *__res
 // GB300 retires about one warp-wide FP64 FMA per 16 SM clocks, so the FP64
 // kernels spend FP64 instructions only where a projector can be nonzero: lane
 // = vector (32 per CTA), and every FP64 instruction of a warp belongs to one
-// owned node and one group of 4 projectors (warp-uniform control flow), taken
-// only up to the last group with a nonzero value on that node (own_lg).
+// owned node and one group of OWN_GROUP projectors (warp-uniform control flow),
+// taken only up to the last group with a nonzero value on that node (own_lg).
+// (Groups of 2 multiply 1.08 times the nonzero entries of P on the workloads
+// here, groups of 4 1.23 times.)
 // The same kernels run in pair-of-FP32 arithmetic (R = f32x2, f32x2.cuh) for
 // the FP64-class step 2 on the FP32 pipes: projector values and coefficients
 // then come as pairs, X and Y stay FP64.
@@ -694,7 +696,8 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
                                                        int ldx, int ncols, const double *__restrict__ rowscale,
                                                        double *__restrict__ U) {
   using A = Ar<R>;
-  constexpr int NG = NPAD / 4, NWARP = 8;
+  constexpr int G = OWN_GROUP, NG = NPAD / G, NWARP = 8;
+  static_assert(G % 2 == 0 && NPAD % G == 0, "groups of an even number of projectors");
   __shared__ int ooff[OWN_MAX];
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int e = blockIdx.y, v0 = blockIdx.x * 32;   // vector tiles of one cell are adjacent: P reused from L2
@@ -736,14 +739,14 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
 #pragma unroll
       for (int g = 0; g < NG; ++g)
         if (i < cg[g]) {
-          ldg2(Pr + 4 * g, pv[4 * g], pv[4 * g + 1]);
-          ldg2(Pr + 4 * g + 2, pv[4 * g + 2], pv[4 * g + 3]);
+#pragma unroll
+          for (int h = 0; h < G; h += 2) ldg2(Pr + G * g + h, pv[G * g + h], pv[G * g + h + 1]);
         }
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         if (i >= cg[g]) break;   // this and the later groups are zero on the node
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[4 * g + j] = A::fma(pv[4 * g + j], x, acc[4 * g + j]);
+        for (int j = 0; j < G; ++j) acc[G * g + j] = A::fma(pv[G * g + j], x, acc[G * g + j]);
       }
       o = onext;
     }
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(256) k_own_project64(int n, int p, int N1, con
     const int nwk = min(NWARP, cg[0]);
     int nact = 0;
 #pragma unroll
-    for (int g = 0; g < NG; ++g) nact += (cg[g] > 0) ? 4 : 0;
+    for (int g = 0; g < NG; ++g) nact += (cg[g] > 0) ? G : 0;
     if (warp < nwk) {
 #pragma unroll
       for (int al = 0; al < NPAD; ++al)
@@ -784,7 +787,8 @@ __global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const R *__rest
                                                       const int8_t *__restrict__ own_lg,
                                                       const R *__restrict__ W1, const R *__restrict__ W2) {
   using Q = Ar<R>;
-  constexpr int NG = NPAD / 4, NWARP = 8;
+  constexpr int G = OWN_GROUP, NG = NPAD / G, NWARP = 8;
+  static_assert(G % 2 == 0 && 4 % G == 0, "groups of 2 or 4 projectors");
   constexpr int NW = (MODE == EXP_RECURRENCE) ? 2 : 1;
   __shared__ int ooff[OWN_MAX];
   __shared__ int patom[PAIRS_PER_CELL_MAX];
@@ -814,14 +818,19 @@ __global__ void __launch_bounds__(256) k_own_expand64(ExpArgs A, const R *__rest
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
         if (g > lg) break;
-        R pv[4];
-        ldg2(Pr + 4 * g, pv[0], pv[1]);
-        ldg2(Pr + 4 * g + 2, pv[2], pv[3]);
+        R pv[G];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) s1[j] = Q::fma(pv[j], ldg1(w1 + (size_t)(4 * g + j) * ncols), s1[j]);
+        for (int h = 0; h < G; h += 2) ldg2(Pr + G * g + h, pv[h], pv[h + 1]);
+        // the four chains take the projectors of the group in turn (static indices)
+        constexpr int CH = 4 / G;
+        const int c0 = (g % CH) * G;
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+          s1[c0 + j] = Q::fma(pv[j], ldg1(w1 + (size_t)(G * g + j) * ncols), s1[c0 + j]);
         if constexpr (NW == 2) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) s2[j] = Q::fma(pv[j], ldg1(w2 + (size_t)(4 * g + j) * ncols), s2[j]);
+          for (int j = 0; j < G; ++j)
+            s2[c0 + j] = Q::fma(pv[j], ldg1(w2 + (size_t)(G * g + j) * ncols), s2[c0 + j]);
         }
       }
     }

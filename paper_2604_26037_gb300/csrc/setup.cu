@@ -624,7 +624,7 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
     PAW_CUDA(cudaMemcpy(c->own_ngrp.ptr, ngrp.data(), sizeof(int) * ngrp.size(), cudaMemcpyHostToDevice));
     // last nonzero group per (pair, owned node), nodes sorted by it, prefix counts per group
     {
-      const int ng4 = c->npad / 4, own = c->own;
+      const int ng4 = c->npad / OWN_GROUP, own = c->own;
       std::vector<int8_t> lg(std::max<size_t>(1, keys.size() * own), -1);
       std::vector<int16_t> sidx(std::max<size_t>(1, keys.size() * own), 0);
       std::vector<int> cnt(std::max<size_t>(1, keys.size() * ng4), 0);
@@ -638,7 +638,7 @@ void build_operators(paw_context *c, const paw_vloc *vloc) {
               last = al;
               break;
             }
-          L[o] = (int8_t)(last >= 0 ? last / 4 : -1);
+          L[o] = (int8_t)(last >= 0 ? last / OWN_GROUP : -1);
           for (int g = 0; g <= L[o]; ++g) cnt[k * ng4 + g]++;
         }
         int16_t *S = sidx.data() + k * own;
