@@ -712,13 +712,13 @@ def sf_flops_per_cell_vec(n1):
     fl = 0
     fl += lines * (split(n1) + 2 * 2 * eo(n1, n1) + 2 * outs(n1))                  # P, Q
     fl += lines * (2 * split(n1) + 3 * 2 * eo(n1, n1) + 2 * n1 + 2 * outs(n1))  # S, R (R = kf T + c S on the halves)
-    fl += lines * (2 * split(n1) + 2 * 2 * eo(n1, n1) + outs(n1))                # y (one accumulator)
     fl += n1 * n1 * (split(n1) + 2 * eo(q1, n1) + outs(q1))                      # U1
     fl += q1 * n1 * (split(n1) + 2 * eo(q1, n1) + outs(q1))                      # U2
     fl += q1 * q1 * (split(n1) + 2 * eo(q1, n1) + outs(q1) + q1)                 # U3 (times w V)
     fl += q1 * q1 * (split(q1) + 2 * eo(n1, q1) + outs(n1))                      # B2
     fl += q1 * n1 * (split(q1) + 2 * eo(n1, q1) + outs(n1))                      # B1
-    fl += n1 * n1 * (split(q1) + 2 * eo(n1, q1) + outs(n1) + n1)                 # y += ...
+    # y: the last kinetic / mass and potential contractions in one accumulator per line
+    fl += lines * (2 * split(n1) + split(q1) + 2 * 2 * eo(n1, n1) + 2 * eo(n1, q1) + outs(n1))
     return fl
 
 

@@ -17,10 +17,13 @@
 //
 // Block: one cell, VT vectors; each 1D contraction handles one line (all
 // points along the contracted direction) per thread, in the even/odd split of
-// the centro-symmetric 1D matrices (about 26.9k FP64 instructions, 45.3k flops,
+// the centro-symmetric 1D matrices (about 26.3k FP64 instructions, 44.6k flops,
 // per cell and vector at p = 6 instead of 35.7k instructions).  Terms that
 // share an output line are summed on the halves before the one recombination
-// (the kinetic factor is folded into the tables kD, kM).  Shared-memory
+// (the kinetic factor is folded into the tables kD, kM); the potential part
+// runs first, so that the last contraction of the kinetic and mass part and the
+// last one of the potential part share their output lines, which are added into
+// Y straight from the registers.  Shared-memory
 // tensors are stored [node][vector] so that consecutive threads touch
 // consecutive words.
 #include <type_traits>
@@ -150,11 +153,11 @@ __device__ __forceinline__ void sf_body(const SfTablesT<R> &tab, int ncells, con
   __shared__ SfTablesT<R> st;
   __shared__ int dofs[N3];
   extern __shared__ double sm[];
-  R *A0 = reinterpret_cast<R *>(sm);   // x                  [N3][VT]
-  R *A1 = A0 + N3 * VT;                // P, then y          [N3][VT]
-  R *A2 = A1 + N3 * VT;                // Q, then U1, B1     [S1][VT]
-  R *A3 = A2 + S1 * VT;                // S, then U2, B2     [S2][VT]
-  R *A4 = A3 + S2 * VT;                // R, then U3         [S3][VT]
+  R *A0 = reinterpret_cast<R *>(sm);   // x, then R          [N3][VT]
+  R *A1 = A0 + N3 * VT;                // P                  [N3][VT]
+  R *A2 = A1 + N3 * VT;                // U1, then B1        [S1][VT]
+  R *A3 = A2 + S1 * VT;                // U2, B2, then Q     [S2][VT]
+  R *A4 = A3 + S2 * VT;                // U3, then S         [S3][VT]
   R *sw = A4 + S3 * VT;                // w_q V_q            [NQ^3]
   const int e = blockIdx.x, v0 = blockIdx.y * VT, tid = threadIdx.x;
   {
@@ -186,63 +189,9 @@ __device__ __forceinline__ void sf_body(const SfTablesT<R> &tab, int ncells, con
   }
   __syncthreads();
   const double mf = st.mfac;
-  // c-contractions, one (a, b) line per thread: P = M_c x, Q = D_c x
-  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
-    const int ab = idx / VT, v = idx - ab * VT;
-    const Split<NP, R> x = split_line<NP, R>(A0 + ab * VT + v, NP * NP * VT);
-    Half<NP, R> P, Q;
-    P.zero();
-    Q.zero();
-    eo_acc<NP, NP, R>(st.M, x, P.E, P.O);
-    eo_acc<NP, NP, R>(st.D, x, Q.E, Q.O);
-#pragma unroll
-    for (int c2 = 0; c2 < NP; ++c2) {
-      A1[(c2 * NP * NP + ab) * VT + v] = P.out(c2);
-      A2[(c2 * NP * NP + ab) * VT + v] = Q.out(c2);
-    }
-  }
-  __syncthreads();
-  // b-contractions, one (a, c) line per thread: S = M_b P, R = kf (D_b P + M_b Q) + c_j mf S,
-  // R formed on the even/odd halves (kf folded into the tables kD, kM)
-  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
-    const int ac = idx / VT, v = idx - ac * VT;
-    const int a = ac % NP, c = ac / NP;
-    const int base = (c * NP * NP + a) * VT + v;
-    const Split<NP, R> p = split_line<NP, R>(A1 + base, NP * VT);
-    const Split<NP, R> q = split_line<NP, R>(A2 + base, NP * VT);
-    Half<NP, R> S, T;
-    S.zero();
-    T.zero();
-    eo_acc<NP, NP, R>(st.M, p, S.E, S.O);
-    eo_acc<NP, NP, R>(st.kD, p, T.E, T.O);
-    eo_acc<NP, NP, R>(st.kM, q, T.E, T.O);
-    const R cmv = A::from((cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0)) * mf);
-#pragma unroll
-    for (int i = 0; i < (NP + 1) / 2; ++i) T.E[i] = A::fma(cmv, A::norm(S.E[i]), T.E[i]);
-#pragma unroll
-    for (int i = 0; i < NP / 2; ++i) T.O[i] = A::fma(cmv, A::norm(S.O[i]), T.O[i]);
-#pragma unroll
-    for (int b2 = 0; b2 < NP; ++b2) {
-      A3[base + b2 * NP * VT] = S.out(b2);
-      A4[base + b2 * NP * VT] = T.out(b2);
-    }
-  }
-  __syncthreads();
-  // a-contractions, one (b, c) line per thread: y = kf D_a S + M_a R (one accumulator)
-  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
-    const int bc = idx / VT, v = idx - bc * VT;
-    const int base = bc * NP * VT + v;
-    const Split<NP, R> sl = split_line<NP, R>(A3 + base, VT);
-    const Split<NP, R> rl = split_line<NP, R>(A4 + base, VT);
-    Half<NP, R> Yl;
-    Yl.zero();
-    eo_acc<NP, NP, R>(st.kD, sl, Yl.E, Yl.O);
-    eo_acc<NP, NP, R>(st.M, rl, Yl.E, Yl.O);
-#pragma unroll
-    for (int a2 = 0; a2 < NP; ++a2) A1[base + a2 * VT] = Yl.out(a2);
-  }
+  // Potential part first (x stays in A0): U1, U2, U3 = w V interpolated values, back to
+  // B1 = Phi^T-contracted along z and y (B1 in A2 until the last stage)
   if (doV) {
-    __syncthreads();
     // U1[c][b][i] = sum_a phi[i][a] x[c][b][a]            (line (b, c), NP -> NQ)
     for (int idx = tid; idx < NP * NP * VT; idx += NT) {
       const int bc = idx / VT, v = idx - bc * VT;
@@ -300,21 +249,69 @@ __device__ __forceinline__ void sf_body(const SfTablesT<R> &tab, int ncells, con
       for (int b = 0; b < NP; ++b) A2[((c * NP + b) * NQ + i) * VT + v] = B.out(b);
     }
     __syncthreads();
-    // y[c][b][a] += sum_i phi[i][a] B1[c][b][i]            (line (b, c))
-    for (int idx = tid; idx < NP * NP * VT; idx += NT) {
-      const int bc = idx / VT, v = idx - bc * VT;
-      const Split<NQ, R> x = split_line<NQ, R>(A2 + bc * NQ * VT + v, VT);
-      Half<NP, R> B;
-      B.zero();
-      eo_acc<NP, NQ, R>(st.phit, x, B.E, B.O);
+  }
+  // kinetic and mass part.  c-contractions, one (a, b) line per thread: P = M_c x (A1), Q = D_c x (A3)
+  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
+    const int ab = idx / VT, v = idx - ab * VT;
+    const Split<NP, R> x = split_line<NP, R>(A0 + ab * VT + v, NP * NP * VT);
+    Half<NP, R> P, Q;
+    P.zero();
+    Q.zero();
+    eo_acc<NP, NP, R>(st.M, x, P.E, P.O);
+    eo_acc<NP, NP, R>(st.D, x, Q.E, Q.O);
 #pragma unroll
-      for (int a = 0; a < NP; ++a) A1[(bc * NP + a) * VT + v] = A::add(A1[(bc * NP + a) * VT + v], B.out(a));
+    for (int c2 = 0; c2 < NP; ++c2) {
+      A1[(c2 * NP * NP + ab) * VT + v] = P.out(c2);
+      A3[(c2 * NP * NP + ab) * VT + v] = Q.out(c2);
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < N3 * VT; idx += NT) {
-    const int r = idx / VT, v = idx - r * VT;
-    if (v0 + v < ncols) atomicAdd(&Y[(size_t)dofs[r] * ldy + v0 + v], alpha * A::to(A1[idx]));
+  // b-contractions, one (a, c) line per thread: S = M_b P (A4), R = kf (D_b P + M_b Q) + c_j mf S
+  // (A0: x is no longer needed), R formed on the even/odd halves (kf folded into the tables kD, kM)
+  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
+    const int ac = idx / VT, v = idx - ac * VT;
+    const int a = ac % NP, c = ac / NP;
+    const int base = (c * NP * NP + a) * VT + v;
+    const Split<NP, R> p = split_line<NP, R>(A1 + base, NP * VT);
+    const Split<NP, R> q = split_line<NP, R>(A3 + base, NP * VT);
+    Half<NP, R> S, T;
+    S.zero();
+    T.zero();
+    eo_acc<NP, NP, R>(st.M, p, S.E, S.O);
+    eo_acc<NP, NP, R>(st.kD, p, T.E, T.O);
+    eo_acc<NP, NP, R>(st.kM, q, T.E, T.O);
+    const R cmv = A::from((cM + (cMcol ? ((v0 + v < ncols) ? cMcol[v0 + v] : 0.0) : 0.0)) * mf);
+#pragma unroll
+    for (int i = 0; i < (NP + 1) / 2; ++i) T.E[i] = A::fma(cmv, A::norm(S.E[i]), T.E[i]);
+#pragma unroll
+    for (int i = 0; i < NP / 2; ++i) T.O[i] = A::fma(cmv, A::norm(S.O[i]), T.O[i]);
+#pragma unroll
+    for (int b2 = 0; b2 < NP; ++b2) {
+      A4[base + b2 * NP * VT] = S.out(b2);
+      A0[base + b2 * NP * VT] = T.out(b2);
+    }
+  }
+  __syncthreads();
+  // a-contractions, one (b, c) line per thread, every term of the line in one accumulator:
+  // y = kf D_a S + M_a R (+ Phi_a^T B1), added into Y straight from the registers
+  for (int idx = tid; idx < NP * NP * VT; idx += NT) {
+    const int bc = idx / VT, v = idx - bc * VT;
+    const int base = bc * NP * VT + v;
+    const Split<NP, R> sl = split_line<NP, R>(A4 + base, VT);
+    const Split<NP, R> rl = split_line<NP, R>(A0 + base, VT);
+    Half<NP, R> Yl;
+    Yl.zero();
+    eo_acc<NP, NP, R>(st.kD, sl, Yl.E, Yl.O);
+    eo_acc<NP, NP, R>(st.M, rl, Yl.E, Yl.O);
+    if (doV) {
+      const Split<NQ, R> bl = split_line<NQ, R>(A2 + bc * NQ * VT + v, VT);
+      eo_acc<NP, NQ, R>(st.phit, bl, Yl.E, Yl.O);
+    }
+    if (v0 + v < ncols) {
+#pragma unroll
+      for (int a2 = 0; a2 < NP; ++a2)
+        atomicAdd(&Y[(size_t)dofs[bc * NP + a2] * ldy + v0 + v], alpha * A::to(Yl.out(a2)));
+    }
   }
 }
 
