@@ -678,8 +678,8 @@ MEASURED_TRAFFIC = {
     ("cell_products", "tf32"): (23.17, "k_tc_stream<CellStream>", "mid"),
     ("recurrence", "tf32"): (25.60, "k_exp_stream<2>", "mid"),
     ("projection", "tf32"): (5.584, "k_tc_stream<ProjStream>", "mid"),
-    ("residual_local", None): (31.46, "k_local_sf<7,double>", "prof12"),
-    ("residual_nonlocal", None): (32.32, "k_own_project64<16,double> + k_own_expand64<16,0,double>", "prof12"),
+    ("residual_local", None): (30.88, "k_local_sf<7,double>", "prof12"),
+    ("residual_nonlocal", None): (32.33, "k_own_project64<16,double> + k_own_expand64<16,0,double>", "prof12"),
 }
 
 

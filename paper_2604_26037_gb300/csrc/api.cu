@@ -150,6 +150,34 @@ __global__ void k_cheb_init(int64_t rows, int ncols, const double *__restrict__ 
   }
 }
 
+// The same for FP32 R with four columns per thread (16-byte rows, ncols % 4 == 0,
+// rows * ncols / 4 < 2^31): 32-byte loads of Y and 16-byte stores, grid-stride.
+__global__ void k_cheb_init4(int64_t rows, int ncols, const double *__restrict__ Y0, int ldy, float s_hi,
+                             float s_lo, float *__restrict__ RY, float *__restrict__ RX, int ldr,
+                             float *__restrict__ Yhi, float *__restrict__ Ylo) {
+  const uint32_t nq = (uint32_t)(ncols / 4), total = (uint32_t)rows * nq;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const uint32_t i = q / nq;
+    const int v = (int)(q - i * nq) * 4;
+    const double2 a = *reinterpret_cast<const double2 *>(Y0 + (int64_t)i * ldy + v);
+    const double2 b = *reinterpret_cast<const double2 *>(Y0 + (int64_t)i * ldy + v + 2);
+    const double y[4] = {a.x, a.y, b.x, b.y};
+    float h[4], l[4], r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      split_hi_lo(y[j], h[j], l[j]);
+      r[j] = fmaf(s_hi, h[j], fmaf(s_hi, l[j], s_lo * h[j]));   // s y to within an FP32 ulp
+    }
+    const int64_t o = (int64_t)i * ldr + v;
+    *reinterpret_cast<float4 *>(RX + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4 *>(RY + o) = make_float4(r[0], r[1], r[2], r[3]);
+    if (Yhi) {
+      *reinterpret_cast<float4 *>(Yhi + o) = make_float4(h[0], h[1], h[2], h[3]);
+      if (Ylo) *reinterpret_cast<float4 *>(Ylo + o) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
 // Loop body of Algorithm 2 when no atom carries projectors:
 //   T = M_D^-1 R_Y,  R_X = [-beta R_Y - gamma R_X] + c_j Y,  c_j = alpha Lambda_Y[j]
 // (FP32: Y as hi/lo words, c_j as chi + clo, error-free product and sum).
@@ -394,8 +422,23 @@ static void block_loop(paw_context *c, paw_precision prec, const double *X, int 
     PhaseScope ps(c, 1, s);
     const double sc = 1.0 / (a0 - cc);
     const float sc_hi = (float)sc, sc_lo = (float)(sc - (double)sc_hi);
-    k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, sc, sc_hi, sc_lo, RY, RX, ldr, Yhi, Ylo);
-    PAW_LAUNCH_CHECK("k_cheb_init");
+    if constexpr (sizeof(TR) == 4) {
+      if (nb % 4 == 0 && ldr % 4 == 0 && M * (nb / 4) < (int64_t(1) << 31)) {
+        int dev = 0, nsm = 0;
+        PAW_CUDA(cudaGetDevice(&dev));
+        PAW_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t quads = M * (nb / 4);
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((quads + 255) / 256, (int64_t)nsm * 16));
+        k_cheb_init4<<<g, 256, 0, s>>>(M, nb, Y0, nb, sc_hi, sc_lo, RY, RX, ldr, Yhi, Ylo);
+        PAW_LAUNCH_CHECK("k_cheb_init4");
+      } else {
+        k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, sc, sc_hi, sc_lo, RY, RX, ldr, Yhi, Ylo);
+        PAW_LAUNCH_CHECK("k_cheb_init");
+      }
+    } else {
+      k_cheb_init<TR><<<ew_grid(M, nb), blk, 0, s>>>(M, nb, Y0, nb, sc, sc_hi, sc_lo, RY, RX, ldr, Yhi, Ylo);
+      PAW_LAUNCH_CHECK("k_cheb_init");
+    }
   }
   const TR *mdinv = mdinv_of<TR>(c);
   // step 4: R_X <- alpha H Shat^-1 R_Y - beta R_Y - gamma R_X + alpha Y Lambda_Y
