@@ -10,9 +10,14 @@
 // The rows of A are contiguous 128-vector slices of a row-major block (a node
 // row of a DoF-major multivector, or a projector row of the atom-major
 // coefficients), so a chunk arrives vector-contiguous (MN-major); four
-// transposer warps turn it into the K-major operand.  (An MN-major TF32 A
-// descriptor, which would let the MMA read the copied rows directly, gave
-// all-zero products on GB300 in a self-checking test, so the pass stays.)
+// transposer warps turn it into the K-major operand.  The landed rows cannot
+// serve as an MN-major operand as they are: each is 512 bytes of 128 vectors at
+// a 512-byte pitch, while the MN-major shared-memory layouts of tcgen05 hold
+// MN-contiguous runs of at most 128 bytes per K row (the 128-, 64- and 32-byte
+// swizzle atoms, 8 K rows of one run each; without swizzle, core matrices of
+// 8 K rows by 16 bytes, 16 bytes apart).  Landing the rows in such a layout
+// takes one TMA copy per 32 vectors of a row, four times the row copies, and
+// the loader's copy issue already sets these kernels' rate.
 // Roles:
 //   warp 0        loader: the K rows of a chunk with TMA row gathers
 //                 (tile::gather4, four 512-byte rows per instruction, issued by
