@@ -47,3 +47,31 @@ def test_density_pins():
     for a in range(op.natoms):
         assert np.abs(D[a] - D[a].T).max() < 1e-14 * np.abs(D[a]).max()
         assert np.linalg.eigvalsh(D[a]).min() > -1e-12 * np.abs(D[a]).max()
+
+
+def test_hellmann_feynman_at_eigenvectors():
+    """S depends on neither V nor Delta_H, so at S-orthonormal eigenvectors X of
+    H x = lambda S x the derivative of the sum of the lowest k eigenvalues along a direction
+    of V (or of Delta_H) is the gradient of E = tr(X^T H X) at X contracted with that
+    direction (k taken at a gap, where the sum is smooth)."""
+    import scipy.linalg as sla
+    from tests.test_oracle_ops import _two_atom
+    s = _two_atom()
+    op = O.PawOperators(s)
+    w, V = sla.eigh(op.dense_H(), op.dense_S())
+    k = next(j for j in range(6, 40) if w[j] - w[j - 1] > 1e-2)
+    dV, dD = grad.energy_grad(op, V[:, :k])
+    rng = np.random.default_rng(12)
+    dirV = rng.standard_normal(op.Vq.shape)
+    dirD = rng.standard_normal(op.D.shape)
+    dirD = 0.5 * (dirD + np.transpose(dirD, (0, 2, 1)))   # symmetric, as Delta_H
+    h = 1e-5
+
+    def lowest(**kw):
+        o = O.PawOperators(s, **kw)
+        return np.sum(sla.eigh(o.dense_H(), o.dense_S(), eigvals_only=True)[:k])
+
+    fd = (lowest(Vq=op.Vq + h * dirV) - lowest(Vq=op.Vq - h * dirV)) / (2 * h)
+    assert abs(fd - np.sum(dV * dirV)) < 1e-6 * abs(fd)
+    fd = (lowest(D=op.D + h * dirD) - lowest(D=op.D - h * dirD)) / (2 * h)
+    assert abs(fd - np.sum(dD * dirD)) < 1e-6 * abs(fd)
