@@ -387,7 +387,15 @@ def run_ours(args, ws, rank, local):
     # the other stream.  The same kernels timed with the blocks one after another (a second
     # handle, a few calls right after the timed region) give each kernel's own rate.
     iso_run = None
+    iso_skip = None
     if overlapped and args.iso_steps > 0:
+        # a second handle holds as much device memory as the first (its workspaces included,
+        # which the timed calls have grown to full size); leave it out where it does not fit
+        free, _ = torch.cuda.mem_get_info()
+        need = int(fe.info()["device_bytes"])
+        if need > 0.9 * free:
+            iso_skip = f"a second handle ({need / 1e9:.1f} GB) does not fit beside the first ({free / 1e9:.1f} GB free)"
+    if overlapped and args.iso_steps > 0 and iso_skip is None:
         fe_s = P.PawFE.from_system(sysd, block=cfg["block"], y0_fp32=args.y0_fp32, y0_pair32=args.y0_pair32,
                                    kpoint=kp, overlap=False)
         iso_run = timed(args.prec, args.iso_steps, 1, profile=True, h=fe_s)
@@ -614,6 +622,8 @@ def run_ours(args, ws, rank, local):
         iso = {"ms_per_step": round(ms_s, 3), "steps": args.iso_steps, "warmup": 1, "clocks": clk_s,
                "phases_ms_per_step": {k: round(v["ms"] / args.iso_steps, 3) for k, v in ph_s.items()},
                "value": round(whole_job_rate(units_per_step, ws, ms_s), 4)}
+    elif iso_skip is not None:
+        iso = {"skipped": iso_skip}
     launches = prof["total_launches"] // args.steps
 
     res = {
